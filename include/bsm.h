@@ -1,0 +1,251 @@
+/*
+ * bsm.h -- C ABI of libbsm: local block-sparse matrix-matrix multiply on one
+ * GB300 (sm_103a), after the local multiplication of the DBCSR library
+ * (Bethune, Gloess, Hutter, Lazzaro, Pabst, Reid 2017, "Porting of the DBCSR
+ * library for Sparse Matrix-Matrix Multiplications to Intel Xeon Phi
+ * systems", §2).
+ *
+ * Matrices are block-CSR (§2: "blocked compressed sparse row"): a vector of
+ * block-row sizes, a vector of block-column sizes, int64 row pointers,
+ * int32 column-block indices (strictly ascending inside each row), and one
+ * int64 element offset per block.  Each block is a small dense matrix stored
+ * row-major at its offset.  The product C = alpha*A.B + beta*C is a sum of
+ * pairwise block products A_ik.B_kj (§2, C = C + A.B), and a block product is
+ * skipped when the product of the two block norms does not exceed the
+ * threshold (§2, on-the-fly filtering).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a bsm_status; no call aborts, throws or traps.
+ *     Argument errors are detected on the host before any launch.  After a
+ *     non-OK status, bsm_last_error() gives a message (thread-local).
+ *   - All device work is issued on the stream set by bsm_set_stream (default:
+ *     the legacy default stream).  Calls that return sizes or counts
+ *     synchronise that stream.
+ *   - "host or device pointer" arguments are copied with cudaMemcpyDefault,
+ *     so both work (pageable, pinned or device memory).
+ *   - Handles are not thread-safe; distinct handles may be used from
+ *     distinct threads only with distinct streams.
+ *   - Device memory owned by the library is allocated stream-ordered
+ *     (cudaMallocAsync) on the library stream and freed the same way.
+ */
+#ifndef BSM_H
+#define BSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsm_mat *bsm_t;
+
+typedef enum {
+    BSM_OK = 0,
+    BSM_ERR_ARG = 1,          /* invalid argument, pattern or sizes          */
+    BSM_ERR_BLOCKING = 2,     /* block sizes of the operands do not conform  */
+    BSM_ERR_CAPACITY = 3,     /* a fixed capacity would be exceeded          */
+    BSM_ERR_ALLOC = 4,        /* device or host allocation failed            */
+    BSM_ERR_CUDA = 5,         /* a CUDA runtime call failed                  */
+    BSM_ERR_TIMEOUT = 6,      /* a bounded device wait gave up               */
+    BSM_ERR_UNSUPPORTED = 7   /* shape or size outside what the kernels take */
+} bsm_status;
+
+typedef enum { BSM_FP64 = 0, BSM_FP32 = 1 } bsm_dtype;
+
+/* Arithmetic used for the block products (the filter, the norms and the
+ * final alpha/beta combination are FP64 for every choice). */
+typedef enum {
+    BSM_P_FP64 = 0,       /* FP64 FMA (FP32 FMA for FP32 data), FP64 sum     */
+    BSM_P_FP64_DMMA = 1,  /* accepted; runs the FP64 FMA path (same FP64 pipe rate) */
+    BSM_P_TF32x3 = 2,     /* hi/lo TF32 split, 3 tensor-core products, FP32 accumulate, FP64 sum */
+    BSM_P_BF16x3 = 3,     /* hi/lo BF16 split, 3 products                    */
+    BSM_P_BF16x6 = 4      /* hi/mid/lo BF16 split, 6 products                */
+} bsm_prec;
+
+typedef struct {
+    int32_t prec;          /* bsm_prec                                              */
+    int32_t post_filter;   /* 1: after the multiply drop C blocks with norm <= eps   */
+    int32_t build_stacks;  /* 1: also bucket the products by (m,n,k) (bsm_get_stacks) */
+    int32_t flush_every;   /* split paths: block products per FP64 flush (0: default) */
+    int32_t reserved[4];   /* must be zero                                          */
+} bsm_opts;
+
+/* Timing phases recorded when profiling is on (milliseconds, CUDA events on
+ * the library stream). */
+enum {
+    BSM_T_NORMS = 0, BSM_T_SYMBOLIC = 1, BSM_T_FILL = 2, BSM_T_STACKS = 3,
+    BSM_T_NUMERIC = 4, BSM_T_POST = 5, BSM_T_TOTAL = 6, BSM_T_COUNT = 7
+};
+
+/* ---------------------------------------------------------------------- */
+/* library state                                                            */
+/* ---------------------------------------------------------------------- */
+
+/* Message describing the last non-OK status on this thread ("" if none). */
+const char *bsm_last_error(void);
+
+/* All subsequent device work is issued on `stream` (a cudaStream_t; NULL
+ * selects the legacy default stream). */
+bsm_status bsm_set_stream(void *stream);
+
+/* 1: record per-phase CUDA-event timings in every multiply (bsm_get_timings). */
+bsm_status bsm_set_profiling(int32_t on);
+
+/* Fills `opts` with the defaults (FP64, no post filter, stacks built). */
+bsm_status bsm_opts_default(bsm_opts *opts);
+
+/* ---------------------------------------------------------------------- */
+/* matrices                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Data modes of bsm_create. */
+enum { BSM_DATA_COPY = 0, BSM_DATA_BORROW = 1 };
+
+/*
+ * Create a block-CSR matrix (§2, blocked CSR format).
+ *   nbr, nbc        number of block rows / block columns (>= 0)
+ *   row_bs, col_bs  block sizes, host arrays of nbr / nbc entries, each >= 1
+ *                   and <= 256; copied.
+ *   row_ptr         host, nbr+1 entries, row_ptr[0] == 0, non-decreasing;
+ *                   nnzb = row_ptr[nbr].  Copied.
+ *   col_idx         host, nnzb entries, strictly ascending inside a row, in
+ *                   [0, nbc).  Copied.
+ *   blk_off         host, nnzb element offsets; block b occupies
+ *                   [blk_off[b], blk_off[b] + row_bs[i]*col_bs[j]) and must lie
+ *                   inside [0, data_len); blocks must not overlap.  Copied.
+ *   dtype           BSM_FP64 or BSM_FP32 element type.
+ *   data, data_len  element storage (data_len elements).
+ *                   BSM_DATA_COPY: host or device pointer, copied into
+ *                   library-owned device memory.
+ *                   BSM_DATA_BORROW: device pointer kept by the handle; the
+ *                   caller keeps it alive and unchanged-in-size until the
+ *                   handle is destroyed or its pattern is replaced.
+ *   data may be NULL only when nnzb == 0.
+ * Errors: BSM_ERR_ARG for any violated rule above (nothing is launched),
+ * BSM_ERR_ALLOC / BSM_ERR_CUDA.
+ */
+bsm_status bsm_create(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_bs,
+                      const int32_t *col_bs, const int64_t *row_ptr, const int32_t *col_idx,
+                      const int64_t *blk_off, int32_t dtype, const void *data,
+                      int64_t data_len, int32_t data_mode);
+
+/* Create an empty matrix (no blocks) with the given blocking; the usual
+ * target of bsm_multiply / bsm_add. */
+bsm_status bsm_create_empty(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_bs,
+                            const int32_t *col_bs, int32_t dtype);
+
+/* Create a matrix with X's blocking and pattern and zero-filled, library-
+ * owned data (for gradients). */
+bsm_status bsm_create_like(bsm_t *out, bsm_t X);
+
+/* Release the handle and the device memory it owns (stream-ordered). */
+bsm_status bsm_destroy(bsm_t X);
+
+/* Sizes of X: any output pointer may be NULL.  Synchronises the stream. */
+bsm_status bsm_get_info(bsm_t X, int32_t *nbr, int32_t *nbc, int64_t *nnzb,
+                        int64_t *data_len, int32_t *dtype);
+
+/* Copy X's pattern out (host or device destinations; NULL skips an array):
+ * row_ptr nbr+1 entries, col_idx and blk_off nnzb entries. */
+bsm_status bsm_copy_pattern(bsm_t X, int64_t *row_ptr, int32_t *col_idx, int64_t *blk_off);
+
+/* Copy X's data_len elements to `dst` (host or device). */
+bsm_status bsm_copy_data(bsm_t X, void *dst);
+
+/* Overwrite X's data with data_len elements from `src` (host or device);
+ * invalidates the cached block norms. */
+bsm_status bsm_set_data(bsm_t X, const void *src);
+
+/* Device pointer of X's element storage (owned or borrowed). */
+bsm_status bsm_data_ptr(bsm_t X, void **dptr);
+
+/* FP64 Frobenius norm of every block (§2 filtering criterion): fma chain
+ * over the block's elements in row-major order from +0.0, then IEEE sqrt;
+ * FP32 elements widened first.  `out`: nnzb doubles, host or device. */
+bsm_status bsm_block_norms(bsm_t X, double *out);
+
+/* ---------------------------------------------------------------------- */
+/* multiply                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * C = alpha * A.B + beta * C  (§2: local multiplication C = C + A.B as
+ * pairwise products of small dense blocks, with on-the-fly filtering).
+ *
+ *   A: nbr x nbk blocks, B: nbk x nbc blocks; A's block-column sizes must
+ *   equal B's block-row sizes, C's block-row sizes A's, C's block-column
+ *   sizes B's (else BSM_ERR_BLOCKING).  A and B may be the same handle; C
+ *   must differ from both.  A, B and C share one dtype.
+ *   filter_eps: when > 0, the block product A_ik.B_kj is performed iff
+ *   norm(A_ik) * norm(B_kj) > filter_eps (FP64 norms as bsm_block_norms);
+ *   when <= 0 every product of present blocks is performed.
+ *   beta == 0: the old C is not read and its pattern is dropped.
+ *   beta != 0: C's new pattern is the union of the old pattern and the
+ *   pattern of the kept products; old blocks are scaled by beta.
+ *   C's pattern and data are always replaced by library-owned storage; C
+ *   keeps the kept-product list (canonical order: C block row i, then C
+ *   block column j, then k, all ascending) for bsm_multiply_backward and,
+ *   with opts->build_stacks, the per-shape stacks for bsm_get_stacks.
+ *   opts may be NULL (defaults).  The call synchronises the stream once,
+ *   after the symbolic phase, to size C.
+ */
+bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C,
+                        double filter_eps, const bsm_opts *opts);
+
+/*
+ * Adjoint of the last bsm_multiply that wrote C (C = alpha*A.B + ...), at
+ * that multiply's keep-decisions:
+ *   dA_ik = alpha * sum_j dC_ij . B_kj^T   over the kept products (i,k,j)
+ *   dB_kj = alpha * sum_i A_ik^T . dC_ij
+ * dC_data: device pointer laid out with C's blk_off (C's data_len elements,
+ * C's dtype).  dA_data / dB_data: device pointers laid out like A's / B's
+ * data (overwritten, blocks without products set to zero); either may be
+ * NULL.  A and B must be the handles (same pattern) used in that multiply.
+ */
+bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm_t A, bsm_t B,
+                                 void *dA_data, void *dB_data, const bsm_opts *opts);
+
+/* Counts of the last multiply into C: kept products, filtered candidate
+ * products and useful FLOPs (sum of 2*m*n*k over kept products). */
+bsm_status bsm_get_counts(bsm_t C, int64_t *products, int64_t *filtered, double *useful_flop);
+
+/* Per-phase timings of the last multiply into C (BSM_T_COUNT doubles, ms),
+ * valid when profiling was on.  Synchronises the stream. */
+bsm_status bsm_get_timings(bsm_t C, double *ms);
+
+/*
+ * Kept products of the last multiply into C as block indices (canonical
+ * order): a_idx into A's blocks, b_idx into B's, c_idx into C's.  Pass NULL
+ * pointers to query *nprod only; otherwise each array holds *nprod entries
+ * (host or device).
+ */
+bsm_status bsm_get_products(bsm_t C, int64_t *nprod, int32_t *a_idx, int32_t *b_idx,
+                            int32_t *c_idx);
+
+/*
+ * Stacks of the last multiply into C (built with opts->build_stacks): the
+ * kept products bucketed by block shape (m, n, k) -- the batches of §2.
+ * Shapes appear in lexicographic (m, n, k) order; inside a shape, products
+ * keep the canonical (i, j, k) order.  Pass NULL arrays to query
+ * *nshapes / *nprod; then shapes holds 3*nshapes int32 (m, n, k),
+ * stack_ptr nshapes+1 int64, triples 3*nprod int64 (a_off, b_off, c_off)
+ * element offsets.  Host or device destinations.
+ */
+bsm_status bsm_get_stacks(bsm_t C, int32_t *nshapes, int64_t *nprod, int32_t *shapes,
+                          int64_t *stack_ptr, int64_t *triples);
+
+/* ---------------------------------------------------------------------- */
+/* block add (the purification chain's Z = 3 X^2 - 2 X^3)                   */
+/* ---------------------------------------------------------------------- */
+
+/* Z = a*X + b*Y over the union of X's and Y's patterns; with
+ * filter_eps > 0 a result block is kept iff its FP64 norm > filter_eps.
+ * X, Y and Z share one blocking and dtype; Z differs from X and Y.  Z's
+ * pattern and data are replaced. */
+bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSM_H */

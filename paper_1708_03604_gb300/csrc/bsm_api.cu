@@ -1,0 +1,979 @@
+// C ABI of libbsm (declared in include/bsm.h): handle management, argument
+// validation and the orchestration of the symbolic, stack and numeric
+// kernels of the local block-sparse multiply (DBCSR, Bethune et al. 2017 §2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bsm_internal.cuh"
+
+namespace bsm {
+
+namespace {
+thread_local std::string t_err;
+cudaStream_t g_stream = nullptr;
+bool g_prof = false;
+bool g_pool_configured = false;
+int64_t *g_host = nullptr;  // pinned host words for small device->host reads
+
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch() {
+        for (void *p : ptrs) dfree(p);
+    }
+    template <typename T>
+    bsm_status get(T **p, size_t n) {
+        bsm_status st = dalloc_t(p, n);
+        if (st == BSM_OK) ptrs.push_back(*p);
+        return st;
+    }
+    void release(void *p) {  // hand ownership of p to the caller
+        ptrs.erase(std::remove(ptrs.begin(), ptrs.end(), p), ptrs.end());
+    }
+};
+
+bsm_status ensure_globals() {
+    if (!g_pool_configured) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return set_error(BSM_ERR_CUDA, "cudaGetDevice failed");
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        g_pool_configured = true;
+    }
+    if (!g_host) {
+        if (cudaMallocHost(&g_host, 64 * sizeof(int64_t)) != cudaSuccess) {
+            g_host = nullptr;
+            return set_error(BSM_ERR_ALLOC, "cudaMallocHost failed");
+        }
+    }
+    return BSM_OK;
+}
+
+size_t esize(int32_t dtype) { return dtype == BSM_FP64 ? 8 : 4; }
+
+bool same_vec(const std::vector<int32_t> &a, const std::vector<int32_t> &b) { return a == b; }
+
+struct Events {
+    cudaEvent_t ev[BSM_T_COUNT + 1] = {};
+    bool on = false;
+    void start() {
+        on = g_prof;
+        if (!on) return;
+        for (auto &e : ev) cudaEventCreate(&e);
+    }
+    void mark(int idx) {
+        if (on) cudaEventRecord(ev[idx], g_stream);
+    }
+    ~Events() {
+        if (on)
+            for (auto &e : ev) cudaEventDestroy(e);
+    }
+};
+
+void free_results(bsm_mat *C) {
+    dfree(C->cptr); C->cptr = nullptr;
+    dfree(C->pa); C->pa = nullptr;
+    dfree(C->pb); C->pb = nullptr;
+    dfree(C->pc); C->pc = nullptr;
+    dfree(C->stack_ptr); C->stack_ptr = nullptr;
+    dfree(C->triples); C->triples = nullptr;
+    C->nprod = 0; C->nfiltered = 0; C->useful_flop = 0.0;
+    C->nshapes = 0; C->h_shapes.clear();
+    C->prod_A = C->prod_B = nullptr;
+    C->prod_A_nnzb = C->prod_B_nnzb = -1;
+    C->timings_valid = false;
+}
+
+void free_pattern(bsm_mat *X) {
+    dfree(X->row_ptr); X->row_ptr = nullptr;
+    dfree(X->col_idx); X->col_idx = nullptr;
+    dfree(X->blk_off); X->blk_off = nullptr;
+    dfree(X->blk_rc); X->blk_rc = nullptr;
+    if (X->own_data) dfree(X->data);
+    X->data = nullptr;
+    X->own_data = false;
+    dfree(X->norms); X->norms = nullptr;
+    X->norms_valid = false;
+    X->nnzb = 0;
+    X->data_len = 0;
+}
+
+bsm_status check_opts(const bsm_opts *o, bsm_opts *out) {
+    bsm_opts_default(out);
+    if (!o) return BSM_OK;
+    *out = *o;
+    if (o->prec < BSM_P_FP64 || o->prec > BSM_P_BF16x6) return set_error(BSM_ERR_ARG, "opts.prec out of range");
+    if (o->flush_every < 0) return set_error(BSM_ERR_ARG, "opts.flush_every < 0");
+    for (int q = 0; q < 4; ++q)
+        if (o->reserved[q] != 0) return set_error(BSM_ERR_ARG, "opts.reserved must be zero");
+    return BSM_OK;
+}
+
+bool is_tc(int prec) { return prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6; }
+
+// packed fragment planes of one operand (tensor-core paths)
+struct Packed {
+    int64_t *off = nullptr;  // [nnzb+1] word offsets
+    uint32_t *words = nullptr;
+};
+
+// Launch pack-size computation and its scan; the total lands in off[nnzb].
+bsm_status pack_prepare(Scratch &sc, const bsm_mat *M, int role_y, int trans, int prec, Packed &pk) {
+    int64_t *w = nullptr, *tmp = nullptr;
+    bsm_status st;
+    if ((st = sc.get(&w, (size_t)M->nnzb)) != BSM_OK) return st;
+    if ((st = sc.get(&pk.off, (size_t)M->nnzb + 1)) != BSM_OK) return st;
+    if ((st = sc.get(&tmp, scan_tmp_elems(M->nnzb))) != BSM_OK) return st;
+    cudaError_t e = launch_pack_sizes(M, role_y, trans, prec, w, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(w, pk.off, M->nnzb, tmp, g_stream);
+    return cuda_check(e, "pack sizes");
+}
+
+bsm_status pack_fill(Scratch &sc, const bsm_mat *M, int role_y, int trans, int prec, Packed &pk,
+                     int64_t total_words) {
+    bsm_status st;
+    if ((st = sc.get(&pk.words, (size_t)total_words + 16)) != BSM_OK) return st;
+    return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, g_stream), "pack");
+}
+
+bsm_status read_words(const int64_t *const *src, int n) {
+    for (int q = 0; q < n; ++q) {
+        cudaError_t e = cudaMemcpyAsync(g_host + q, src[q], sizeof(int64_t), cudaMemcpyDeviceToHost, g_stream);
+        if (e != cudaSuccess) return cuda_check(e, "reading sizes");
+    }
+    return cuda_check(cudaStreamSynchronize(g_stream), "stream synchronize");
+}
+
+}  // namespace
+
+cudaStream_t stream() { return g_stream; }
+bool profiling() { return g_prof; }
+
+bsm_status set_error(bsm_status st, const std::string &msg) {
+    t_err = msg;
+    return st;
+}
+
+bsm_status cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return BSM_OK;
+    return set_error(e == cudaErrorMemoryAllocation ? BSM_ERR_ALLOC : BSM_ERR_CUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bsm_status dalloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, g_stream);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(BSM_ERR_ALLOC, std::string("device allocation of ") + std::to_string(bytes) +
+                                            " bytes failed: " + cudaGetErrorString(e));
+    }
+    return BSM_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFreeAsync(p, g_stream);
+}
+
+// --------------------------------------------------------------------------
+// shared step: drop blocks with norm <= eps from X (in place), compacting
+// --------------------------------------------------------------------------
+bsm_status norm_filter_compact(bsm_mat *X, double eps) {
+    if (X->nnzb == 0) return BSM_OK;
+    Scratch sc;
+    bsm_status st;
+    double *nrm = nullptr;
+    int64_t *keep = nullptr, *kscan = nullptr, *tmp = nullptr, *rcnt = nullptr, *relem = nullptr,
+            *nrow = nullptr, *nelem = nullptr;
+    const int64_t nb = X->nnzb;
+    if ((st = sc.get(&nrm, nb)) || (st = sc.get(&keep, nb)) || (st = sc.get(&kscan, nb + 1)) ||
+        (st = sc.get(&tmp, scan_tmp_elems(std::max<int64_t>(nb, X->nbr)))) || (st = sc.get(&rcnt, X->nbr)) ||
+        (st = sc.get(&relem, X->nbr)) || (st = sc.get(&nrow, X->nbr + 1)) || (st = sc.get(&nelem, X->nbr + 1)))
+        return st;
+    cudaError_t e = launch_block_norms(X, nrm, g_stream);
+    if (e == cudaSuccess) e = launch_keep_flags(nb, nrm, eps, keep, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(keep, kscan, nb, tmp, g_stream);
+    if (e == cudaSuccess) e = launch_row_keep_counts(X->nbr, X->row_ptr, keep, X->blk_rc, rcnt, relem, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(rcnt, nrow, X->nbr, tmp, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(relem, nelem, X->nbr, tmp, g_stream);
+    if ((st = cuda_check(e, "norm filter"))) return st;
+    const int64_t *src[2] = {nrow + X->nbr, nelem + X->nbr};
+    if ((st = read_words(src, 2))) return st;
+    const int64_t nnz2 = g_host[0], len2 = g_host[1];
+    if (nnz2 == nb) return BSM_OK;  // nothing dropped
+    int32_t *ncol = nullptr, *nrc = nullptr;
+    int64_t *noff = nullptr;
+    void *ndata = nullptr;
+    if ((st = sc.get(&ncol, nnz2)) || (st = sc.get(&noff, nnz2)) || (st = sc.get(&nrc, nnz2))) return st;
+    if ((st = dalloc(&ndata, (size_t)len2 * esize(X->dtype)))) return st;
+    sc.ptrs.push_back(ndata);
+    CompactArgs c{X->nbr, X->row_ptr, X->col_idx, X->blk_off, X->blk_rc, kscan, nrow, nelem,
+                  X->data, X->dtype, ncol, noff, nrc, ndata};
+    if ((st = cuda_check(launch_compact(c, g_stream), "compact"))) return st;
+    // swap in
+    dfree(X->row_ptr); dfree(X->col_idx); dfree(X->blk_off); dfree(X->blk_rc);
+    if (X->own_data) dfree(X->data);
+    dfree(X->norms);
+    X->norms = nullptr;
+    X->norms_valid = false;
+    X->row_ptr = nrow; X->col_idx = ncol; X->blk_off = noff; X->blk_rc = nrc; X->data = ndata;
+    X->own_data = true;
+    X->nnzb = nnz2; X->data_len = len2;
+    for (void *p : {(void *)nrow, (void *)ncol, (void *)noff, (void *)nrc, ndata}) sc.release(p);
+    return BSM_OK;
+}
+
+}  // namespace bsm
+
+using namespace bsm;
+
+// ==========================================================================
+// ABI
+// ==========================================================================
+extern "C" {
+
+const char *bsm_last_error(void) { return t_err.c_str(); }
+
+bsm_status bsm_set_stream(void *s) {
+    g_stream = static_cast<cudaStream_t>(s);
+    return BSM_OK;
+}
+
+bsm_status bsm_set_profiling(int32_t on) {
+    g_prof = on != 0;
+    return BSM_OK;
+}
+
+bsm_status bsm_opts_default(bsm_opts *o) {
+    if (!o) return set_error(BSM_ERR_ARG, "opts is NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->prec = BSM_P_FP64;
+    o->post_filter = 0;
+    o->build_stacks = 1;
+    o->flush_every = 0;
+    return BSM_OK;
+}
+
+static bsm_status create_common(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_bs,
+                                const int32_t *col_bs, int32_t dtype, bsm_mat **made) {
+    if (!out) return set_error(BSM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nbr < 0 || nbc < 0) return set_error(BSM_ERR_ARG, "negative block count");
+    if ((nbr > 0 && !row_bs) || (nbc > 0 && !col_bs)) return set_error(BSM_ERR_ARG, "block sizes are NULL");
+    if (dtype != BSM_FP64 && dtype != BSM_FP32) return set_error(BSM_ERR_ARG, "dtype must be BSM_FP64 or BSM_FP32");
+    for (int32_t i = 0; i < nbr; ++i)
+        if (row_bs[i] < 1 || row_bs[i] > kMaxBlockDim) return set_error(BSM_ERR_ARG, "row block size outside [1, 256]");
+    for (int32_t j = 0; j < nbc; ++j)
+        if (col_bs[j] < 1 || col_bs[j] > kMaxBlockDim) return set_error(BSM_ERR_ARG, "column block size outside [1, 256]");
+    bsm_status st = ensure_globals();
+    if (st) return st;
+    bsm_mat *X = new bsm_mat();
+    X->nbr = nbr;
+    X->nbc = nbc;
+    X->dtype = dtype;
+    X->h_row_bs.assign(row_bs, row_bs + nbr);
+    X->h_col_bs.assign(col_bs, col_bs + nbc);
+    for (int32_t v : X->h_row_bs) X->max_bs_row = std::max(X->max_bs_row, v);
+    for (int32_t v : X->h_col_bs) X->max_bs_col = std::max(X->max_bs_col, v);
+    if ((st = dalloc_t(&X->row_bs, nbr)) || (st = dalloc_t(&X->col_bs, nbc))) {
+        delete X;
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(X->row_bs, row_bs, sizeof(int32_t) * nbr, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(X->col_bs, col_bs, sizeof(int32_t) * nbc, cudaMemcpyHostToDevice, g_stream);
+    if (e != cudaSuccess) {
+        dfree(X->row_bs); dfree(X->col_bs);
+        delete X;
+        return cuda_check(e, "copy block sizes");
+    }
+    *made = X;
+    return BSM_OK;
+}
+
+bsm_status bsm_create(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_bs, const int32_t *col_bs,
+                      const int64_t *row_ptr, const int32_t *col_idx, const int64_t *blk_off, int32_t dtype,
+                      const void *data, int64_t data_len, int32_t data_mode) {
+    if (!row_ptr) return set_error(BSM_ERR_ARG, "row_ptr is NULL");
+    if (data_mode != BSM_DATA_COPY && data_mode != BSM_DATA_BORROW) return set_error(BSM_ERR_ARG, "bad data_mode");
+    if (row_ptr[0] != 0) return set_error(BSM_ERR_ARG, "row_ptr[0] != 0");
+    for (int32_t i = 0; i < nbr; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return set_error(BSM_ERR_ARG, "row_ptr decreases");
+    const int64_t nnzb = nbr > 0 ? row_ptr[nbr] : 0;
+    if (nnzb > INT32_MAX) return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31-1 blocks");
+    if (nnzb > 0 && (!col_idx || !blk_off || !data)) return set_error(BSM_ERR_ARG, "col_idx/blk_off/data NULL");
+    if (data_len < 0) return set_error(BSM_ERR_ARG, "data_len < 0");
+    // pattern checks (host, before any launch)
+    if (nbr > 0 && !row_bs) return set_error(BSM_ERR_ARG, "row_bs is NULL");
+    if (nbc > 0 && !col_bs) return set_error(BSM_ERR_ARG, "col_bs is NULL");
+    std::vector<std::pair<int64_t, int64_t>> spans;
+    spans.reserve((size_t)nnzb);
+    for (int32_t i = 0; i < nbr; ++i) {
+        for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+            const int32_t j = col_idx[b];
+            if (j < 0 || j >= nbc) return set_error(BSM_ERR_ARG, "col_idx out of range");
+            if (b > row_ptr[i] && col_idx[b - 1] >= j) return set_error(BSM_ERR_ARG, "col_idx not strictly ascending in a row");
+            if (row_bs[i] < 1 || row_bs[i] > kMaxBlockDim || col_bs[j] < 1 || col_bs[j] > kMaxBlockDim)
+                return set_error(BSM_ERR_ARG, "block size outside [1, 256]");
+            const int64_t len = (int64_t)row_bs[i] * col_bs[j];
+            if (blk_off[b] < 0 || blk_off[b] + len > data_len) return set_error(BSM_ERR_ARG, "block outside data_len");
+            spans.emplace_back(blk_off[b], len);
+        }
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t q = 1; q < spans.size(); ++q)
+        if (spans[q - 1].first + spans[q - 1].second > spans[q].first) return set_error(BSM_ERR_ARG, "blocks overlap");
+    if (data_mode == BSM_DATA_BORROW && data) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, data) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return set_error(BSM_ERR_ARG, "BSM_DATA_BORROW needs a device pointer");
+        }
+    }
+    bsm_mat *X = nullptr;
+    bsm_status st = create_common(out, nbr, nbc, row_bs, col_bs, dtype, &X);
+    if (st) return st;
+    X->nnzb = nnzb;
+    X->data_len = data_len;
+    if ((st = dalloc_t(&X->row_ptr, (size_t)nbr + 1)) || (st = dalloc_t(&X->col_idx, nnzb)) ||
+        (st = dalloc_t(&X->blk_off, nnzb)) || (st = dalloc_t(&X->blk_rc, nnzb))) {
+        bsm_destroy(X);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(X->row_ptr, row_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess && nnzb)
+        e = cudaMemcpyAsync(X->col_idx, col_idx, sizeof(int32_t) * nnzb, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess && nnzb)
+        e = cudaMemcpyAsync(X->blk_off, blk_off, sizeof(int64_t) * nnzb, cudaMemcpyHostToDevice, g_stream);
+    if (e != cudaSuccess) {
+        bsm_destroy(X);
+        return cuda_check(e, "copy pattern");
+    }
+    if (data_mode == BSM_DATA_BORROW) {
+        X->data = const_cast<void *>(data);
+        X->own_data = false;
+    } else {
+        if ((st = dalloc(&X->data, (size_t)data_len * esize(dtype)))) {
+            bsm_destroy(X);
+            return st;
+        }
+        X->own_data = true;
+        if (data_len > 0) {
+            e = cudaMemcpyAsync(X->data, data, (size_t)data_len * esize(dtype), cudaMemcpyDefault, g_stream);
+            if (e != cudaSuccess) {
+                bsm_destroy(X);
+                return cuda_check(e, "copy data");
+            }
+        }
+    }
+    if ((st = cuda_check(launch_blk_rc(X, X->blk_rc, g_stream), "block shapes"))) {
+        bsm_destroy(X);
+        return st;
+    }
+    // pageable host sources: make sure the copies have consumed them
+    if ((st = cuda_check(cudaStreamSynchronize(g_stream), "stream synchronize"))) {
+        bsm_destroy(X);
+        return st;
+    }
+    *out = X;
+    return BSM_OK;
+}
+
+bsm_status bsm_create_empty(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_bs, const int32_t *col_bs,
+                            int32_t dtype) {
+    bsm_mat *X = nullptr;
+    bsm_status st = create_common(out, nbr, nbc, row_bs, col_bs, dtype, &X);
+    if (st) return st;
+    if ((st = dalloc_t(&X->row_ptr, (size_t)nbr + 1))) {
+        bsm_destroy(X);
+        return st;
+    }
+    cudaError_t e = cudaMemsetAsync(X->row_ptr, 0, sizeof(int64_t) * (nbr + 1), g_stream);
+    if ((st = cuda_check(e, "memset"))) {
+        bsm_destroy(X);
+        return st;
+    }
+    if ((st = cuda_check(cudaStreamSynchronize(g_stream), "stream synchronize"))) {
+        bsm_destroy(X);
+        return st;
+    }
+    *out = X;
+    return BSM_OK;
+}
+
+bsm_status bsm_create_like(bsm_t *out, bsm_t X) {
+    if (!X) return set_error(BSM_ERR_ARG, "X is NULL");
+    bsm_mat *Y = nullptr;
+    bsm_status st = create_common(out, X->nbr, X->nbc, X->h_row_bs.data(), X->h_col_bs.data(), X->dtype, &Y);
+    if (st) return st;
+    Y->nnzb = X->nnzb;
+    Y->data_len = X->data_len;
+    if ((st = dalloc_t(&Y->row_ptr, (size_t)X->nbr + 1)) || (st = dalloc_t(&Y->col_idx, X->nnzb)) ||
+        (st = dalloc_t(&Y->blk_off, X->nnzb)) || (st = dalloc_t(&Y->blk_rc, X->nnzb)) ||
+        (st = dalloc(&Y->data, (size_t)X->data_len * esize(X->dtype)))) {
+        bsm_destroy(Y);
+        return st;
+    }
+    Y->own_data = true;
+    cudaError_t e = cudaMemcpyAsync(Y->row_ptr, X->row_ptr, sizeof(int64_t) * (X->nbr + 1), cudaMemcpyDeviceToDevice, g_stream);
+    if (e == cudaSuccess && X->nnzb) {
+        e = cudaMemcpyAsync(Y->col_idx, X->col_idx, sizeof(int32_t) * X->nnzb, cudaMemcpyDeviceToDevice, g_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Y->blk_off, X->blk_off, sizeof(int64_t) * X->nnzb, cudaMemcpyDeviceToDevice, g_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Y->blk_rc, X->blk_rc, sizeof(int32_t) * X->nnzb, cudaMemcpyDeviceToDevice, g_stream);
+    }
+    if (e == cudaSuccess && X->data_len)
+        e = cudaMemsetAsync(Y->data, 0, (size_t)X->data_len * esize(X->dtype), g_stream);
+    if ((st = cuda_check(e, "create_like"))) {
+        bsm_destroy(Y);
+        return st;
+    }
+    *out = Y;
+    return BSM_OK;
+}
+
+bsm_status bsm_destroy(bsm_t X) {
+    if (!X) return BSM_OK;
+    free_results(X);
+    free_pattern(X);
+    dfree(X->row_bs);
+    dfree(X->col_bs);
+    delete X;
+    return BSM_OK;
+}
+
+bsm_status bsm_get_info(bsm_t X, int32_t *nbr, int32_t *nbc, int64_t *nnzb, int64_t *data_len, int32_t *dtype) {
+    if (!X) return set_error(BSM_ERR_ARG, "X is NULL");
+    if (nbr) *nbr = X->nbr;
+    if (nbc) *nbc = X->nbc;
+    if (nnzb) *nnzb = X->nnzb;
+    if (data_len) *data_len = X->data_len;
+    if (dtype) *dtype = X->dtype;
+    return BSM_OK;
+}
+
+bsm_status bsm_copy_pattern(bsm_t X, int64_t *row_ptr, int32_t *col_idx, int64_t *blk_off) {
+    if (!X) return set_error(BSM_ERR_ARG, "X is NULL");
+    cudaError_t e = cudaSuccess;
+    if (row_ptr) e = cudaMemcpyAsync(row_ptr, X->row_ptr, sizeof(int64_t) * (X->nbr + 1), cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess && col_idx && X->nnzb)
+        e = cudaMemcpyAsync(col_idx, X->col_idx, sizeof(int32_t) * X->nnzb, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess && blk_off && X->nnzb)
+        e = cudaMemcpyAsync(blk_off, X->blk_off, sizeof(int64_t) * X->nnzb, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    return cuda_check(e, "copy pattern");
+}
+
+bsm_status bsm_copy_data(bsm_t X, void *dst) {
+    if (!X || (!dst && X->data_len)) return set_error(BSM_ERR_ARG, "NULL argument");
+    if (X->data_len == 0) return BSM_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, X->data, (size_t)X->data_len * esize(X->dtype), cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    return cuda_check(e, "copy data");
+}
+
+bsm_status bsm_set_data(bsm_t X, const void *src) {
+    if (!X || (!src && X->data_len)) return set_error(BSM_ERR_ARG, "NULL argument");
+    X->norms_valid = false;
+    if (X->data_len == 0) return BSM_OK;
+    cudaError_t e = cudaMemcpyAsync(X->data, src, (size_t)X->data_len * esize(X->dtype), cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    return cuda_check(e, "set data");
+}
+
+bsm_status bsm_data_ptr(bsm_t X, void **dptr) {
+    if (!X || !dptr) return set_error(BSM_ERR_ARG, "NULL argument");
+    *dptr = X->data;
+    return BSM_OK;
+}
+
+bsm_status bsm_block_norms(bsm_t X, double *out) {
+    if (!X || (!out && X->nnzb)) return set_error(BSM_ERR_ARG, "NULL argument");
+    if (X->nnzb == 0) return BSM_OK;
+    Scratch sc;
+    double *d = nullptr;
+    bsm_status st = sc.get(&d, X->nnzb);
+    if (st) return st;
+    cudaError_t e = launch_block_norms(X, d, g_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * X->nnzb, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    return cuda_check(e, "block norms");
+}
+
+// --------------------------------------------------------------------------
+// multiply
+// --------------------------------------------------------------------------
+bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, double filter_eps,
+                        const bsm_opts *opts_in) {
+    if (!A || !B || !C) return set_error(BSM_ERR_ARG, "NULL matrix");
+    if (C == A || C == B) return set_error(BSM_ERR_ARG, "C must differ from A and B");
+    bsm_opts opts;
+    bsm_status st = check_opts(opts_in, &opts);
+    if (st) return st;
+    if (A->dtype != B->dtype || A->dtype != C->dtype) return set_error(BSM_ERR_ARG, "A, B and C must share a dtype");
+    if (A->nbc != B->nbr || !same_vec(A->h_col_bs, B->h_row_bs))
+        return set_error(BSM_ERR_BLOCKING, "A's block columns do not match B's block rows");
+    if (C->nbr != A->nbr || !same_vec(C->h_row_bs, A->h_row_bs))
+        return set_error(BSM_ERR_BLOCKING, "C's block rows do not match A's block rows");
+    if (C->nbc != B->nbc || !same_vec(C->h_col_bs, B->h_col_bs))
+        return set_error(BSM_ERR_BLOCKING, "C's block columns do not match B's block columns");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || std::isnan(filter_eps))
+        return set_error(BSM_ERR_ARG, "alpha, beta and eps must be finite");
+    if ((st = ensure_globals())) return st;
+
+    const int32_t nbr = A->nbr, nbk = A->nbc, nbc = B->nbc;
+    const bool use_filter = filter_eps > 0.0;
+    const bool use_old = beta != 0.0 && C->nnzb > 0;
+    const int32_t nwords = (nbc + 31) / 32;
+    Events ev;
+    ev.start();
+    ev.mark(0);
+    Scratch sc;
+
+    // ---- a1: block norms (FP64) of A and B
+    double *nA = nullptr, *nB = nullptr;
+    if (use_filter) {
+        if ((st = sc.get(&nA, A->nnzb))) return st;
+        if ((st = cuda_check(launch_block_norms(A, nA, g_stream), "norms A"))) return st;
+        if (B == A) {
+            nB = nA;
+        } else {
+            if ((st = sc.get(&nB, B->nnzb))) return st;
+            if ((st = cuda_check(launch_block_norms(B, nB, g_stream), "norms B"))) return st;
+        }
+    }
+    ev.mark(1);
+
+    // ---- a2: symbolic count
+    SymbolicArgs sa{};
+    sa.nbr = nbr; sa.nbk = nbk; sa.nbc = nbc;
+    sa.a_row_bs = A->row_bs; sa.a_col_bs = A->col_bs; sa.a_row_ptr = A->row_ptr; sa.a_col_idx = A->col_idx;
+    sa.a_norm = nA;
+    sa.b_row_ptr = B->row_ptr; sa.b_col_idx = B->col_idx; sa.b_col_bs = B->col_bs; sa.b_norm = nB;
+    sa.o_row_ptr = use_old ? C->row_ptr : nullptr;
+    sa.o_col_idx = use_old ? C->col_idx : nullptr;
+    sa.o_blk_off = use_old ? C->blk_off : nullptr;
+    sa.eps = filter_eps;
+    sa.use_filter = use_filter ? 1 : 0;
+    sa.nwords = nwords;
+    if ((size_t)nwords * 4 > 200 * 1024) return set_error(BSM_ERR_UNSUPPORTED, "too many block columns for the symbolic phase");
+    int64_t *prod_cnt, *ccol_cnt, *celem_cnt, *prod_ptr, *crow_ptr, *celem_ptr, *stmp;
+    uint32_t *bitmaps;
+    unsigned long long *totals;
+    if ((st = sc.get(&prod_cnt, nbr)) || (st = sc.get(&ccol_cnt, nbr)) || (st = sc.get(&celem_cnt, nbr)) ||
+        (st = sc.get(&prod_ptr, (size_t)nbr + 1)) || (st = sc.get(&crow_ptr, (size_t)nbr + 1)) ||
+        (st = sc.get(&celem_ptr, (size_t)nbr + 1)) || (st = sc.get(&stmp, scan_tmp_elems(nbr))) ||
+        (st = sc.get(&bitmaps, (size_t)nbr * nwords)) || (st = sc.get(&totals, 4)))
+        return st;
+    cudaError_t e = cudaMemsetAsync(totals, 0, 4 * sizeof(unsigned long long), g_stream);
+    if (e == cudaSuccess) e = launch_symbolic_count(sa, prod_cnt, ccol_cnt, celem_cnt, bitmaps, totals, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(prod_cnt, prod_ptr, nbr, stmp, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(ccol_cnt, crow_ptr, nbr, stmp, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(celem_cnt, celem_ptr, nbr, stmp, g_stream);
+    if ((st = cuda_check(e, "symbolic count"))) return st;
+    // pack sizes of the tensor-core operands, read with the symbolic totals
+    Packed pkA, pkB;
+    const bool tc = is_tc(opts.prec);
+    if (tc) {
+        if ((st = pack_prepare(sc, A, 0, 0, opts.prec, pkA))) return st;
+        if ((st = pack_prepare(sc, B, 1, 0, opts.prec, pkB))) return st;
+    }
+    // max C columns in a row: reuse a scan-free reduction on the host side
+    // (nbr values, small) -- read the whole ccol_cnt array
+    std::vector<int64_t> h_ccnt((size_t)nbr);
+    const int64_t zero = 0;
+    const int64_t *src[7] = {prod_ptr + nbr, crow_ptr + nbr, celem_ptr + nbr, (const int64_t *)totals,
+                             (const int64_t *)(totals + 1), tc ? pkA.off + A->nnzb : &zero,
+                             tc ? pkB.off + B->nnzb : &zero};
+    int nsrc = tc ? 7 : 5;
+    if (nbr > 0) {
+        e = cudaMemcpyAsync(h_ccnt.data(), ccol_cnt, sizeof(int64_t) * nbr, cudaMemcpyDeviceToHost, g_stream);
+        if ((st = cuda_check(e, "read counts"))) return st;
+    }
+    if ((st = read_words(src, nsrc))) return st;
+    const int64_t nprod = g_host[0], nnzbC = g_host[1], lenC = g_host[2];
+    const int64_t nfilt = g_host[3];
+    const int64_t mnk = g_host[4];
+    const int64_t packA_words = tc ? g_host[5] : 0, packB_words = tc ? g_host[6] : 0;
+    int64_t max_ccnt = 0;
+    for (int64_t v : h_ccnt) max_ccnt = std::max(max_ccnt, v);
+    if (nprod > INT32_MAX || nnzbC > INT32_MAX)
+        return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31-1 products or C blocks");
+    const int fill_smem = symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt);
+    if (fill_smem > 220 * 1024) return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
+    ev.mark(2);
+
+    // ---- a3: fill C's pattern and the product list
+    int32_t *c_col = nullptr, *c_rc = nullptr, *pa = nullptr, *pb = nullptr, *pc = nullptr;
+    int64_t *c_off = nullptr, *cptr = nullptr, *old_off = nullptr;
+    void *c_data = nullptr;
+    if ((st = sc.get(&c_col, nnzbC)) || (st = sc.get(&c_off, nnzbC)) || (st = sc.get(&c_rc, nnzbC)) ||
+        (st = sc.get(&cptr, (size_t)nnzbC + 1)) || (st = sc.get(&pa, nprod)) || (st = sc.get(&pb, nprod)) ||
+        (st = sc.get(&pc, nprod)))
+        return st;
+    if (use_old && (st = sc.get(&old_off, nnzbC))) return st;
+    if ((st = dalloc(&c_data, (size_t)lenC * esize(C->dtype)))) return st;
+    sc.ptrs.push_back(c_data);
+    FillOut fo{prod_ptr, crow_ptr, celem_ptr, c_col, c_off, c_rc, cptr, pa, pb, pc, old_off, (int32_t)max_ccnt};
+    e = launch_symbolic_fill(sa, bitmaps, fo, g_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cptr + nnzbC, prod_ptr + nbr, sizeof(int64_t), cudaMemcpyDeviceToDevice, g_stream);
+    if ((st = cuda_check(e, "symbolic fill"))) return st;
+    ev.mark(3);
+
+    // ---- a4: stacks by shape (m, n, k)
+    int32_t nshapes = 0;
+    std::vector<int32_t> h_shapes;
+    int64_t *stack_ptr = nullptr, *triples = nullptr;
+    if (opts.build_stacks && nprod > 0) {
+        std::vector<int32_t> sizes;
+        for (auto *v : {&A->h_row_bs, &A->h_col_bs, &B->h_col_bs}) sizes.insert(sizes.end(), v->begin(), v->end());
+        std::sort(sizes.begin(), sizes.end());
+        sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+        const int32_t ns = (int32_t)sizes.size();
+        const int64_t nsh = (int64_t)ns * ns * ns;
+        if (nsh > (1 << 24)) return set_error(BSM_ERR_UNSUPPORTED, "too many distinct block sizes for stacks");
+        std::vector<int32_t> sidx(kMaxBlockDim + 1, 0);
+        for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
+        int32_t *d_sidx, *iota, *order, *vals_alt;
+        uint32_t *keys, *keys_sorted, *keys_alt;
+        int64_t *rtmp, *counts;
+        if ((st = sc.get(&d_sidx, kMaxBlockDim + 1)) || (st = sc.get(&iota, nprod)) || (st = sc.get(&order, nprod)) ||
+            (st = sc.get(&vals_alt, nprod)) || (st = sc.get(&keys, nprod)) || (st = sc.get(&keys_sorted, nprod)) ||
+            (st = sc.get(&keys_alt, nprod)) || (st = sc.get(&rtmp, radix_tmp_elems(nprod))) ||
+            (st = sc.get(&counts, nsh)))
+            return st;
+        int bits = 1;
+        while ((1ll << bits) < nsh) ++bits;
+        e = cudaMemcpyAsync(d_sidx, sidx.data(), sizeof(int32_t) * sidx.size(), cudaMemcpyHostToDevice, g_stream);
+        if (e == cudaSuccess) e = launch_product_shape_ids(nprod, pa, pb, A->blk_rc, B->blk_rc, d_sidx, ns, keys, iota, g_stream);
+        if (e == cudaSuccess)
+            e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, nprod, bits, rtmp, g_stream);
+        if (e == cudaSuccess) e = launch_histogram_u32(nprod, keys, nsh, counts, g_stream);
+        std::vector<int64_t> h_counts((size_t)nsh);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_counts.data(), counts, sizeof(int64_t) * nsh, cudaMemcpyDeviceToHost, g_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+        if ((st = cuda_check(e, "stacks"))) return st;
+        std::vector<int64_t> h_ptr(1, 0);
+        for (int64_t id = 0; id < nsh; ++id) {
+            if (!h_counts[id]) continue;
+            const int32_t mi = (int32_t)(id / ((int64_t)ns * ns)), ni = (int32_t)((id / ns) % ns), ki = (int32_t)(id % ns);
+            h_shapes.push_back(sizes[mi]);
+            h_shapes.push_back(sizes[ni]);
+            h_shapes.push_back(sizes[ki]);
+            h_ptr.push_back(h_ptr.back() + h_counts[id]);
+        }
+        nshapes = (int32_t)(h_ptr.size() - 1);
+        if ((st = dalloc_t(&stack_ptr, h_ptr.size()))) return st;
+        sc.ptrs.push_back(stack_ptr);
+        if ((st = dalloc_t(&triples, (size_t)nprod * 3))) return st;
+        sc.ptrs.push_back(triples);
+        e = cudaMemcpyAsync(stack_ptr, h_ptr.data(), sizeof(int64_t) * h_ptr.size(), cudaMemcpyHostToDevice, g_stream);
+        if (e == cudaSuccess)
+            e = launch_stack_triples(nprod, order, pa, pb, pc, A->blk_off, B->blk_off, c_off, triples, g_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);  // h_ptr is pageable
+        if ((st = cuda_check(e, "stack triples"))) return st;
+    }
+    ev.mark(4);
+
+    // ---- a5/a6: numeric
+    if (tc) {
+        if ((st = pack_fill(sc, A, 0, 0, opts.prec, pkA, packA_words))) return st;
+        if ((st = pack_fill(sc, B, 1, 0, opts.prec, pkB, packB_words))) return st;
+    }
+    NumericArgs na{};
+    na.n_items = nnzbC;
+    na.seg_ptr = cptr;
+    na.px = pa;
+    na.py = pb;
+    na.out_data = c_data;
+    na.out_blk_off = c_off;
+    na.out_blk_rc = c_rc;
+    na.x_data = A->data; na.x_blk_off = A->blk_off; na.x_blk_rc = A->blk_rc; na.x_trans = 0;
+    na.y_data = B->data; na.y_blk_off = B->blk_off; na.y_blk_rc = B->blk_rc; na.y_trans = 0;
+    na.alpha = alpha;
+    na.beta = use_old ? beta : 0.0;
+    na.old_data = use_old ? C->data : nullptr;
+    na.old_off = old_off;
+    na.dtype = C->dtype;
+    na.prec = opts.prec;
+    na.flush_every = opts.flush_every;
+    na.x_pack = pkA.words; na.x_pack_off = pkA.off;
+    na.y_pack = pkB.words; na.y_pack_off = pkB.off;
+    if ((st = sc.get(&na.work_counter, 2))) return st;
+    ev.mark(5);
+    if ((st = cuda_check(launch_numeric(na, g_stream), "numeric"))) return st;
+    ev.mark(6);
+
+    // ---- swap C's pattern (old arrays are freed stream-ordered after the numeric kernel)
+    free_results(C);
+    free_pattern(C);
+    C->row_ptr = crow_ptr;
+    C->col_idx = c_col;
+    C->blk_off = c_off;
+    C->blk_rc = c_rc;
+    C->data = c_data;
+    C->own_data = true;
+    C->nnzb = nnzbC;
+    C->data_len = lenC;
+    C->cptr = cptr;
+    C->pa = pa; C->pb = pb; C->pc = pc;
+    C->nprod = nprod;
+    C->nfiltered = nfilt;
+    C->useful_flop = 2.0 * (double)mnk;
+    C->nshapes = nshapes;
+    C->h_shapes = h_shapes;
+    C->stack_ptr = stack_ptr;
+    C->triples = triples;
+    C->prod_A = A; C->prod_B = B;
+    C->prod_A_nnzb = A->nnzb; C->prod_B_nnzb = B->nnzb;
+    for (void *p : {(void *)crow_ptr, (void *)c_col, (void *)c_off, (void *)c_rc, c_data, (void *)cptr, (void *)pa,
+                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples})
+        sc.release(p);
+
+    // ---- optional post filter (drops C blocks with norm <= eps)
+    if (opts.post_filter && use_filter) {
+        const int64_t before = C->nnzb;
+        if ((st = norm_filter_compact(C, filter_eps))) return st;
+        if (C->nnzb != before) {
+            // the product list no longer indexes C's blocks
+            dfree(C->cptr); C->cptr = nullptr;
+            dfree(C->pa); C->pa = nullptr;
+            dfree(C->pb); C->pb = nullptr;
+            dfree(C->pc); C->pc = nullptr;
+            dfree(C->stack_ptr); C->stack_ptr = nullptr;
+            dfree(C->triples); C->triples = nullptr;
+            C->nshapes = 0;
+            C->h_shapes.clear();
+            C->prod_A = C->prod_B = nullptr;
+        }
+    }
+    ev.mark(7);
+    if (ev.on) {
+        cudaEventSynchronize(ev.ev[7]);
+        float ms;
+        const int pairs[BSM_T_COUNT][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {5, 6}, {6, 7}, {0, 7}};
+        for (int q = 0; q < BSM_T_COUNT; ++q) {
+            cudaEventElapsedTime(&ms, ev.ev[pairs[q][0]], ev.ev[pairs[q][1]]);
+            C->timings[q] = ms;
+        }
+        C->timings_valid = true;
+    }
+    return BSM_OK;
+}
+
+// --------------------------------------------------------------------------
+// adjoint
+// --------------------------------------------------------------------------
+static bsm_status group_products(Scratch &sc, int64_t nprod, const int32_t *key_src, int64_t nkeys,
+                                 int32_t **order_out, int64_t **seg_out) {
+    bsm_status st;
+    int32_t *iota, *order, *vals_alt;
+    uint32_t *keys, *keys_sorted, *keys_alt;
+    int64_t *rtmp, *counts, *seg, *stmp;
+    if ((st = sc.get(&iota, nprod)) || (st = sc.get(&order, nprod)) || (st = sc.get(&vals_alt, nprod)) ||
+        (st = sc.get(&keys, nprod)) || (st = sc.get(&keys_sorted, nprod)) || (st = sc.get(&keys_alt, nprod)) ||
+        (st = sc.get(&rtmp, radix_tmp_elems(nprod))) || (st = sc.get(&counts, nkeys)) ||
+        (st = sc.get(&seg, (size_t)nkeys + 1)) || (st = sc.get(&stmp, scan_tmp_elems(nkeys))))
+        return st;
+    int bits = 1;
+    while ((1ll << bits) < nkeys) ++bits;
+    cudaError_t e = launch_iota_keys(nprod, key_src, keys, iota, g_stream);
+    if (e == cudaSuccess)
+        e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, nprod, bits, rtmp, g_stream);
+    if (e == cudaSuccess) e = launch_histogram_u32(nprod, keys, nkeys, counts, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(counts, seg, nkeys, stmp, g_stream);
+    *order_out = order;
+    *seg_out = seg;
+    return cuda_check(e, "group products");
+}
+
+bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm_t A, bsm_t B, void *dA_data,
+                                 void *dB_data, const bsm_opts *opts_in) {
+    if (!C || !A || !B) return set_error(BSM_ERR_ARG, "NULL matrix");
+    if (!dA_data && !dB_data) return BSM_OK;
+    if (!dC_data && C->data_len) return set_error(BSM_ERR_ARG, "dC_data is NULL");
+    bsm_opts opts;
+    bsm_status st = check_opts(opts_in, &opts);
+    if (st) return st;
+    if (C->prod_A != A || C->prod_B != B || C->prod_A_nnzb != A->nnzb || C->prod_B_nnzb != B->nnzb || !C->cptr)
+        return set_error(BSM_ERR_ARG, "C does not hold the product list of a multiply of these A and B");
+    if ((st = ensure_globals())) return st;
+    Scratch sc;
+    const bool tc = is_tc(opts.prec);
+    // dC as a matrix with C's pattern
+    bsm_mat dC;
+    dC.nbr = C->nbr; dC.nbc = C->nbc; dC.dtype = C->dtype; dC.nnzb = C->nnzb; dC.data_len = C->data_len;
+    dC.row_bs = C->row_bs; dC.col_bs = C->col_bs; dC.row_ptr = C->row_ptr; dC.col_idx = C->col_idx;
+    dC.blk_off = C->blk_off; dC.blk_rc = C->blk_rc; dC.data = const_cast<void *>(dC_data);
+    const int64_t nprod = C->nprod;
+    for (int side = 0; side < 2; ++side) {
+        void *out = side == 0 ? dA_data : dB_data;
+        if (!out) continue;
+        bsm_mat *OUT = side == 0 ? A : B;
+        if (OUT->nnzb == 0) continue;
+        int32_t *order = nullptr;
+        int64_t *seg = nullptr;
+        int32_t *px = nullptr, *py = nullptr;
+        if (nprod > 0) {
+            if ((st = group_products(sc, nprod, side == 0 ? C->pa : C->pb, OUT->nnzb, &order, &seg))) return st;
+            if ((st = sc.get(&px, nprod)) || (st = sc.get(&py, nprod))) return st;
+            cudaError_t e;
+            if (side == 0) {  // dA = dC . B^T : X = dC (by C block), Y = B^T
+                e = launch_gather_i32(nprod, order, C->pc, px, g_stream);
+                if (e == cudaSuccess) e = launch_gather_i32(nprod, order, C->pb, py, g_stream);
+            } else {          // dB = A^T . dC : X = A^T, Y = dC
+                e = launch_gather_i32(nprod, order, C->pa, px, g_stream);
+                if (e == cudaSuccess) e = launch_gather_i32(nprod, order, C->pc, py, g_stream);
+            }
+            if ((st = cuda_check(e, "gather products"))) return st;
+        } else {
+            if ((st = sc.get(&seg, (size_t)OUT->nnzb + 1))) return st;
+            if ((st = cuda_check(cudaMemsetAsync(seg, 0, sizeof(int64_t) * (OUT->nnzb + 1), g_stream), "memset")))
+                return st;
+        }
+        const bsm_mat *X = side == 0 ? &dC : A;
+        const bsm_mat *Y = side == 0 ? B : &dC;
+        const int xt = side == 0 ? 0 : 1, yt = side == 0 ? 1 : 0;
+        Packed pkX, pkY;
+        if (tc && nprod > 0) {
+            if ((st = pack_prepare(sc, X, 0, xt, opts.prec, pkX))) return st;
+            if ((st = pack_prepare(sc, Y, 1, yt, opts.prec, pkY))) return st;
+            const int64_t *src[2] = {pkX.off + X->nnzb, pkY.off + Y->nnzb};
+            if ((st = read_words(src, 2))) return st;
+            const int64_t wx = g_host[0], wy = g_host[1];
+            if ((st = pack_fill(sc, X, 0, xt, opts.prec, pkX, wx))) return st;
+            if ((st = pack_fill(sc, Y, 1, yt, opts.prec, pkY, wy))) return st;
+        }
+        NumericArgs na{};
+        na.n_items = OUT->nnzb;
+        na.seg_ptr = seg;
+        na.px = px;
+        na.py = py;
+        na.out_data = out;
+        na.out_blk_off = OUT->blk_off;
+        na.out_blk_rc = OUT->blk_rc;
+        na.x_data = X->data; na.x_blk_off = X->blk_off; na.x_blk_rc = X->blk_rc; na.x_trans = xt;
+        na.y_data = Y->data; na.y_blk_off = Y->blk_off; na.y_blk_rc = Y->blk_rc; na.y_trans = yt;
+        na.alpha = alpha;
+        na.beta = 0.0;
+        na.dtype = C->dtype;
+        na.prec = opts.prec;
+        na.flush_every = opts.flush_every;
+        na.x_pack = pkX.words; na.x_pack_off = pkX.off;
+        na.y_pack = pkY.words; na.y_pack_off = pkY.off;
+        if ((st = sc.get(&na.work_counter, 2))) return st;
+        if ((st = cuda_check(launch_numeric(na, g_stream), "adjoint numeric"))) return st;
+    }
+    return BSM_OK;
+}
+
+bsm_status bsm_get_counts(bsm_t C, int64_t *products, int64_t *filtered, double *useful_flop) {
+    if (!C) return set_error(BSM_ERR_ARG, "C is NULL");
+    if (products) *products = C->nprod;
+    if (filtered) *filtered = C->nfiltered;
+    if (useful_flop) *useful_flop = C->useful_flop;
+    return BSM_OK;
+}
+
+bsm_status bsm_get_timings(bsm_t C, double *ms) {
+    if (!C || !ms) return set_error(BSM_ERR_ARG, "NULL argument");
+    if (!C->timings_valid) return set_error(BSM_ERR_ARG, "no timings recorded (profiling off?)");
+    for (int q = 0; q < BSM_T_COUNT; ++q) ms[q] = C->timings[q];
+    return BSM_OK;
+}
+
+bsm_status bsm_get_products(bsm_t C, int64_t *nprod, int32_t *a_idx, int32_t *b_idx, int32_t *c_idx) {
+    if (!C || !nprod) return set_error(BSM_ERR_ARG, "NULL argument");
+    *nprod = C->pa ? C->nprod : 0;
+    if (!a_idx && !b_idx && !c_idx) return BSM_OK;
+    if (!C->pa) return set_error(BSM_ERR_ARG, "C holds no product list");
+    cudaError_t e = cudaSuccess;
+    const size_t bytes = sizeof(int32_t) * (size_t)C->nprod;
+    if (a_idx && bytes) e = cudaMemcpyAsync(a_idx, C->pa, bytes, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess && b_idx && bytes) e = cudaMemcpyAsync(b_idx, C->pb, bytes, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess && c_idx && bytes) e = cudaMemcpyAsync(c_idx, C->pc, bytes, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    return cuda_check(e, "copy products");
+}
+
+bsm_status bsm_get_stacks(bsm_t C, int32_t *nshapes, int64_t *nprod, int32_t *shapes, int64_t *stack_ptr,
+                          int64_t *triples) {
+    if (!C || !nshapes || !nprod) return set_error(BSM_ERR_ARG, "NULL argument");
+    *nshapes = C->nshapes;
+    *nprod = C->triples ? C->nprod : 0;
+    if (!shapes && !stack_ptr && !triples) return BSM_OK;
+    cudaError_t e = cudaSuccess;
+    if (shapes && C->nshapes)
+        e = cudaMemcpyAsync(shapes, C->h_shapes.data(), sizeof(int32_t) * 3 * C->nshapes, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess && stack_ptr && C->stack_ptr)
+        e = cudaMemcpyAsync(stack_ptr, C->stack_ptr, sizeof(int64_t) * (C->nshapes + 1), cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess && triples && C->triples && C->nprod)
+        e = cudaMemcpyAsync(triples, C->triples, sizeof(int64_t) * 3 * C->nprod, cudaMemcpyDefault, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    return cuda_check(e, "copy stacks");
+}
+
+// --------------------------------------------------------------------------
+// add
+// --------------------------------------------------------------------------
+bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps) {
+    if (!X || !Y || !Z) return set_error(BSM_ERR_ARG, "NULL matrix");
+    if (Z == X || Z == Y) return set_error(BSM_ERR_ARG, "Z must differ from X and Y");
+    if (X->dtype != Y->dtype || X->dtype != Z->dtype) return set_error(BSM_ERR_ARG, "X, Y and Z must share a dtype");
+    if (X->nbr != Y->nbr || X->nbc != Y->nbc || X->nbr != Z->nbr || X->nbc != Z->nbc ||
+        !same_vec(X->h_row_bs, Y->h_row_bs) || !same_vec(X->h_col_bs, Y->h_col_bs) ||
+        !same_vec(X->h_row_bs, Z->h_row_bs) || !same_vec(X->h_col_bs, Z->h_col_bs))
+        return set_error(BSM_ERR_BLOCKING, "X, Y and Z must share one blocking");
+    if (!std::isfinite(a) || !std::isfinite(b) || std::isnan(filter_eps))
+        return set_error(BSM_ERR_ARG, "a, b and eps must be finite");
+    bsm_status st = ensure_globals();
+    if (st) return st;
+    Scratch sc;
+    const int32_t nbr = X->nbr;
+    int64_t *ccnt, *celem, *zrow, *zelem, *stmp;
+    if ((st = sc.get(&ccnt, nbr)) || (st = sc.get(&celem, nbr)) || (st = sc.get(&zrow, (size_t)nbr + 1)) ||
+        (st = sc.get(&zelem, (size_t)nbr + 1)) || (st = sc.get(&stmp, scan_tmp_elems(nbr))))
+        return st;
+    cudaError_t e = launch_add_count(X, Y, ccnt, celem, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(ccnt, zrow, nbr, stmp, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(celem, zelem, nbr, stmp, g_stream);
+    if ((st = cuda_check(e, "add count"))) return st;
+    const int64_t *src[2] = {zrow + nbr, zelem + nbr};
+    if ((st = read_words(src, 2))) return st;
+    const int64_t nnz = g_host[0], len = g_host[1];
+    int32_t *zc, *zrc;
+    int64_t *zo, *xs, *ys;
+    void *zd;
+    if ((st = sc.get(&zc, nnz)) || (st = sc.get(&zo, nnz)) || (st = sc.get(&zrc, nnz)) || (st = sc.get(&xs, nnz)) ||
+        (st = sc.get(&ys, nnz)))
+        return st;
+    if ((st = dalloc(&zd, (size_t)len * esize(X->dtype)))) return st;
+    sc.ptrs.push_back(zd);
+    AddFill f{zrow, zelem, zc, zo, zrc, xs, ys};
+    e = launch_add_fill(X, Y, f, g_stream);
+    if (e == cudaSuccess) e = launch_add_values(nnz, zo, zrc, xs, ys, a, X->data, b, Y->data, zd, X->dtype, g_stream);
+    if ((st = cuda_check(e, "add fill"))) return st;
+    free_results(Z);
+    free_pattern(Z);
+    Z->row_ptr = zrow; Z->col_idx = zc; Z->blk_off = zo; Z->blk_rc = zrc; Z->data = zd; Z->own_data = true;
+    Z->nnzb = nnz; Z->data_len = len;
+    for (void *p : {(void *)zrow, (void *)zc, (void *)zo, (void *)zrc, zd}) sc.release(p);
+    if (filter_eps > 0.0) {
+        if ((st = norm_filter_compact(Z, filter_eps))) return st;
+    }
+    return BSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+// Internal declarations of libbsm (not part of the C ABI).
+//
+// Device layout of a block-CSR matrix (the blocked CSR format of DBCSR,
+// Bethune et al. 2017 §2):
+//   row_bs[nbr], col_bs[nbc]      int32 block sizes
+//   row_ptr[nbr+1]                int64
+//   col_idx[nnzb]                 int32, ascending inside a row
+//   blk_off[nnzb]                 int64 element offset of each block
+//   blk_rc[nnzb]                  int32 packed (rows << 16) | cols of each block
+//   data[data_len]                FP64 or FP32, row-major inside a block
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bsm.h"
+
+namespace bsm {
+
+constexpr int kMaxBlockDim = 256;
+
+__host__ __device__ inline int rc_rows(int32_t rc) { return (int)((uint32_t)rc >> 16); }
+__host__ __device__ inline int rc_cols(int32_t rc) { return (int)(rc & 0xffff); }
+
+// Status bits written by kernels into a per-call device word.
+enum : int32_t { DEV_OK = 0, DEV_ERR_CAPACITY = 1, DEV_ERR_RANGE = 2 };
+
+// One stored operand view for the numeric kernels: element (r, t) of the
+// logical R x T block is data[off + (trans ? t*R + r : r*T + t)], where the
+// stored block is R x T (trans = 0) or T x R (trans = 1).
+template <typename T>
+struct OperandView {
+    const T *data;
+    const int64_t *blk_off;
+    const int32_t *blk_rc;
+    int trans;
+};
+
+}  // namespace bsm
+
+// The handle behind bsm_t.
+struct bsm_mat {
+    int32_t nbr = 0, nbc = 0;
+    int32_t dtype = BSM_FP64;
+    int64_t nnzb = 0, data_len = 0;
+    std::vector<int32_t> h_row_bs, h_col_bs;  // host copies of the blocking
+    int32_t *row_bs = nullptr, *col_bs = nullptr;
+    int64_t *row_ptr = nullptr;
+    int32_t *col_idx = nullptr;
+    int64_t *blk_off = nullptr;
+    int32_t *blk_rc = nullptr;
+    void *data = nullptr;
+    bool own_data = false;
+    double *norms = nullptr;
+    bool norms_valid = false;
+    int32_t max_bs_row = 0, max_bs_col = 0;
+
+    // results of the last multiply that wrote this matrix
+    int64_t nprod = 0, nfiltered = 0;
+    double useful_flop = 0.0;
+    int64_t *cptr = nullptr;  // [nnzb+1] product segment of every block
+    int32_t *pa = nullptr, *pb = nullptr, *pc = nullptr;  // [nprod]
+    int32_t nshapes = 0;
+    std::vector<int32_t> h_shapes;  // 3*nshapes
+    int64_t *stack_ptr = nullptr;   // [nshapes+1] device
+    int64_t *triples = nullptr;     // [3*nprod] device
+    bsm_t prod_A = nullptr, prod_B = nullptr;  // operands of that multiply
+    int64_t prod_A_nnzb = -1, prod_B_nnzb = -1;
+    double timings[BSM_T_COUNT] = {0};
+    bool timings_valid = false;
+};
+
+namespace bsm {
+
+// ---------------------------------------------------------------- host glue
+cudaStream_t stream();
+bool profiling();
+bsm_status set_error(bsm_status st, const std::string &msg);
+bsm_status cuda_check(cudaError_t e, const char *what);
+bsm_status dalloc(void **p, size_t bytes);
+void dfree(void *p);
+template <typename T>
+inline bsm_status dalloc_t(T **p, size_t n) {
+    return dalloc(reinterpret_cast<void **>(p), n * sizeof(T) + (n == 0 ? 16 : 0));
+}
+
+// ---------------------------------------------------------------- launchers
+// (all asynchronous on `s`; they return cudaGetLastError())
+cudaError_t launch_blk_rc(const bsm_mat *X, int32_t *out_rc, cudaStream_t s);
+cudaError_t launch_block_norms(const bsm_mat *X, double *out, cudaStream_t s);
+
+// Exclusive scan of n int64 values into out[0..n] (out[n] = total).
+// `tmp` needs scan_tmp_elems(n) int64.
+size_t scan_tmp_elems(int64_t n);
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t s);
+
+struct SymbolicArgs {
+    int32_t nbr, nbk, nbc;
+    const int32_t *a_row_bs, *a_col_bs;  // m sizes, k sizes
+    const int64_t *a_row_ptr;
+    const int32_t *a_col_idx;
+    const double *a_norm;
+    const int64_t *b_row_ptr;
+    const int32_t *b_col_idx;
+    const int32_t *b_col_bs;             // n sizes
+    const double *b_norm;
+    const int64_t *o_row_ptr;            // old C (beta != 0) or nullptr
+    const int32_t *o_col_idx;
+    const int64_t *o_blk_off;
+    double eps;
+    int use_filter;
+    int32_t nwords;                      // ceil(nbc / 32)
+};
+
+// Per block row: kept products, distinct C columns, C elements; bitmaps of
+// the C columns (nbr * nwords words); totals[0] += filtered, totals[1] += sum m*n*k.
+cudaError_t launch_symbolic_count(const SymbolicArgs &a, int64_t *prod_cnt, int64_t *ccol_cnt,
+                                  int64_t *celem_cnt, uint32_t *bitmaps,
+                                  unsigned long long *totals, cudaStream_t s);
+
+struct FillOut {
+    const int64_t *prod_ptr, *crow_ptr, *celem_ptr;  // scans, [nbr+1]
+    int32_t *c_col_idx;
+    int64_t *c_blk_off;
+    int32_t *c_blk_rc;
+    int64_t *cptr;       // [nnzbC+1]
+    int32_t *pa, *pb, *pc;
+    int64_t *old_off;    // [nnzbC] or nullptr
+    int32_t max_ccnt;
+};
+cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
+                                 cudaStream_t s);
+int symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt);
+
+// Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits.
+// Buffers: keys/vals in and out may not alias; `tmp` needs
+// radix_tmp_elems(n) int64.  Result lands in (keys_out, vals_out).
+size_t radix_tmp_elems(int64_t n);
+cudaError_t launch_radix_sort_pairs(const uint32_t *keys_in, const int32_t *vals_in, uint32_t *keys_alt,
+                                    int32_t *vals_alt, uint32_t *keys_out, int32_t *vals_out,
+                                    int64_t n, int key_bits, int64_t *tmp, cudaStream_t s);
+
+// shape id of every product (for stacks): (mi * ns + ni) * ns + ki
+cudaError_t launch_product_shape_ids(int64_t nprod, const int32_t *pa, const int32_t *pb,
+                                     const int32_t *a_blk_rc, const int32_t *b_blk_rc,
+                                     const int32_t *size_index /*[kMaxBlockDim+1]*/, int32_t ns,
+                                     uint32_t *keys, int32_t *iota, cudaStream_t s);
+cudaError_t launch_stack_triples(int64_t nprod, const int32_t *order, const int32_t *pa,
+                                 const int32_t *pb, const int32_t *pc, const int64_t *a_off,
+                                 const int64_t *b_off, const int64_t *c_off, int64_t *triples,
+                                 cudaStream_t s);
+cudaError_t launch_histogram_u32(int64_t n, const uint32_t *keys, int64_t nbins, int64_t *counts,
+                                 cudaStream_t s);
+cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *src, int32_t *dst,
+                              cudaStream_t s);
+cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota,
+                             cudaStream_t s);
+
+// ---------------------------------------------------------------- numeric
+struct NumericArgs {
+    int64_t n_items;
+    const int64_t *seg_ptr;     // [n_items+1] product range of each output block
+    const int32_t *px, *py;     // operand block index of every product
+    // output blocks: item q writes block q of the output matrix
+    void *out_data;
+    const int64_t *out_blk_off;
+    const int32_t *out_blk_rc;
+    // operands
+    const void *x_data; const int64_t *x_blk_off; const int32_t *x_blk_rc; int x_trans;
+    const void *y_data; const int64_t *y_blk_off; const int32_t *y_blk_rc; int y_trans;
+    double alpha, beta;
+    const void *old_data;       // beta != 0: old values at old_off[q] (or -1)
+    const int64_t *old_off;
+    int32_t dtype;
+    int32_t prec;
+    int32_t flush_every;
+    // pre-split operand planes (tensor-core paths)
+    const void *x_pack; const int64_t *x_pack_off;
+    const void *y_pack; const int64_t *y_pack_off;
+    int32_t max_out_rows, max_out_cols;
+    unsigned long long *work_counter;  // 8 bytes of device memory, zeroed by the launcher
+};
+cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s);
+
+// Tensor-core paths: packed fragment planes of a matrix in role X (A
+// fragments, logical R x T) or Y (B fragments, logical T x S).
+struct PackInfo {
+    int64_t total_words;        // 32-bit words
+};
+cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec, int64_t *pack_words,
+                              cudaStream_t s);
+cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
+                        void *pack, cudaStream_t s);
+
+// ---------------------------------------------------------------- add
+cudaError_t launch_add_count(const bsm_mat *X, const bsm_mat *Y, int64_t *ccnt, int64_t *celem,
+                             cudaStream_t s);
+struct AddFill {
+    const int64_t *zrow_ptr, *zelem_ptr;
+    int32_t *z_col_idx;
+    int64_t *z_blk_off;
+    int32_t *z_blk_rc;
+    int64_t *x_src, *y_src;  // [nnzbZ] source block offsets or -1
+};
+cudaError_t launch_add_fill(const bsm_mat *X, const bsm_mat *Y, const AddFill &f, cudaStream_t s);
+cudaError_t launch_add_values(int64_t nnzb, const int64_t *z_blk_off, const int32_t *z_blk_rc,
+                              const int64_t *x_src, const int64_t *y_src, double a, const void *x,
+                              double b, const void *y, void *z, int32_t dtype, cudaStream_t s);
+
+// Post filter: keep flag per block (norm > eps), then compaction.
+cudaError_t launch_keep_flags(int64_t nnzb, const double *norms, double eps, int64_t *keep,
+                              cudaStream_t s);
+cudaError_t launch_row_keep_counts(int32_t nbr, const int64_t *row_ptr, const int64_t *keep,
+                                   const int32_t *blk_rc, int64_t *row_cnt, int64_t *row_elem,
+                                   cudaStream_t s);
+struct CompactArgs {
+    int32_t nbr;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const int64_t *blk_off;
+    const int32_t *blk_rc;
+    const int64_t *keep_scan;   // exclusive scan of keep flags [nnzb+1]
+    const int64_t *nrow_ptr;    // new row pointers
+    const int64_t *nelem_ptr;   // new per-row element starts
+    const void *data;
+    int32_t dtype;
+    int32_t *n_col_idx;
+    int64_t *n_blk_off;
+    int32_t *n_blk_rc;
+    void *n_data;
+};
+cudaError_t launch_compact(const CompactArgs &c, cudaStream_t s);
+
+}  // namespace bsm

@@ -1,0 +1,563 @@
+// Numeric phase: every output block accumulates its list of small dense
+// block products (the "batches" of DBCSR, Bethune et al. 2017 §2) in a fixed
+// order, owned by exactly one warp -- the GPU analogue of the paper's static
+// assignment of an A row-block to one thread, so no atomics touch C.
+//
+// One generic contraction serves the forward product and both adjoints:
+//   out_q = alpha * sum_{p in seg(q)} X_p . Y_p  (+ beta * old_q)
+// with X_p a logical R x T block and Y_p a logical T x S block, either stored
+// as is or transposed:
+//   forward  C_ij  = sum_k A_ik . B_kj          X = A,      Y = B
+//   adjoint  dA_ik = sum_j dC_ij . B_kj^T       X = dC,     Y = B^T
+//   adjoint  dB_kj = sum_i A_ik^T . dC_ij       X = A^T,    Y = dC
+//
+// Two arithmetic paths:
+//   * CUDA cores: FP64 FMA for FP64 data (FP32 FMA with an FP64 running sum
+//     for FP32 data); one lane owns a fixed set of output elements.
+//   * Tensor cores (mma.sync m16n8k8 TF32 / m16n8k16 BF16): operands were
+//     split beforehand into 2 or 3 narrow pieces (hi, lo[, lo2]) and packed
+//     in mma fragment order; the cross products of the pieces accumulate in
+//     FP32 inside the tensor core and are added into an FP64 accumulator
+//     every `flush_every` block products.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "bsm_internal.cuh"
+
+namespace bsm {
+
+namespace {
+
+constexpr int kWarpsPerCta = 4;
+constexpr int kThreadsNum = kWarpsPerCta * 32;
+
+// =====================================================================
+// CUDA-core path
+// =====================================================================
+template <typename T, int Q>
+__device__ __forceinline__ void cc_item(const NumericArgs &a, int64_t q, int lane) {
+    const T *__restrict__ X = static_cast<const T *>(a.x_data);
+    const T *__restrict__ Y = static_cast<const T *>(a.y_data);
+    T *__restrict__ O = static_cast<T *>(a.out_data);
+    const int32_t orc = a.out_blk_rc[q];
+    const int R = rc_rows(orc), S = rc_cols(orc);
+    const int RS = R * S;
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+    const T *OLD = static_cast<const T *>(a.old_data);
+    const int F = a.flush_every > 0 ? a.flush_every : 1;
+
+    for (int e0 = 0; e0 < RS; e0 += 32 * Q) {
+        int rr[Q], ss[Q];
+        double acc[Q];
+        T acc_n[Q];
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+            const int e = e0 + lane + 32 * u;
+            const bool v = e < RS;
+            rr[u] = v ? e / S : 0;
+            ss[u] = v ? e % S : 0;
+            acc[u] = 0.0;
+            acc_n[u] = T(0);
+        }
+        int since = 0;
+        for (int64_t p = p0; p < p1; ++p) {
+            const int32_t ix = a.px[p], iy = a.py[p];
+            const T *xb = X + a.x_blk_off[ix];
+            const T *yb = Y + a.y_blk_off[iy];
+            const int32_t xrc = a.x_blk_rc[ix];
+            const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+            const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+            const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+            int xo[Q], yo[Q];
+#pragma unroll
+            for (int u = 0; u < Q; ++u) {
+                xo[u] = rr[u] * xs_r;
+                yo[u] = ss[u] * ys_s;
+            }
+            for (int t = 0; t < Tn; ++t) {
+#pragma unroll
+                for (int u = 0; u < Q; ++u) {
+                    const T xv = __ldg(xb + xo[u] + t * xs_t);
+                    const T yv = __ldg(yb + t * ys_t + yo[u]);
+                    acc_n[u] = fma(xv, yv, acc_n[u]);
+                }
+            }
+            if constexpr (sizeof(T) == 4) {
+                if (++since == F) {
+                    since = 0;
+#pragma unroll
+                    for (int u = 0; u < Q; ++u) {
+                        acc[u] += (double)acc_n[u];
+                        acc_n[u] = T(0);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+            const int e = e0 + lane + 32 * u;
+            if (e < RS) {
+                double v = (sizeof(T) == 8) ? (double)acc_n[u] : acc[u] + (double)acc_n[u];
+                v = a.alpha * v;
+                if (old >= 0) v = fma(a.beta, (double)OLD[old + e], v);
+                O[out_off + e] = (T)v;
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void cc_dispatch(const NumericArgs &a, int64_t q, int lane) {
+    const int32_t orc = a.out_blk_rc[q];
+    const int RS = rc_rows(orc) * rc_cols(orc);
+    const int need = (RS + 31) >> 5;
+    if (need <= 1) cc_item<T, 1>(a, q, lane);
+    else if (need <= 2) cc_item<T, 2>(a, q, lane);
+    else if (need <= 3) cc_item<T, 3>(a, q, lane);
+    else if (need <= 4) cc_item<T, 4>(a, q, lane);
+    else if (need <= 6) cc_item<T, 6>(a, q, lane);
+    else if (need <= 8) cc_item<T, 8>(a, q, lane);
+    else if (need <= 10) cc_item<T, 10>(a, q, lane);
+    else if (need <= 12) cc_item<T, 12>(a, q, lane);
+    else if (need <= 14) cc_item<T, 14>(a, q, lane);
+    else if (need <= 17) cc_item<T, 17>(a, q, lane);
+    else if (need <= 20) cc_item<T, 20>(a, q, lane);
+    else cc_item<T, 24>(a, q, lane);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long *ctr = a.work_counter;
+    while (true) {
+        int64_t q = 0;
+        if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= a.n_items) break;
+        cc_dispatch<T>(a, q, lane);
+    }
+}
+
+// =====================================================================
+// Tensor-core split path
+// =====================================================================
+// Packed fragment planes.  For a logical R x T operand in role X (mma "A"
+// operand) the tiles are (kt, mt) with MT = ceil(R/16), kt over K steps;
+// for a logical T x S operand in role Y ("B" operand) tiles are (kt, nt)
+// with NT = ceil(S/8).  Words per lane per tile:
+//   prec      K step   X words   Y words
+//   TF32x3       8        8         4      (hi[4] lo[4] | hi[2] lo[2])
+//   BF16x3      16        8         4      (hi[4] lo[4] | hi[2] lo[2])
+//   BF16x6      16       12         6      (p0[4] p1[4] p2[4] | p0[2] p1[2] p2[2])
+template <int PREC> struct PrecTraits;
+template <> struct PrecTraits<BSM_P_TF32x3> { static constexpr int K = 8, XW = 8, YW = 4, NP = 2; };
+template <> struct PrecTraits<BSM_P_BF16x3> { static constexpr int K = 16, XW = 8, YW = 4, NP = 2; };
+template <> struct PrecTraits<BSM_P_BF16x6> { static constexpr int K = 16, XW = 12, YW = 6, NP = 3; };
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma_piece(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    if constexpr (PREC == BSM_P_TF32x3) mma_tf32(d, a, b);
+    else mma_bf16(d, a, b);
+}
+
+template <int PREC>
+__device__ __forceinline__ void load_x(const uint32_t *p, uint32_t (&f)[PrecTraits<PREC>::NP][4]) {
+    const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(p));
+    const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+    f[0][0] = v0.x; f[0][1] = v0.y; f[0][2] = v0.z; f[0][3] = v0.w;
+    f[1][0] = v1.x; f[1][1] = v1.y; f[1][2] = v1.z; f[1][3] = v1.w;
+    if constexpr (PrecTraits<PREC>::NP == 3) {
+        const uint4 v2 = __ldg(reinterpret_cast<const uint4 *>(p) + 2);
+        f[2][0] = v2.x; f[2][1] = v2.y; f[2][2] = v2.z; f[2][3] = v2.w;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void load_y(const uint32_t *p, uint32_t (&f)[PrecTraits<PREC>::NP][2]) {
+    if constexpr (PrecTraits<PREC>::NP == 2) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        f[0][0] = v.x; f[0][1] = v.y; f[1][0] = v.z; f[1][1] = v.w;
+    } else {
+        const uint2 v0 = __ldg(reinterpret_cast<const uint2 *>(p));
+        const uint2 v1 = __ldg(reinterpret_cast<const uint2 *>(p) + 1);
+        const uint2 v2 = __ldg(reinterpret_cast<const uint2 *>(p) + 2);
+        f[0][0] = v0.x; f[0][1] = v0.y; f[1][0] = v1.x; f[1][1] = v1.y;
+        f[2][0] = v2.x; f[2][1] = v2.y;
+    }
+}
+
+// One pass over a super tile of MTC x NTC (at most 2 x 3) fragment tiles
+// starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
+template <int PREC, int MTC, int NTC>
+__device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0) {
+    using PT = PrecTraits<PREC>;
+    const int32_t orc = a.out_blk_rc[q];
+    const int R = rc_rows(orc), S = rc_cols(orc);
+    const int MT = (R + 15) >> 4, NT = (S + 7) >> 3;
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const uint32_t *XP = static_cast<const uint32_t *>(a.x_pack);
+    const uint32_t *YP = static_cast<const uint32_t *>(a.y_pack);
+    const int F = a.flush_every > 0 ? a.flush_every : 1;
+
+    float acc[MTC][NTC][4];
+    double acc64[MTC][NTC][4];
+#pragma unroll
+    for (int i = 0; i < MTC; ++i)
+#pragma unroll
+        for (int j = 0; j < NTC; ++j)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                acc[i][j][v] = 0.f;
+                acc64[i][j][v] = 0.0;
+            }
+    int since = 0;
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t ix = a.px[p], iy = a.py[p];
+        const int32_t xrc = a.x_blk_rc[ix];
+        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+        const int KT = (Tn + PT::K - 1) / PT::K;
+        const uint32_t *xp = XP + a.x_pack_off[ix] + lane * PT::XW;
+        const uint32_t *yp = YP + a.y_pack_off[iy] + lane * PT::YW;
+        for (int kt = 0; kt < KT; ++kt) {
+            uint32_t fa[MTC][PT::NP][4];
+#pragma unroll
+            for (int i = 0; i < MTC; ++i)
+                if (mt0 + i < MT) load_x<PREC>(xp + (int64_t)(kt * MT + mt0 + i) * 32 * PT::XW, fa[i]);
+#pragma unroll
+            for (int j = 0; j < NTC; ++j) {
+                if (nt0 + j >= NT) continue;
+                uint32_t fb[PT::NP][2];
+                load_y<PREC>(yp + (int64_t)(kt * NT + nt0 + j) * 32 * PT::YW, fb);
+#pragma unroll
+                for (int i = 0; i < MTC; ++i) {
+                    if (mt0 + i >= MT) continue;
+                    if constexpr (PT::NP == 2) {
+                        mma_piece<PREC>(acc[i][j], fa[i][1], fb[0]);
+                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[1]);
+                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[0]);
+                    } else {
+                        mma_piece<PREC>(acc[i][j], fa[i][2], fb[0]);
+                        mma_piece<PREC>(acc[i][j], fa[i][1], fb[1]);
+                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[2]);
+                        mma_piece<PREC>(acc[i][j], fa[i][1], fb[0]);
+                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[1]);
+                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[0]);
+                    }
+                }
+            }
+        }
+        if (++since == F) {
+            since = 0;
+#pragma unroll
+            for (int i = 0; i < MTC; ++i)
+#pragma unroll
+                for (int j = 0; j < NTC; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        acc64[i][j][v] += (double)acc[i][j][v];
+                        acc[i][j][v] = 0.f;
+                    }
+        }
+    }
+    // epilogue: fragment element v of tile (i, j) sits at
+    // row (mt0+i)*16 + g + 8*(v>=2), column (nt0+j)*8 + 2*t4 + (v&1)
+    const int g = lane >> 2, t4 = lane & 3;
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+#pragma unroll
+    for (int i = 0; i < MTC; ++i)
+#pragma unroll
+        for (int j = 0; j < NTC; ++j)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int r = (mt0 + i) * 16 + g + ((v >> 1) << 3);
+                const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
+                if (r < R && c < S) {
+                    double val = a.alpha * (acc64[i][j][v] + (double)acc[i][j][v]);
+                    const int64_t e = (int64_t)r * S + c;
+                    if (a.dtype == BSM_FP64) {
+                        if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
+                        static_cast<double *>(a.out_data)[out_off + e] = val;
+                    } else {
+                        if (old >= 0) val = fma(a.beta, (double)static_cast<const float *>(a.old_data)[old + e], val);
+                        static_cast<float *>(a.out_data)[out_off + e] = (float)val;
+                    }
+                }
+            }
+}
+
+template <int PREC>
+__device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lane) {
+    const int32_t orc = a.out_blk_rc[q];
+    const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
+    for (int mt0 = 0; mt0 < MT; mt0 += 2) {
+        const int mtc = min(2, MT - mt0);
+        for (int nt0 = 0; nt0 < NT; nt0 += 3) {
+            const int ntc = min(3, NT - nt0);
+            if (mtc == 1) {
+                switch (ntc) {
+                    case 1: tc_pass<PREC, 1, 1>(a, q, lane, mt0, nt0); break;
+                    case 2: tc_pass<PREC, 1, 2>(a, q, lane, mt0, nt0); break;
+                    default: tc_pass<PREC, 1, 3>(a, q, lane, mt0, nt0); break;
+                }
+            } else {
+                switch (ntc) {
+                    case 1: tc_pass<PREC, 2, 1>(a, q, lane, mt0, nt0); break;
+                    case 2: tc_pass<PREC, 2, 2>(a, q, lane, mt0, nt0); break;
+                    default: tc_pass<PREC, 2, 3>(a, q, lane, mt0, nt0); break;
+                }
+            }
+        }
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long *ctr = a.work_counter;
+    while (true) {
+        int64_t q = 0;
+        if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= a.n_items) break;
+        tc_item<PREC>(a, q, lane);
+    }
+}
+
+// =====================================================================
+// Operand splitting and fragment packing
+// =====================================================================
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Split x into `np` pieces of the precision's narrow type, most significant
+// first; returns the bit patterns (TF32 in 32 bits, BF16 in the low 16).
+template <int PREC>
+__device__ __forceinline__ void split_value(double x, uint32_t (&out)[3]) {
+    if constexpr (PREC == BSM_P_TF32x3) {
+        const uint32_t hi = f32_to_tf32((float)x);
+        const double r = x - (double)__uint_as_float(hi);
+        out[0] = hi;
+        out[1] = f32_to_tf32((float)r);
+        out[2] = 0;
+    } else {
+        const __nv_bfloat16 h0 = __double2bfloat16(x);
+        const double r1 = x - (double)__bfloat162float(h0);
+        const __nv_bfloat16 h1 = __double2bfloat16(r1);
+        const double r2 = r1 - (double)__bfloat162float(h1);
+        const __nv_bfloat16 h2 = __double2bfloat16(r2);
+        out[0] = __bfloat16_as_ushort(h0);
+        out[1] = __bfloat16_as_ushort(h1);
+        out[2] = __bfloat16_as_ushort(h2);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double elem(const T *b, int R, int Tn, int trans, int r, int t) {
+    // logical R x Tn block, stored R x Tn (trans=0) or Tn x R (trans=1)
+    if (r >= R || t >= Tn) return 0.0;
+    return (double)(trans ? b[(int64_t)t * R + r] : b[(int64_t)r * Tn + t]);
+}
+
+// words of one block's packing
+__device__ __forceinline__ int64_t pack_words(int R, int C, int role_y, int prec) {
+    const int K = (prec == BSM_P_TF32x3) ? 8 : 16;
+    if (!role_y) {
+        const int XW = (prec == BSM_P_BF16x6) ? 12 : 8;
+        return (int64_t)((R + 15) / 16) * ((C + K - 1) / K) * 32 * XW;
+    }
+    const int YW = (prec == BSM_P_BF16x6) ? 6 : 4;
+    return (int64_t)((R + K - 1) / K) * ((C + 7) / 8) * 32 * YW;
+}
+
+// logical dims of block b for the role: X is R x T, Y is T x S
+__device__ __forceinline__ void logical_dims(int32_t rc, int trans, int &rows, int &cols) {
+    rows = trans ? rc_cols(rc) : rc_rows(rc);
+    cols = trans ? rc_rows(rc) : rc_cols(rc);
+}
+
+__global__ void k_pack_sizes(int64_t nnzb, const int32_t *blk_rc, int role_y, int trans, int prec,
+                             int64_t *words) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nnzb;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int rows, cols;
+        logical_dims(blk_rc[b], trans, rows, cols);
+        words[b] = pack_words(rows, cols, role_y, prec);
+    }
+}
+
+// one warp per block; lane L writes its fragment words of every tile
+template <typename T, int PREC>
+__global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_rc, const T *data,
+                       int role_y, int trans, const int64_t *pack_off, uint32_t *pack) {
+    using PT = PrecTraits<PREC>;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = wid; b < nnzb; b += nwarp) {
+        const T *src = data + blk_off[b];
+        int rows, cols;
+        logical_dims(blk_rc[b], trans, rows, cols);
+        // element accessor of the logical rows x cols block
+        auto at = [&](int r, int c) -> double {
+            return elem<T>(src, rows, cols, trans, r, c);
+        };
+        uint32_t *dst = pack + pack_off[b];
+        uint32_t sp[3];
+        if (!role_y) {
+            const int MT = (rows + 15) / 16, KT = (cols + PT::K - 1) / PT::K;
+            for (int kt = 0; kt < KT; ++kt)
+                for (int mt = 0; mt < MT; ++mt) {
+                    uint32_t *w = dst + ((int64_t)(kt * MT + mt) * 32 + lane) * PT::XW;
+                    const int r0 = mt * 16 + g, k0 = kt * PT::K;
+                    if constexpr (PREC == BSM_P_TF32x3) {
+                        const int rr[4] = {r0, r0 + 8, r0, r0 + 8};
+                        const int kk[4] = {k0 + t4, k0 + t4, k0 + t4 + 4, k0 + t4 + 4};
+                        for (int v = 0; v < 4; ++v) {
+                            split_value<PREC>(at(rr[v], kk[v]), sp);
+                            w[v] = sp[0];
+                            w[4 + v] = sp[1];
+                        }
+                    } else {
+                        // reg v holds (row, k) and (row, k+1)
+                        const int rr[4] = {r0, r0 + 8, r0, r0 + 8};
+                        const int kk[4] = {k0 + 2 * t4, k0 + 2 * t4, k0 + 2 * t4 + 8, k0 + 2 * t4 + 8};
+                        for (int v = 0; v < 4; ++v) {
+                            uint32_t lo[3], hi[3];
+                            split_value<PREC>(at(rr[v], kk[v]), lo);
+                            split_value<PREC>(at(rr[v], kk[v] + 1), hi);
+                            for (int pc = 0; pc < PT::NP; ++pc) w[4 * pc + v] = lo[pc] | (hi[pc] << 16);
+                        }
+                    }
+                }
+        } else {
+            const int KT = (rows + PT::K - 1) / PT::K, NT = (cols + 7) / 8;
+            for (int kt = 0; kt < KT; ++kt)
+                for (int nt = 0; nt < NT; ++nt) {
+                    uint32_t *w = dst + ((int64_t)(kt * NT + nt) * 32 + lane) * PT::YW;
+                    const int n0 = nt * 8 + g, k0 = kt * PT::K;
+                    if constexpr (PREC == BSM_P_TF32x3) {
+                        const int kk[2] = {k0 + t4, k0 + t4 + 4};
+                        for (int v = 0; v < 2; ++v) {
+                            split_value<PREC>(at(kk[v], n0), sp);
+                            w[v] = sp[0];
+                            w[2 + v] = sp[1];
+                        }
+                    } else {
+                        const int kk[2] = {k0 + 2 * t4, k0 + 2 * t4 + 8};
+                        for (int v = 0; v < 2; ++v) {
+                            uint32_t lo[3], hi[3];
+                            split_value<PREC>(at(kk[v], n0), lo);
+                            split_value<PREC>(at(kk[v] + 1, n0), hi);
+                            for (int pc = 0; pc < PT::NP; ++pc) w[2 * pc + v] = lo[pc] | (hi[pc] << 16);
+                        }
+                    }
+                }
+        }
+    }
+}
+
+int g_num_sms = 0;
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+template <typename K>
+int persistent_grid(K kernel, int64_t n_items) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreadsNum, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)num_sms() * per_sm;
+    const int64_t need = (n_items + kWarpsPerCta - 1) / kWarpsPerCta;
+    if (g > need) g = need;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
+    if (a.n_items == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const bool tc = a.prec == BSM_P_TF32x3 || a.prec == BSM_P_BF16x3 || a.prec == BSM_P_BF16x6;
+    if (!tc) {
+        if (a.dtype == BSM_FP64) {
+            k_numeric_cc<double><<<persistent_grid(k_numeric_cc<double>, a.n_items), kThreadsNum, 0, s>>>(a);
+        } else {
+            k_numeric_cc<float><<<persistent_grid(k_numeric_cc<float>, a.n_items), kThreadsNum, 0, s>>>(a);
+        }
+    } else if (a.prec == BSM_P_TF32x3) {
+        k_numeric_tc<BSM_P_TF32x3><<<persistent_grid(k_numeric_tc<BSM_P_TF32x3>, a.n_items), kThreadsNum, 0, s>>>(a);
+    } else if (a.prec == BSM_P_BF16x3) {
+        k_numeric_tc<BSM_P_BF16x3><<<persistent_grid(k_numeric_tc<BSM_P_BF16x3>, a.n_items), kThreadsNum, 0, s>>>(a);
+    } else {
+        k_numeric_tc<BSM_P_BF16x6><<<persistent_grid(k_numeric_tc<BSM_P_BF16x6>, a.n_items), kThreadsNum, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec, int64_t *pack_words,
+                              cudaStream_t s) {
+    if (M->nnzb == 0) return cudaSuccess;
+    int64_t g = (M->nnzb + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_pack_sizes<<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_rc, role_y, trans, prec, pack_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
+                        void *pack, cudaStream_t s) {
+    if (M->nnzb == 0) return cudaSuccess;
+    int64_t g = (M->nnzb * 32 + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    uint32_t *p = static_cast<uint32_t *>(pack);
+    const bool f64 = M->dtype == BSM_FP64;
+#define BSM_PACK_CASE(PREC)                                                                           \
+    if (f64)                                                                                          \
+        k_pack<double, PREC><<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc,              \
+                                                         static_cast<const double *>(M->data), role_y, \
+                                                         trans, pack_off, p);                         \
+    else                                                                                              \
+        k_pack<float, PREC><<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc,               \
+                                                        static_cast<const float *>(M->data), role_y,   \
+                                                        trans, pack_off, p);
+    if (prec == BSM_P_TF32x3) {
+        BSM_PACK_CASE(BSM_P_TF32x3)
+    } else if (prec == BSM_P_BF16x3) {
+        BSM_PACK_CASE(BSM_P_BF16x3)
+    } else {
+        BSM_PACK_CASE(BSM_P_BF16x6)
+    }
+#undef BSM_PACK_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace bsm

@@ -1,0 +1,72 @@
+"""The C-ABI library loads and exports every entry point include/bsm.h
+declares (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "bsm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libbsm():
+    from paper_1708_03604_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("bsm_create", "bsm_multiply", "bsm_multiply_backward", "bsm_add", "bsm_get_stacks"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libbsm):
+    missing = [n for n in _declared() if not hasattr(libbsm, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_export(libbsm):
+    from paper_1708_03604_gb300 import bsm
+    assert sorted(bsm.EXPORTS) == _declared()
+    L = bsm.lib()
+    for n in _declared():
+        assert getattr(L, n).argtypes is not None or n == "bsm_last_error"
+
+
+def test_host_side_argument_errors_need_no_gpu(libbsm):
+    """Argument checks run on the host before any CUDA call."""
+    from paper_1708_03604_gb300 import bsm
+    import numpy as np
+    L = bsm.lib()
+    h = ctypes.c_void_p()
+    bs = np.array([2, 3], np.int32)
+    rp = np.array([0, 1, 2], np.int64)
+    ci = np.array([1, 0], np.int32)
+    bo = np.array([0, 6], np.int64)
+    # block outside data_len
+    st = L.bsm_create(ctypes.byref(h), 2, 2, bs.ctypes.data, bs.ctypes.data, rp.ctypes.data, ci.ctypes.data,
+                      bo.ctypes.data, 0, 1, 10, 0)
+    assert st == bsm.BSM_ERR_ARG and b"data_len" in L.bsm_last_error()
+    # unsorted columns
+    rp2 = np.array([0, 2, 2], np.int64)
+    ci2 = np.array([1, 0], np.int32)
+    st = L.bsm_create(ctypes.byref(h), 2, 2, bs.ctypes.data, bs.ctypes.data, rp2.ctypes.data, ci2.ctypes.data,
+                      bo.ctypes.data, 0, 1, 100, 0)
+    assert st == bsm.BSM_ERR_ARG and b"ascending" in L.bsm_last_error()
+    # bad block size
+    bad = np.array([0, 3], np.int32)
+    st = L.bsm_create(ctypes.byref(h), 2, 2, bad.ctypes.data, bs.ctypes.data, rp.ctypes.data, ci.ctypes.data,
+                      bo.ctypes.data, 0, 1, 100, 0)
+    assert st == bsm.BSM_ERR_ARG
+    # bad opts are rejected before anything is read from the matrices
+    o = bsm.Opts()
+    o.prec = 99
+    assert L.bsm_multiply(1.0, None, None, 0.0, None, 0.0, ctypes.byref(o)) == bsm.BSM_ERR_ARG

@@ -1,0 +1,200 @@
+"""GPU parity of the block-sparse multiply against the CPU oracle.
+
+Integer results (C's pattern, the product list, the stacks, the filter
+decisions) must match bit for bit; FP64 values within a relative Frobenius
+error of 1e-12 (the accumulation order inside a block product differs from
+the oracle's naive loop), split-precision values within 1e-6 (TF32x3,
+BF16x6), FP32 data within 1e-5 of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1708_03604_gb300 import inputs as I
+from tests.helpers import random_bcsr, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def bsm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_03604_gb300 import bsm as B
+    B.lib()
+    return B
+
+
+def _check_pattern(C_gpu, C_ref):
+    rp, ci, bo = C_gpu.pattern()
+    np.testing.assert_array_equal(rp, C_ref.row_ptr)
+    np.testing.assert_array_equal(ci, C_ref.col_idx)
+    np.testing.assert_array_equal(bo, C_ref.blk_off)
+
+
+def _run(bsm, oracle, A, B, eps, prec="fp64", beta=0.0, C0=None, alpha=1.0, **kw):
+    dA, dB = bsm.Matrix.from_host(A), (bsm.Matrix.from_host(B) if B is not A else None)
+    dB = dB or dA
+    Cg = bsm.Matrix.from_host(C0) if C0 is not None else None
+    Cg = bsm.multiply(alpha, dA, dB, beta=beta, Cm=Cg, eps=eps, prec=prec, **kw)
+    ref = oracle.multiply(alpha, A, B, beta=beta, Cold=C0, eps=eps)
+    return Cg, ref, dA, dB
+
+
+def test_norms_bitexact(bsm, oracle):
+    bs = I.mixed_sizes(70, (1, 5, 13, 23, 40), (0.2, 0.3, 0.2, 0.2, 0.1), seed=3)
+    X = random_bcsr(bs, bs, 0.2, seed=11)
+    g = bsm.Matrix.from_host(X).block_norms()
+    np.testing.assert_array_equal(g, oracle.block_norms(X))
+    X32 = X.astype(np.float32)
+    g32 = bsm.Matrix.from_host(X32).block_norms()
+    np.testing.assert_array_equal(g32, oracle.block_norms(X32))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6", "bf16x3"])
+def test_uniform_23_small(bsm, oracle, prec):
+    w = I.uniform_23(nb=40, occ=0.2)
+    Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], 0.0, prec=prec)
+    _check_pattern(Cg, ref.C)
+    err = rel_fro(Cg.data_host(), ref.C.data)
+    assert err <= TOL[prec], err
+    p = Cg.products()
+    np.testing.assert_array_equal(p.a, ref.prods.a)
+    np.testing.assert_array_equal(p.b, ref.prods.b)
+    np.testing.assert_array_equal(p.c, ref.prods.c)
+    cnt = Cg.counts()
+    assert cnt.products == len(ref.prods.a)
+    assert cnt.useful_flop == ref.useful_flop
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
+def test_mixed_banded_filtered(bsm, oracle, prec):
+    # banded-then-permuted, sizes {5, 13, 23}, a threshold that filters a
+    # good share of the candidate products
+    w = I.mixed_banded(nb=240, occ=0.1, eps=1.0, decay=8.0)
+    Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], w["eps"], prec=prec)
+    assert ref.nfiltered > 0
+    _check_pattern(Cg, ref.C)
+    cnt = Cg.counts()
+    assert (cnt.products, cnt.filtered) == (len(ref.prods.a), ref.nfiltered)
+    err = rel_fro(Cg.data_host(), ref.C.data)
+    assert err <= TOL[prec], err
+    shapes, ptr, trip = Cg.stacks()
+    s_ref, p_ref, t_ref = oracle.stacks(w["A"], w["B"], ref.C, ref.prods)
+    np.testing.assert_array_equal(shapes, s_ref)
+    np.testing.assert_array_equal(ptr, p_ref)
+    np.testing.assert_array_equal(trip, t_ref)
+
+
+def test_ragged_sizes_and_large_blocks(bsm, oracle):
+    # block sizes 1..40 (several fragment tiles and element passes per block)
+    rng = np.random.default_rng(5)
+    rbs = rng.integers(1, 41, size=17).astype(np.int32)
+    kbs = rng.integers(1, 41, size=13).astype(np.int32)
+    cbs = rng.integers(1, 41, size=19).astype(np.int32)
+    A = random_bcsr(rbs, kbs, 0.4, seed=21)
+    B = random_bcsr(kbs, cbs, 0.4, seed=22)
+    for prec in ("fp64", "tf32x3", "bf16x6"):
+        Cg, ref, _, _ = _run(bsm, oracle, A, B, 0.0, prec=prec)
+        _check_pattern(Cg, ref.C)
+        assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
+
+
+def test_alpha_beta_merge(bsm, oracle):
+    bs = I.mixed_sizes(50, (2, 7, 11), (0.4, 0.3, 0.3), seed=9)
+    A, B, C0 = (random_bcsr(bs, bs, 0.15, seed=s) for s in (31, 32, 33))
+    for prec in ("fp64", "tf32x3"):
+        Cg, ref, _, _ = _run(bsm, oracle, A, B, 0.0, prec=prec, beta=-0.5, C0=C0, alpha=2.0)
+        _check_pattern(Cg, ref.C)
+        assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
+
+
+def test_beta_zero_ignores_old_nan(bsm, oracle):
+    bs = I.uniform_sizes(20, 4)
+    A, B, C0 = (random_bcsr(bs, bs, 0.2, seed=s) for s in (41, 42, 43))
+    C0.data[:] = np.nan
+    Cg, ref, _, _ = _run(bsm, oracle, A, B, 0.0, beta=0.0, C0=C0)
+    _check_pattern(Cg, ref.C)
+    assert np.all(np.isfinite(Cg.data_host()))
+
+
+def test_edge_cases(bsm, oracle):
+    bs = I.mixed_sizes(12, (1, 3), (0.5, 0.5), seed=1)
+    A = random_bcsr(bs, bs, 0.3, seed=51)
+    E = I.empty(bs, bs)
+    # empty operand -> empty C
+    for X, Y in ((A, E), (E, A), (E, E)):
+        Cg, ref, _, _ = _run(bsm, oracle, X, Y, 0.0)
+        assert Cg.nnzb == 0 and ref.C.nnzb == 0
+    # huge threshold -> everything filtered
+    Cg, ref, _, _ = _run(bsm, oracle, A, A, 1e300)
+    assert Cg.nnzb == 0 and Cg.counts().filtered == ref.nfiltered > 0
+    # A.A with the same handle (X^2)
+    dA = bsm.Matrix.from_host(A)
+    Cg = bsm.multiply(1.0, dA, dA)
+    ref = oracle.multiply(1.0, A, A)
+    _check_pattern(Cg, ref.C)
+    assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-12
+    # 1x1 blocks only
+    b1 = I.uniform_sizes(30, 1)
+    A1, B1 = random_bcsr(b1, b1, 0.3, seed=61), random_bcsr(b1, b1, 0.3, seed=62)
+    Cg, ref, _, _ = _run(bsm, oracle, A1, B1, 0.0)
+    _check_pattern(Cg, ref.C)
+    assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-12
+
+
+def test_blocking_mismatch_is_reported(bsm):
+    a = random_bcsr(I.uniform_sizes(5, 3), I.uniform_sizes(5, 3), 0.5, seed=1)
+    b = random_bcsr(I.uniform_sizes(5, 4), I.uniform_sizes(5, 4), 0.5, seed=2)
+    with pytest.raises(bsm.BsmError) as e:
+        bsm.multiply(1.0, bsm.Matrix.from_host(a), bsm.Matrix.from_host(b))
+    assert e.value.status == bsm.BSM_ERR_BLOCKING
+
+
+def test_deterministic(bsm):
+    w = I.mixed_banded(nb=200, occ=0.1, eps=1e-6)
+    A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+    for prec in ("fp64", "tf32x3"):
+        x = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec).data_host()
+        y = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec).data_host()
+        np.testing.assert_array_equal(x, y)
+
+
+def test_fp32_data(bsm, oracle):
+    w = I.differentiation_13(nb=60, occ=0.15, dtype=np.float32)
+    Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], 0.0)
+    _check_pattern(Cg, ref.C)
+    assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-5
+    Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], 0.0, prec="tf32x3")
+    assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_backward_matches_oracle(bsm, oracle, prec):
+    bs = I.mixed_sizes(40, (3, 7, 13), (0.4, 0.3, 0.3), seed=23)
+    A, B = random_bcsr(bs, bs, 0.15, seed=71), random_bcsr(bs, bs, 0.15, seed=72)
+    import torch
+    gA, gB = bsm.Matrix.from_host(A), bsm.Matrix.from_host(B)
+    Cg = bsm.multiply(0.75, gA, gB, eps=0.0)
+    ref = oracle.multiply(0.75, A, B)
+    G = np.random.default_rng(3).standard_normal(ref.C.data_len)
+    dA_ref, dB_ref = oracle.multiply_backward(0.75, A, B, ref.C, G, ref.prods)
+    dC = torch.tensor(G, device="cuda")
+    dA = torch.full((len(A.data),), np.nan, dtype=torch.float64, device="cuda")
+    dB = torch.full((len(B.data),), np.nan, dtype=torch.float64, device="cuda")
+    bsm.multiply_backward(0.75, Cg, dC, gA, gB, dA, dB, prec=prec)
+    assert rel_fro(dA.cpu().numpy(), dA_ref) <= TOL[prec]
+    assert rel_fro(dB.cpu().numpy(), dB_ref) <= TOL[prec]
+
+
+def test_add_bitexact(bsm, oracle):
+    bs = I.mixed_sizes(60, (1, 4), (0.5, 0.5), seed=29)
+    X, Y = random_bcsr(bs, bs, 0.1, seed=81), random_bcsr(bs, bs, 0.1, seed=82)
+    gX, gY = bsm.Matrix.from_host(X), bsm.Matrix.from_host(Y)
+    for eps in (0.0, 1.0):
+        Z = bsm.add(3.0, gX, -2.0, gY, eps=eps)
+        ref = oracle.add(3.0, X, -2.0, Y, eps=eps)
+        _check_pattern(Z, ref)
+        np.testing.assert_array_equal(Z.data_host(), ref.data)
