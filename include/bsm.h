@@ -92,6 +92,10 @@ bsm_status bsm_set_stream(void *stream);
 /* 1: record per-phase CUDA-event timings in every multiply (bsm_get_timings). */
 bsm_status bsm_set_profiling(int32_t on);
 
+/* Number of CUDA kernels the library has launched since it was loaded
+ * (all handles, all streams). */
+bsm_status bsm_get_launch_count(int64_t *count);
+
 /* Fills `opts` with the defaults (FP64, no post filter, stacks built). */
 bsm_status bsm_opts_default(bsm_opts *opts);
 

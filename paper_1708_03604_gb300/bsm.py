@@ -30,7 +30,7 @@ PREC = {"fp64": BSM_P_FP64, "fp64_dmma": BSM_P_FP64_DMMA, "tf32x3": BSM_P_TF32x3
 BSM_DATA_COPY, BSM_DATA_BORROW = 0, 1
 TIMING_PHASES = ["norms", "symbolic", "fill", "stacks", "numeric", "post", "total"]
 
-EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_opts_default", "bsm_create",
+EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_launch_count", "bsm_opts_default", "bsm_create",
            "bsm_create_empty", "bsm_create_like", "bsm_destroy", "bsm_get_info", "bsm_copy_pattern",
            "bsm_copy_data", "bsm_set_data", "bsm_data_ptr", "bsm_block_norms", "bsm_multiply",
            "bsm_multiply_backward", "bsm_get_counts", "bsm_get_timings", "bsm_get_products",
@@ -66,6 +66,7 @@ def lib() -> C.CDLL:
         "bsm_last_error": ([], C.c_char_p),
         "bsm_set_stream": ([_vp], _i32),
         "bsm_set_profiling": ([_i32], _i32),
+        "bsm_get_launch_count": ([_P(_i64)], _i32),
         "bsm_opts_default": ([_P(Opts)], _i32),
         "bsm_create": ([_P(_vp), _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _i64, _i32], _i32),
         "bsm_create_empty": ([_P(_vp), _i32, _i32, _vp, _vp, _i32], _i32),
@@ -128,6 +129,12 @@ def make_opts(prec="fp64", post_filter=False, build_stacks=True, flush_every=0) 
 # ---------------------------------------------------------------------------
 def bsm_set_profiling(on: bool):
     _check(lib().bsm_set_profiling(1 if on else 0))
+
+
+def bsm_get_launch_count() -> int:
+    n = _i64()
+    _check(lib().bsm_get_launch_count(C.byref(n)))
+    return n.value
 
 
 def bsm_create(row_bs, col_bs, row_ptr, col_idx, blk_off, dtype, data_ptr, data_len, data_mode) -> int:

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,6 +21,7 @@ cudaStream_t g_stream = nullptr;
 bool g_prof = false;
 bool g_pool_configured = false;
 int64_t *g_host = nullptr;  // pinned host words for small device->host reads
+std::atomic<int64_t> g_launches{0};
 
 struct Scratch {
     std::vector<void *> ptrs;
@@ -155,6 +157,8 @@ bsm_status read_words(const int64_t *const *src, int n) {
 }  // namespace
 
 cudaStream_t stream() { return g_stream; }
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 bool profiling() { return g_prof; }
 
 bsm_status set_error(bsm_status st, const std::string &msg) {
@@ -246,6 +250,12 @@ const char *bsm_last_error(void) { return t_err.c_str(); }
 
 bsm_status bsm_set_stream(void *s) {
     g_stream = static_cast<cudaStream_t>(s);
+    return BSM_OK;
+}
+
+bsm_status bsm_get_launch_count(int64_t *count) {
+    if (!count) return set_error(BSM_ERR_ARG, "count is NULL");
+    *count = launch_count();
     return BSM_OK;
 }
 

@@ -82,6 +82,9 @@ bsm_status set_error(bsm_status st, const std::string &msg);
 bsm_status cuda_check(cudaError_t e, const char *what);
 bsm_status dalloc(void **p, size_t bytes);
 void dfree(void *p);
+// Kernel launches issued by the library since it was loaded.
+void count_launch(int n);
+int64_t launch_count();
 template <typename T>
 inline bsm_status dalloc_t(T **p, size_t n) {
     return dalloc(reinterpret_cast<void **>(p), n * sizeof(T) + (n == 0 ? 16 : 0));

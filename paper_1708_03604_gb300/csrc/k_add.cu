@@ -234,12 +234,14 @@ cudaError_t launch_add_count(const bsm_mat *X, const bsm_mat *Y, int64_t *ccnt, 
     if (X->nbr == 0) return cudaSuccess;
     k_add_count<<<grid_for((int64_t)X->nbr * 32), kThreads, 0, s>>>(X->nbr, pat_of(*X), pat_of(*Y), ccnt,
                                                                    celem);
+    count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_fill(const bsm_mat *X, const bsm_mat *Y, const AddFill &f, cudaStream_t s) {
     if (X->nbr == 0) return cudaSuccess;
     k_add_fill<<<grid_for((int64_t)X->nbr * 32), kThreads, 0, s>>>(X->nbr, pat_of(*X), pat_of(*Y), f);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -256,12 +258,14 @@ cudaError_t launch_add_values(int64_t nnzb, const int64_t *z_blk_off, const int3
         k_add_values<float><<<g, kThreads, 0, s>>>(nnzb, z_blk_off, z_blk_rc, x_src, y_src, a,
                                                     static_cast<const float *>(x), b,
                                                     static_cast<const float *>(y), static_cast<float *>(z));
+    count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_keep_flags(int64_t nnzb, const double *norms, double eps, int64_t *keep, cudaStream_t s) {
     if (nnzb == 0) return cudaSuccess;
     k_keep_flags<<<grid_for(nnzb), kThreads, 0, s>>>(nnzb, norms, eps, keep);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -271,6 +275,7 @@ cudaError_t launch_row_keep_counts(int32_t nbr, const int64_t *row_ptr, const in
     if (nbr == 0) return cudaSuccess;
     k_row_keep_counts<<<grid_for((int64_t)nbr * 32), kThreads, 0, s>>>(nbr, row_ptr, keep, blk_rc, row_cnt,
                                                                       row_elem);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -279,6 +284,7 @@ cudaError_t launch_compact(const CompactArgs &c, cudaStream_t s) {
     const int g = grid_for((int64_t)c.nbr * 32);
     if (c.dtype == BSM_FP64) k_compact<double><<<g, kThreads, 0, s>>>(c);
     else k_compact<float><<<g, kThreads, 0, s>>>(c);
+    count_launch(1);
     return cudaGetLastError();
 }
 

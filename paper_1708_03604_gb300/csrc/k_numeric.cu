@@ -521,6 +521,7 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
     } else {
         k_numeric_tc<BSM_P_BF16x6><<<persistent_grid(k_numeric_tc<BSM_P_BF16x6>, a.n_items), kThreadsNum, 0, s>>>(a);
     }
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -530,6 +531,7 @@ cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec,
     int64_t g = (M->nnzb + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
     k_pack_sizes<<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_rc, role_y, trans, prec, pack_words);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -557,6 +559,7 @@ cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const
         BSM_PACK_CASE(BSM_P_BF16x6)
     }
 #undef BSM_PACK_CASE
+    count_launch(1);
     return cudaGetLastError();
 }
 

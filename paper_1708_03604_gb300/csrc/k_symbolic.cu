@@ -6,6 +6,8 @@
 // DBCSR, Bethune et al. 2017 §2).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "bsm_internal.cuh"
 
 namespace bsm {
@@ -422,11 +424,29 @@ __global__ void k_stack_triples(int64_t nprod, const int32_t *order, const int32
     }
 }
 
+// Counts of keys < nbins.  Few bins (shape ids): a per-CTA shared-memory
+// histogram merged with one global atomic per bin and CTA; many bins (block
+// indices): global atomics, which then rarely collide.
+constexpr int kSmemBins = 4096;
 __global__ void k_histogram(int64_t n, const uint32_t *keys, int64_t nbins, int64_t *counts) {
+    __shared__ unsigned int h[kSmemBins];
+    const bool local = nbins <= kSmemBins;
+    if (local) {
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0u;
+        __syncthreads();
+    }
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = keys[p];
-        if ((int64_t)k < nbins) atomicAdd(reinterpret_cast<unsigned long long *>(counts + k), 1ull);
+        if ((int64_t)k < nbins) {
+            if (local) atomicAdd(&h[k], 1u);
+            else atomicAdd(reinterpret_cast<unsigned long long *>(counts + k), 1ull);
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (h[b]) atomicAdd(reinterpret_cast<unsigned long long *>(counts + b), (unsigned long long)h[b]);
     }
 }
 
@@ -459,6 +479,7 @@ cudaError_t launch_blk_rc(const bsm_mat *X, int32_t *out_rc, cudaStream_t s) {
     const int64_t warps = X->nbr;
     k_blk_rc<<<grid_for(warps * 32), kThreads, 0, s>>>(X->nbr, X->row_bs, X->col_bs, X->row_ptr,
                                                        X->col_idx, out_rc);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -471,6 +492,7 @@ cudaError_t launch_block_norms(const bsm_mat *X, double *out, cudaStream_t s) {
     else
         k_block_norms<float><<<g, 128, 0, s>>>(X->nnzb, X->blk_off, X->blk_rc,
                                                 static_cast<const float *>(X->data), out);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -482,6 +504,7 @@ cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t 
     k_scan_tile_sums<<<(unsigned)nt, kThreads, 0, s>>>(in, n, tmp);
     k_scan_sums<<<1, kThreads, 0, s>>>(tmp, nt);
     k_scan_tiles<<<(unsigned)nt, kThreads, 0, s>>>(in, out, n, tmp, nt);
+    count_launch(3);
     return cudaGetLastError();
 }
 
@@ -496,6 +519,7 @@ cudaError_t launch_symbolic_count(const SymbolicArgs &a, int64_t *prod_cnt, int6
         if (e != cudaSuccess) return e;
     }
     k_sym_count<<<a.nbr, kThreads, smem, s>>>(a, prod_cnt, ccol_cnt, celem_cnt, bitmaps, totals);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -512,6 +536,7 @@ cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps,
         if (e != cudaSuccess) return e;
     }
     k_sym_fill<<<a.nbr, kThreads, smem, s>>>(a, bitmaps, o);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -543,6 +568,7 @@ cudaError_t launch_radix_sort_pairs(const uint32_t *keys_in, const int32_t *vals
         cudaError_t e = launch_scan_i64(hist, offs, h, stmp, s);
         if (e != cudaSuccess) return e;
         k_radix_scatter<<<(unsigned)nt, kThreads, 0, s>>>(ki, vi, ko, vo, n, 8 * p, nt, offs);
+        count_launch(2);
         ki = ko;
         vi = vo;
     }
@@ -556,6 +582,7 @@ cudaError_t launch_product_shape_ids(int64_t nprod, const int32_t *pa, const int
     if (nprod == 0) return cudaSuccess;
     k_product_shape_ids<<<grid_for(nprod), kThreads, 0, s>>>(nprod, pa, pb, a_blk_rc, b_blk_rc,
                                                              size_index, ns, keys, iota);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -565,6 +592,7 @@ cudaError_t launch_stack_triples(int64_t nprod, const int32_t *order, const int3
     if (nprod == 0) return cudaSuccess;
     k_stack_triples<<<grid_for(nprod), kThreads, 0, s>>>(nprod, order, pa, pb, pc, a_off, b_off, c_off,
                                                          triples);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -572,7 +600,9 @@ cudaError_t launch_histogram_u32(int64_t n, const uint32_t *keys, int64_t nbins,
                                  cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * (size_t)nbins, s);
     if (e != cudaSuccess || n == 0) return e;
-    k_histogram<<<grid_for(n), kThreads, 0, s>>>(n, keys, nbins, counts);
+    const int g = nbins <= kSmemBins ? std::min(grid_for(n), 152 * 4) : grid_for(n);
+    k_histogram<<<g, kThreads, 0, s>>>(n, keys, nbins, counts);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -580,12 +610,14 @@ cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *sr
                               cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_gather_i32<<<grid_for(n), kThreads, 0, s>>>(n, order, src, dst);
+    count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_iota_keys<<<grid_for(n), kThreads, 0, s>>>(n, src, keys, iota);
+    count_launch(1);
     return cudaGetLastError();
 }
 
