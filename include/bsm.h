@@ -239,6 +239,27 @@ bsm_status bsm_get_products(bsm_t C, int64_t *nprod, int32_t *a_idx, int32_t *b_
 bsm_status bsm_get_stacks(bsm_t C, int32_t *nshapes, int64_t *nprod, int32_t *shapes,
                           int64_t *stack_ptr, int64_t *triples);
 
+/*
+ * Allocation-free sizing of C = A.B (the paper has no counterpart; this is
+ * a library convenience).  For callers that must not allocate device memory
+ * when they size a product -- code running inside another framework's
+ * memory pool or arena, or a host thread that may not call cudaMalloc /
+ * cudaFree because those calls synchronise the device -- it computes, per
+ * block row i of C, the number of kept block products (prod_cnt[i]) and of
+ * C blocks (cblk_cnt[i]) under the same filter rule as bsm_multiply, and
+ * totals[0..2] = (kept products, filtered candidates, sum of m*n*k).
+ * All three outputs are device pointers supplied by the caller (nbr, nbr and
+ * 3 int64).  The call allocates nothing: the FP64 block norms it needs live
+ * in one fixed 16 MiB device array inside the library, so with
+ * filter_eps > 0 it accepts nnzb(A) + nnzb(B) <= 2,097,152 and returns
+ * BSM_ERR_CAPACITY beyond that.  The first call on each device looks the
+ * array up (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race on it.
+ */
+bsm_status bsm_count_products_static(bsm_t A, bsm_t B, double filter_eps, int64_t *prod_cnt,
+                                     int64_t *cblk_cnt, int64_t *totals);
+
 /* ---------------------------------------------------------------------- */
 /* block add (the purification chain's Z = 3 X^2 - 2 X^3)                   */
 /* ---------------------------------------------------------------------- */

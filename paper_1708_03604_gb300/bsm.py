@@ -34,7 +34,7 @@ EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_lau
            "bsm_create_empty", "bsm_create_like", "bsm_destroy", "bsm_get_info", "bsm_copy_pattern",
            "bsm_copy_data", "bsm_set_data", "bsm_data_ptr", "bsm_block_norms", "bsm_multiply",
            "bsm_multiply_backward", "bsm_get_counts", "bsm_get_timings", "bsm_get_products",
-           "bsm_get_stacks", "bsm_add"]
+           "bsm_get_stacks", "bsm_add", "bsm_count_products_static"]
 
 
 class BsmError(RuntimeError):
@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
         "bsm_get_products": ([_vp, _P(_i64), _vp, _vp, _vp], _i32),
         "bsm_get_stacks": ([_vp, _P(_i32), _P(_i64), _vp, _vp, _vp], _i32),
         "bsm_add": ([_f64, _vp, _f64, _vp, _vp, _f64], _i32),
+        "bsm_count_products_static": ([_vp, _vp, _f64, _vp, _vp, _vp], _i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
