@@ -297,8 +297,9 @@ def main():
     split = {}
     if not args.no_split:
         ref_norm = torch.linalg.vector_norm(C64).item()
-        for prec in ("tf32x3", "bf16x6", "bf16x3"):
-            step(prec)
+        for key, prec, fl in (("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
+                              ("tf32x3_fp64sum", "tf32x3", 1)):
+            step(prec, fl)
             torch.cuda.synchronize()
             bsm.bsm_set_profiling(True)
             ks = max(3, min(args.steps, 5))
@@ -306,14 +307,14 @@ def main():
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(stream)
             for _ in range(ks):
-                step(prec)
+                step(prec, fl)
                 num.append(Cm.timings()["numeric"])
             f1.record(stream)
             torch.cuda.synchronize()
             bsm.bsm_set_profiling(False)
             sms = max_over_ranks(f0.elapsed_time(f1)) / ks
             err = (torch.linalg.vector_norm(Cm.data_tensor() - C64).item() / ref_norm)
-            split[prec] = {"value": world * flop / (sms * 1e-3) / 1e12, "ms_per_step": sms,
+            split[key] = {"value": world * flop / (sms * 1e-3) / 1e12, "ms_per_step": sms,
                            "numeric_ms": statistics.mean(num), "speedup_vs_fp64": ms / sms,
                            "rel_fro_err_vs_fp64_path": err}
         step()  # leave the FP64 result in Cm

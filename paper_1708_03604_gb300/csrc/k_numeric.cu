@@ -177,37 +177,52 @@ __device__ __forceinline__ void mma_piece(float (&d)[4], const uint32_t (&a)[4],
     else mma_bf16(d, a, b);
 }
 
-template <int PREC>
-__device__ __forceinline__ void load_x(const uint32_t *p, uint32_t (&f)[PrecTraits<PREC>::NP][4]) {
-    const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(p));
-    const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
-    f[0][0] = v0.x; f[0][1] = v0.y; f[0][2] = v0.z; f[0][3] = v0.w;
-    f[1][0] = v1.x; f[1][1] = v1.y; f[1][2] = v1.z; f[1][3] = v1.w;
-    if constexpr (PrecTraits<PREC>::NP == 3) {
-        const uint4 v2 = __ldg(reinterpret_cast<const uint4 *>(p) + 2);
-        f[2][0] = v2.x; f[2][1] = v2.y; f[2][2] = v2.z; f[2][3] = v2.w;
-    }
-}
+// Per-lane staging ring: every lane copies its own fragment words of the
+// next (product, k-step) steps from global memory into its private slice of
+// shared memory with cp.async and reads back only those words, so the ring
+// needs no warp barrier -- only each lane's own cp.async.wait_group.
+template <int PREC> struct RingTraits;
+template <> struct RingTraits<BSM_P_TF32x3> { static constexpr int STAGES = 6, SW = 2 * 8 + 3 * 4; };
+template <> struct RingTraits<BSM_P_BF16x3> { static constexpr int STAGES = 6, SW = 2 * 8 + 3 * 4; };
+template <> struct RingTraits<BSM_P_BF16x6> { static constexpr int STAGES = 4, SW = 2 * 12 + 3 * 6 + 2; };
 
 template <int PREC>
-__device__ __forceinline__ void load_y(const uint32_t *p, uint32_t (&f)[PrecTraits<PREC>::NP][2]) {
-    if constexpr (PrecTraits<PREC>::NP == 2) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
-        f[0][0] = v.x; f[0][1] = v.y; f[1][0] = v.z; f[1][1] = v.w;
-    } else {
-        const uint2 v0 = __ldg(reinterpret_cast<const uint2 *>(p));
-        const uint2 v1 = __ldg(reinterpret_cast<const uint2 *>(p) + 1);
-        const uint2 v2 = __ldg(reinterpret_cast<const uint2 *>(p) + 2);
-        f[0][0] = v0.x; f[0][1] = v0.y; f[1][0] = v1.x; f[1][1] = v1.y;
-        f[2][0] = v2.x; f[2][1] = v2.y;
-    }
+__host__ __device__ constexpr int ring_words_per_warp() { return RingTraits<PREC>::STAGES * 32 * RingTraits<PREC>::SW; }
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+// Compensated (error-free) addition of b into the pair (hi, lo): hi + lo
+// carries about 48 significant bits (Knuth's TwoSum on FP32 values).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bp = __fsub_rn(s, hi);
+    const float ap = __fsub_rn(s, bp);
+    const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(b, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
 }
 
 // One pass over a super tile of MTC x NTC (at most 2 x 3) fragment tiles
 // starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
-template <int PREC, int MTC, int NTC>
-__device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0) {
+// FF: cross-product sum as a float-float pair (TwoSum after every block
+// product); otherwise an FP64 sum refreshed every `flush_every` products.
+template <int PREC, int MTC, int NTC, bool FF>
+__device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
+                                        uint32_t *ring) {
     using PT = PrecTraits<PREC>;
+    using RT = RingTraits<PREC>;
+    constexpr int ST = RT::STAGES, SW = RT::SW;
     const int32_t orc = a.out_blk_rc[q];
     const int R = rc_rows(orc), S = rc_cols(orc);
     const int MT = (R + 15) >> 4, NT = (S + 7) >> 3;
@@ -215,9 +230,12 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
     const uint32_t *XP = static_cast<const uint32_t *>(a.x_pack);
     const uint32_t *YP = static_cast<const uint32_t *>(a.y_pack);
     const int F = a.flush_every > 0 ? a.flush_every : 1;
+    uint32_t *myring = ring + lane * SW;          // stage st at myring + st * 32 * SW
+    const uint32_t ring_s = smem_addr(myring);
 
     float acc[MTC][NTC][4];
-    double acc64[MTC][NTC][4];
+    float shi[FF ? MTC : 1][FF ? NTC : 1][4], slo[FF ? MTC : 1][FF ? NTC : 1][4];
+    double s64[FF ? 1 : MTC][FF ? 1 : NTC][4];
 #pragma unroll
     for (int i = 0; i < MTC; ++i)
 #pragma unroll
@@ -225,26 +243,101 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 acc[i][j][v] = 0.f;
-                acc64[i][j][v] = 0.0;
+                if constexpr (FF) {
+                    shi[i][j][v] = 0.f;
+                    slo[i][j][v] = 0.f;
+                } else {
+                    s64[i][j][v] = 0.0;
+                }
             }
     int since = 0;
-    for (int64_t p = p0; p < p1; ++p) {
-        const int32_t ix = a.px[p], iy = a.py[p];
-        const int32_t xrc = a.x_blk_rc[ix];
-        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
-        const int KT = (Tn + PT::K - 1) / PT::K;
-        const uint32_t *xp = XP + a.x_pack_off[ix] + lane * PT::XW;
-        const uint32_t *yp = YP + a.y_pack_off[iy] + lane * PT::YW;
-        for (int kt = 0; kt < KT; ++kt) {
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+        const int nb = (int)min((int64_t)32, p1 - pb);
+        // metadata of up to 32 products, one per lane
+        int64_t mxo = 0, myo = 0;
+        int mkt = 0;
+        if (lane < nb) {
+            const int32_t ix = a.px[pb + lane], iy = a.py[pb + lane];
+            const int32_t xrc = a.x_blk_rc[ix];
+            const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+            mxo = a.x_pack_off[ix];
+            myo = a.y_pack_off[iy];
+            mkt = (Tn + PT::K - 1) / PT::K;
+        }
+        int nsteps = mkt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nsteps += __shfl_xor_sync(0xffffffffu, nsteps, o);
+        // producer cursor over the (product, k-step) sequence
+        int pu = 0, pk = 0;
+        int64_t pxo = __shfl_sync(0xffffffffu, mxo, 0), pyo = __shfl_sync(0xffffffffu, myo, 0);
+        int pkt = __shfl_sync(0xffffffffu, mkt, 0);
+        auto produce = [&](int st) {
+            const uint32_t dst = ring_s + (uint32_t)(st * 32 * SW) * 4u;
+#pragma unroll
+            for (int i = 0; i < MTC; ++i) {
+                if (mt0 + i < MT) {
+                    const uint32_t *src = XP + pxo + ((int64_t)(pk * MT + mt0 + i) * 32 + lane) * PT::XW;
+#pragma unroll
+                    for (int c = 0; c < PT::XW / 4; ++c) cp_async16(dst + (i * PT::XW + 4 * c) * 4u, src + 4 * c);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NTC; ++j) {
+                if (nt0 + j < NT) {
+                    const uint32_t *src = YP + pyo + ((int64_t)(pk * NT + nt0 + j) * 32 + lane) * PT::YW;
+                    const uint32_t d = dst + (MTC * PT::XW + j * PT::YW) * 4u;
+                    if constexpr (PT::YW == 4) {
+                        cp_async16(d, src);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < PT::YW / 2; ++c) cp_async8(d + 8u * c, src + 2 * c);
+                    }
+                }
+            }
+            if (++pk == pkt) {
+                pk = 0;
+                ++pu;
+                const int src_lane = pu < nb ? pu : 0;
+                pxo = __shfl_sync(0xffffffffu, mxo, src_lane);
+                pyo = __shfl_sync(0xffffffffu, myo, src_lane);
+                pkt = __shfl_sync(0xffffffffu, mkt, src_lane);
+            }
+        };
+#pragma unroll
+        for (int st = 0; st < ST - 1; ++st) {
+            if (st < nsteps) produce(st);
+            cp_async_commit();
+        }
+        int cu = 0, ck = 0;
+        int ckt = __shfl_sync(0xffffffffu, mkt, 0);
+        for (int s = 0; s < nsteps; ++s) {
+            if (s + ST - 1 < nsteps) produce((s + ST - 1) % ST);
+            cp_async_commit();
+            cp_async_wait<ST - 1>();
+            const uint32_t *w = myring + (s % ST) * 32 * SW;
             uint32_t fa[MTC][PT::NP][4];
 #pragma unroll
             for (int i = 0; i < MTC; ++i)
-                if (mt0 + i < MT) load_x<PREC>(xp + (int64_t)(kt * MT + mt0 + i) * 32 * PT::XW, fa[i]);
+#pragma unroll
+                for (int pc = 0; pc < PT::NP; ++pc) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(w + i * PT::XW + 4 * pc);
+                    fa[i][pc][0] = v.x; fa[i][pc][1] = v.y; fa[i][pc][2] = v.z; fa[i][pc][3] = v.w;
+                }
 #pragma unroll
             for (int j = 0; j < NTC; ++j) {
                 if (nt0 + j >= NT) continue;
                 uint32_t fb[PT::NP][2];
-                load_y<PREC>(yp + (int64_t)(kt * NT + nt0 + j) * 32 * PT::YW, fb);
+                const uint32_t *wy = w + MTC * PT::XW + j * PT::YW;
+                if constexpr (PT::NP == 2) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(wy);
+                    fb[0][0] = v.x; fb[0][1] = v.y; fb[1][0] = v.z; fb[1][1] = v.w;
+                } else {
+#pragma unroll
+                    for (int pc = 0; pc < 3; ++pc) {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(wy + 2 * pc);
+                        fb[pc][0] = v.x; fb[pc][1] = v.y;
+                    }
+                }
 #pragma unroll
                 for (int i = 0; i < MTC; ++i) {
                     if (mt0 + i >= MT) continue;
@@ -262,19 +355,26 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                     }
                 }
             }
+            if (++ck == ckt) {  // a block product is complete
+                ck = 0;
+                ++cu;
+                ckt = __shfl_sync(0xffffffffu, mkt, cu < nb ? cu : 0);
+                if (++since == F) {
+                    since = 0;
+#pragma unroll
+                    for (int i = 0; i < MTC; ++i)
+#pragma unroll
+                        for (int j = 0; j < NTC; ++j)
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                if constexpr (FF) two_sum_acc(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
+                                else s64[i][j][v] += (double)acc[i][j][v];
+                                acc[i][j][v] = 0.f;
+                            }
+                }
+            }
         }
-        if (++since == F) {
-            since = 0;
-#pragma unroll
-            for (int i = 0; i < MTC; ++i)
-#pragma unroll
-                for (int j = 0; j < NTC; ++j)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        acc64[i][j][v] += (double)acc[i][j][v];
-                        acc[i][j][v] = 0.f;
-                    }
-        }
+        cp_async_wait<0>();
     }
     // epilogue: fragment element v of tile (i, j) sits at
     // row (mt0+i)*16 + g + 8*(v>=2), column (nt0+j)*8 + 2*t4 + (v&1)
@@ -290,7 +390,10 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                 const int r = (mt0 + i) * 16 + g + ((v >> 1) << 3);
                 const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
                 if (r < R && c < S) {
-                    double val = a.alpha * (acc64[i][j][v] + (double)acc[i][j][v]);
+                    double sum;
+                    if constexpr (FF) sum = ((double)shi[i][j][v] + (double)slo[i][j][v]) + (double)acc[i][j][v];
+                    else sum = s64[i][j][v] + (double)acc[i][j][v];
+                    double val = a.alpha * sum;
                     const int64_t e = (int64_t)r * S + c;
                     if (a.dtype == BSM_FP64) {
                         if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
@@ -303,8 +406,8 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
             }
 }
 
-template <int PREC>
-__device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lane) {
+template <int PREC, bool FF>
+__device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
     for (int mt0 = 0; mt0 < MT; mt0 += 2) {
@@ -313,31 +416,33 @@ __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lan
             const int ntc = min(3, NT - nt0);
             if (mtc == 1) {
                 switch (ntc) {
-                    case 1: tc_pass<PREC, 1, 1>(a, q, lane, mt0, nt0); break;
-                    case 2: tc_pass<PREC, 1, 2>(a, q, lane, mt0, nt0); break;
-                    default: tc_pass<PREC, 1, 3>(a, q, lane, mt0, nt0); break;
+                    case 1: tc_pass<PREC, 1, 1, FF>(a, q, lane, mt0, nt0, ring); break;
+                    case 2: tc_pass<PREC, 1, 2, FF>(a, q, lane, mt0, nt0, ring); break;
+                    default: tc_pass<PREC, 1, 3, FF>(a, q, lane, mt0, nt0, ring); break;
                 }
             } else {
                 switch (ntc) {
-                    case 1: tc_pass<PREC, 2, 1>(a, q, lane, mt0, nt0); break;
-                    case 2: tc_pass<PREC, 2, 2>(a, q, lane, mt0, nt0); break;
-                    default: tc_pass<PREC, 2, 3>(a, q, lane, mt0, nt0); break;
+                    case 1: tc_pass<PREC, 2, 1, FF>(a, q, lane, mt0, nt0, ring); break;
+                    case 2: tc_pass<PREC, 2, 2, FF>(a, q, lane, mt0, nt0, ring); break;
+                    default: tc_pass<PREC, 2, 3, FF>(a, q, lane, mt0, nt0, ring); break;
                 }
             }
         }
     }
 }
 
-template <int PREC>
+template <int PREC, bool FF>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
-    const int lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) uint32_t tc_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC>();
     unsigned long long *ctr = a.work_counter;
     while (true) {
         int64_t q = 0;
         if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= a.n_items) break;
-        tc_item<PREC>(a, q, lane);
+        tc_item<PREC, FF>(a, q, lane, ring);
     }
 }
 
@@ -490,15 +595,29 @@ int num_sms() {
 }
 
 template <typename K>
-int persistent_grid(K kernel, int64_t n_items) {
+int persistent_grid(K kernel, int64_t n_items, size_t smem = 0) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreadsNum, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreadsNum, smem);
     if (per_sm < 1) per_sm = 1;
     int64_t g = (int64_t)num_sms() * per_sm;
     const int64_t need = (n_items + kWarpsPerCta - 1) / kWarpsPerCta;
     if (g > need) g = need;
     if (g < 1) g = 1;
     return (int)g;
+}
+
+template <int PREC, bool FF>
+cudaError_t launch_tc_ff(const NumericArgs &a, cudaStream_t s) {
+    const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC>() * kWarpsPerCta;
+    cudaError_t e = cudaFuncSetAttribute(k_numeric_tc<PREC, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_numeric_tc<PREC, FF><<<persistent_grid(k_numeric_tc<PREC, FF>, a.n_items, smem), kThreadsNum, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_tc(const NumericArgs &a, cudaStream_t s) {
+    return a.flush_every > 0 ? launch_tc_ff<PREC, false>(a, s) : launch_tc_ff<PREC, true>(a, s);
 }
 
 }  // namespace
@@ -515,12 +634,13 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
             k_numeric_cc<float><<<persistent_grid(k_numeric_cc<float>, a.n_items), kThreadsNum, 0, s>>>(a);
         }
     } else if (a.prec == BSM_P_TF32x3) {
-        k_numeric_tc<BSM_P_TF32x3><<<persistent_grid(k_numeric_tc<BSM_P_TF32x3>, a.n_items), kThreadsNum, 0, s>>>(a);
+        e = launch_tc<BSM_P_TF32x3>(a, s);
     } else if (a.prec == BSM_P_BF16x3) {
-        k_numeric_tc<BSM_P_BF16x3><<<persistent_grid(k_numeric_tc<BSM_P_BF16x3>, a.n_items), kThreadsNum, 0, s>>>(a);
+        e = launch_tc<BSM_P_BF16x3>(a, s);
     } else {
-        k_numeric_tc<BSM_P_BF16x6><<<persistent_grid(k_numeric_tc<BSM_P_BF16x6>, a.n_items), kThreadsNum, 0, s>>>(a);
+        e = launch_tc<BSM_P_BF16x6>(a, s);
     }
+    if (e != cudaSuccess) return e;
     count_launch(1);
     return cudaGetLastError();
 }

@@ -88,6 +88,15 @@ def test_mixed_banded_filtered(bsm, oracle, prec):
     np.testing.assert_array_equal(trip, t_ref)
 
 
+@pytest.mark.parametrize("prec,flush", [("tf32x3", 1), ("tf32x3", 4), ("bf16x6", 2)])
+def test_split_with_fp64_sum(bsm, oracle, prec, flush):
+    # cross-product sum in FP64, refreshed every `flush` block products
+    w = I.mixed_banded(nb=200, occ=0.1, eps=1e-6)
+    Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], w["eps"], prec=prec, flush_every=flush)
+    _check_pattern(Cg, ref.C)
+    assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
+
+
 def test_ragged_sizes_and_large_blocks(bsm, oracle):
     # block sizes 1..40 (several fragment tiles and element passes per block)
     rng = np.random.default_rng(5)
