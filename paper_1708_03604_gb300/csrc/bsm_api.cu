@@ -146,6 +146,47 @@ bsm_status pack_fill(Scratch &sc, const bsm_mat *M, int role_y, int trans, int p
     return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, g_stream), "pack");
 }
 
+// Processing order of n output blocks for the numeric kernels: grouped by
+// block shape, larger blocks first, so that neighbouring warps run the same
+// code path and the heaviest items start early.
+bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std::vector<int32_t> &rsz,
+                       const std::vector<int32_t> &csz, int32_t **order) {
+    *order = nullptr;
+    if (n <= 1) return BSM_OK;
+    std::vector<int32_t> sizes(rsz);
+    sizes.insert(sizes.end(), csz.begin(), csz.end());
+    std::sort(sizes.begin(), sizes.end());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    const int32_t ns = (int32_t)sizes.size();
+    if ((int64_t)ns * ns > (1 << 16)) return BSM_OK;  // too many shapes: natural order
+    std::vector<int32_t> sidx(kMaxBlockDim + 1, 0), table((size_t)ns * ns);
+    for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
+    std::vector<std::pair<int64_t, int32_t>> cls;
+    for (int32_t r = 0; r < ns; ++r)
+        for (int32_t c = 0; c < ns; ++c) cls.emplace_back(-(int64_t)sizes[r] * sizes[c], r * ns + c);
+    std::sort(cls.begin(), cls.end());
+    for (size_t q = 0; q < cls.size(); ++q) table[cls[q].second] = (int32_t)q;
+    int bits = 1;
+    while ((1ll << bits) < (int64_t)table.size()) ++bits;
+    bsm_status st;
+    int32_t *d_sidx, *d_table, *iota, *vals_alt, *out;
+    uint32_t *keys, *keys_alt, *keys_sorted;
+    int64_t *rtmp;
+    if ((st = sc.get(&d_sidx, sidx.size())) || (st = sc.get(&d_table, table.size())) || (st = sc.get(&iota, n)) ||
+        (st = sc.get(&vals_alt, n)) || (st = sc.get(&out, n)) || (st = sc.get(&keys, n)) ||
+        (st = sc.get(&keys_alt, n)) || (st = sc.get(&keys_sorted, n)) || (st = sc.get(&rtmp, radix_tmp_elems(n))))
+        return st;
+    cudaError_t e = cudaMemcpyAsync(d_sidx, sidx.data(), sizeof(int32_t) * sidx.size(), cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_table, table.data(), sizeof(int32_t) * table.size(), cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = launch_class_keys(n, blk_rc, d_sidx, ns, d_table, keys, iota, g_stream);
+    if (e == cudaSuccess)
+        e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
+    if ((st = cuda_check(e, "shape order"))) return st;
+    *order = out;
+    return BSM_OK;
+}
+
 bsm_status read_words(const int64_t *const *src, int n) {
     for (int q = 0; q < n; ++q) {
         cudaError_t e = cudaMemcpyAsync(g_host + q, src[q], sizeof(int64_t), cudaMemcpyDeviceToHost, g_stream);
@@ -619,8 +660,10 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     for (int64_t v : h_ccnt) max_ccnt = std::max(max_ccnt, v);
     if (nprod > INT32_MAX || nnzbC > INT32_MAX)
         return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31-1 products or C blocks");
-    const int fill_smem = symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt);
-    if (fill_smem > 220 * 1024) return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
+    int nchunk = 8;
+    while (nchunk > 1 && symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 160 * 1024) nchunk >>= 1;
+    if (symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 220 * 1024)
+        return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
     ev.mark(2);
 
     // ---- a3: fill C's pattern and the product list
@@ -634,7 +677,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (use_old && (st = sc.get(&old_off, nnzbC))) return st;
     if ((st = dalloc(&c_data, (size_t)lenC * esize(C->dtype)))) return st;
     sc.ptrs.push_back(c_data);
-    FillOut fo{prod_ptr, crow_ptr, celem_ptr, c_col, c_off, c_rc, cptr, pa, pb, pc, old_off, (int32_t)max_ccnt};
+    FillOut fo{prod_ptr, crow_ptr, celem_ptr, c_col, c_off, c_rc, cptr, pa, pb, pc, old_off, (int32_t)max_ccnt, nchunk};
     e = launch_symbolic_fill(sa, bitmaps, fo, g_stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cptr + nnzbC, prod_ptr + nbr, sizeof(int64_t), cudaMemcpyDeviceToDevice, g_stream);
@@ -722,6 +765,9 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.x_pack = pkA.words; na.x_pack_off = pkA.off;
     na.y_pack = pkB.words; na.y_pack_off = pkB.off;
     if ((st = sc.get(&na.work_counter, 2))) return st;
+    int32_t *order = nullptr;
+    if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order))) return st;
+    na.item_order = order;
     ev.mark(5);
     if ((st = cuda_check(launch_numeric(na, g_stream), "numeric"))) return st;
     ev.mark(6);
@@ -884,6 +930,9 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.x_pack = pkX.words; na.x_pack_off = pkX.off;
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;
         if ((st = sc.get(&na.work_counter, 2))) return st;
+        int32_t *item_order = nullptr;
+        if ((st = shape_order(sc, OUT->nnzb, OUT->blk_rc, OUT->h_row_bs, OUT->h_col_bs, &item_order))) return st;
+        na.item_order = item_order;
         if ((st = cuda_check(launch_numeric(na, g_stream), "adjoint numeric"))) return st;
     }
     return BSM_OK;

@@ -133,10 +133,11 @@ struct FillOut {
     int32_t *pa, *pb, *pc;
     int64_t *old_off;    // [nnzbC] or nullptr
     int32_t max_ccnt;
+    int32_t nchunk;      // A-block chunks per row (1..8, one warp each)
 };
 cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
                                  cudaStream_t s);
-int symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt);
+int64_t symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt, int nchunk);
 
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits.
 // Buffers: keys/vals in and out may not alias; `tmp` needs
@@ -161,6 +162,9 @@ cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *sr
                               cudaStream_t s);
 cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota,
                              cudaStream_t s);
+// Shape-class key of every block: table[size_index[rows] * ns + size_index[cols]].
+cudaError_t launch_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
+                              const int32_t *table, uint32_t *keys, int32_t *iota, cudaStream_t s);
 
 // ---------------------------------------------------------------- numeric
 struct NumericArgs {
@@ -184,6 +188,7 @@ struct NumericArgs {
     const void *x_pack; const int64_t *x_pack_off;
     const void *y_pack; const int64_t *y_pack_off;
     int32_t max_out_rows, max_out_cols;
+    const int32_t *item_order;  // nullable: processing order of the items (grouped by block shape)
     unsigned long long *work_counter;  // 8 bytes of device memory, zeroed by the launcher
 };
 cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s);

@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
         if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= a.n_items) break;
+        if (a.item_order) q = a.item_order[q];
         cc_dispatch<T>(a, q, lane);
     }
 }
@@ -157,14 +158,14 @@ template <> struct PrecTraits<BSM_P_BF16x3> { static constexpr int K = 16, XW = 
 template <> struct PrecTraits<BSM_P_BF16x6> { static constexpr int K = 16, XW = 12, YW = 6, NP = 3; };
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -182,9 +183,9 @@ __device__ __forceinline__ void mma_piece(float (&d)[4], const uint32_t (&a)[4],
 // shared memory with cp.async and reads back only those words, so the ring
 // needs no warp barrier -- only each lane's own cp.async.wait_group.
 template <int PREC> struct RingTraits;
-template <> struct RingTraits<BSM_P_TF32x3> { static constexpr int STAGES = 6, SW = 2 * 8 + 3 * 4; };
-template <> struct RingTraits<BSM_P_BF16x3> { static constexpr int STAGES = 6, SW = 2 * 8 + 3 * 4; };
-template <> struct RingTraits<BSM_P_BF16x6> { static constexpr int STAGES = 4, SW = 2 * 12 + 3 * 6 + 2; };
+template <> struct RingTraits<BSM_P_TF32x3> { static constexpr int STAGES = 4, SW = 2 * 8 + 3 * 4; };
+template <> struct RingTraits<BSM_P_BF16x3> { static constexpr int STAGES = 4, SW = 2 * 8 + 3 * 4; };
+template <> struct RingTraits<BSM_P_BF16x6> { static constexpr int STAGES = 3, SW = 2 * 12 + 3 * 6 + 2; };
 
 template <int PREC>
 __host__ __device__ constexpr int ring_words_per_warp() { return RingTraits<PREC>::STAGES * 32 * RingTraits<PREC>::SW; }
@@ -323,37 +324,35 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                     const uint4 v = *reinterpret_cast<const uint4 *>(w + i * PT::XW + 4 * pc);
                     fa[i][pc][0] = v.x; fa[i][pc][1] = v.y; fa[i][pc][2] = v.z; fa[i][pc][3] = v.w;
                 }
+            uint32_t fb[NTC][PT::NP][2];
 #pragma unroll
             for (int j = 0; j < NTC; ++j) {
-                if (nt0 + j >= NT) continue;
-                uint32_t fb[PT::NP][2];
                 const uint32_t *wy = w + MTC * PT::XW + j * PT::YW;
                 if constexpr (PT::NP == 2) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(wy);
-                    fb[0][0] = v.x; fb[0][1] = v.y; fb[1][0] = v.z; fb[1][1] = v.w;
+                    fb[j][0][0] = v.x; fb[j][0][1] = v.y; fb[j][1][0] = v.z; fb[j][1][1] = v.w;
                 } else {
 #pragma unroll
                     for (int pc = 0; pc < 3; ++pc) {
                         const uint2 v = *reinterpret_cast<const uint2 *>(wy + 2 * pc);
-                        fb[pc][0] = v.x; fb[pc][1] = v.y;
+                        fb[j][pc][0] = v.x; fb[j][pc][1] = v.y;
                     }
                 }
+            }
+            // piece products, smallest first; consecutive mma instructions go
+            // to different tiles so their accumulator chains overlap
+            constexpr int NTERM = PT::NP == 2 ? 3 : 6;
+            constexpr int TA[6] = {1, 0, 0, 0, 0, 0}, TB[6] = {0, 1, 0, 0, 0, 0};
+            constexpr int SA[6] = {2, 1, 0, 1, 0, 0}, SB[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
-                for (int i = 0; i < MTC; ++i) {
-                    if (mt0 + i >= MT) continue;
-                    if constexpr (PT::NP == 2) {
-                        mma_piece<PREC>(acc[i][j], fa[i][1], fb[0]);
-                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[1]);
-                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[0]);
-                    } else {
-                        mma_piece<PREC>(acc[i][j], fa[i][2], fb[0]);
-                        mma_piece<PREC>(acc[i][j], fa[i][1], fb[1]);
-                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[2]);
-                        mma_piece<PREC>(acc[i][j], fa[i][1], fb[0]);
-                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[1]);
-                        mma_piece<PREC>(acc[i][j], fa[i][0], fb[0]);
-                    }
-                }
+            for (int t = 0; t < NTERM; ++t) {
+                const int ia = PT::NP == 2 ? TA[t] : SA[t];
+                const int ib = PT::NP == 2 ? TB[t] : SB[t];
+#pragma unroll
+                for (int j = 0; j < NTC; ++j)
+#pragma unroll
+                    for (int i = 0; i < MTC; ++i)
+                        if (mt0 + i < MT && nt0 + j < NT) mma_piece<PREC>(acc[i][j], fa[i][ia], fb[j][ib]);
             }
             if (++ck == ckt) {  // a block product is complete
                 ck = 0;
@@ -442,6 +441,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
         if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= a.n_items) break;
+        if (a.item_order) q = a.item_order[q];
         tc_item<PREC, FF>(a, q, lane, ring);
     }
 }

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_fill(SymbolicArgs a, const uin
     int32_t *wpre = reinterpret_cast<int32_t *>(smem + nw);
     int32_t *cnt = wpre + nw;
     const int i = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t crow = o.crow_ptr[i];
     const int32_t ccnt = (int32_t)(o.crow_ptr[i + 1] - crow);
     const int64_t prow = o.prod_ptr[i];
@@ -312,36 +312,66 @@ __global__ void __launch_bounds__(kThreads) k_sym_fill(SymbolicArgs a, const uin
             o.old_off[crow + col_rank(bm, wpre, j)] = a.o_blk_off[c];
         }
     }
-    // products per C block
-    for (int32_t r = tid; r < ccnt; r += blockDim.x) cnt[r] = 0;
+    // Products per C block.  The row's A blocks are cut into o.nchunk
+    // contiguous chunks, one per warp; wc[c][r] counts chunk c's products for
+    // C column rank r.  Scanning over r (then over c) gives every chunk its own
+    // cursor per C block, so each warp scatters its chunk in ascending k
+    // without waiting for the others: chunk c's products of a C block all
+    // precede chunk c+1's.
+    int32_t *wc = cnt + o.max_ccnt;  // [nchunk][max_ccnt]
+    const int nchunk = o.nchunk;
+    for (int32_t r = tid; r < ccnt; r += blockDim.x)
+        for (int c = 0; c < nchunk; ++c) wc[c * o.max_ccnt + r] = 0;
     __syncthreads();
     const int64_t a_beg = a.a_row_ptr[i], a_end = a.a_row_ptr[i + 1];
-    for (int64_t ai = a_beg + warp; ai < a_end; ai += nwarps) {
-        const int32_t k = a.a_col_idx[ai];
-        const double na = a.use_filter ? a.a_norm[ai] : 0.0;
-        for (int64_t b = a.b_row_ptr[k] + lane; b < a.b_row_ptr[k + 1]; b += 32)
-            if (keep_product(a, na, b)) atomicAdd(&cnt[col_rank(bm, wpre, a.b_col_idx[b])], 1);
+    const int64_t per = (a_end - a_beg + nchunk - 1) / nchunk;
+    const int64_t c_beg = a_beg + (int64_t)warp * per, c_end = min(a_end, c_beg + per);
+    int32_t *my = wc + warp * o.max_ccnt;
+    if (warp < nchunk) {
+        for (int64_t ai = c_beg; ai < c_end; ++ai) {
+            const int32_t k = a.a_col_idx[ai];
+            const double na = a.use_filter ? a.a_norm[ai] : 0.0;
+            for (int64_t b = a.b_row_ptr[k] + lane; b < a.b_row_ptr[k + 1]; b += 32)
+                if (keep_product(a, na, b)) my[col_rank(bm, wpre, a.b_col_idx[b])]++;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // totals per C block, their scan, then the per-chunk cursors
+    for (int32_t r = tid; r < ccnt; r += blockDim.x) {
+        int32_t t = 0;
+        for (int c = 0; c < nchunk; ++c) t += wc[c * o.max_ccnt + r];
+        cnt[r] = t;
     }
     __syncthreads();
     block_exscan_array(cnt, ccnt, wtmp);
-    for (int32_t r = tid; r < ccnt; r += blockDim.x) o.cptr[crow + r] = prow + cnt[r];
-    __syncthreads();
-    // scatter in ascending k inside every C block: A blocks one at a time;
-    // inside one A block the target columns j are distinct, so the cursor
-    // increments do not collide.
-    for (int64_t ai = a_beg; ai < a_end; ++ai) {
-        const int32_t k = a.a_col_idx[ai];
-        const double na = a.use_filter ? a.a_norm[ai] : 0.0;
-        for (int64_t b = a.b_row_ptr[k] + tid; b < a.b_row_ptr[k + 1]; b += blockDim.x) {
-            if (keep_product(a, na, b)) {
-                const int32_t r = col_rank(bm, wpre, a.b_col_idx[b]);
-                const int32_t pos = cnt[r]++;
-                o.pa[prow + pos] = (int32_t)ai;
-                o.pb[prow + pos] = (int32_t)b;
-                o.pc[prow + pos] = (int32_t)(crow + r);
-            }
+    for (int32_t r = tid; r < ccnt; r += blockDim.x) {
+        o.cptr[crow + r] = prow + cnt[r];
+        int32_t run = cnt[r];
+        for (int c = 0; c < nchunk; ++c) {
+            const int32_t v = wc[c * o.max_ccnt + r];
+            wc[c * o.max_ccnt + r] = run;
+            run += v;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // scatter: inside one A block the target columns j are distinct, so the
+    // lanes' cursor increments do not collide
+    if (warp < nchunk) {
+        for (int64_t ai = c_beg; ai < c_end; ++ai) {
+            const int32_t k = a.a_col_idx[ai];
+            const double na = a.use_filter ? a.a_norm[ai] : 0.0;
+            for (int64_t b = a.b_row_ptr[k] + lane; b < a.b_row_ptr[k + 1]; b += 32) {
+                if (keep_product(a, na, b)) {
+                    const int32_t r = col_rank(bm, wpre, a.b_col_idx[b]);
+                    const int32_t pos = my[r]++;
+                    o.pa[prow + pos] = (int32_t)ai;
+                    o.pb[prow + pos] = (int32_t)b;
+                    o.pc[prow + pos] = (int32_t)(crow + r);
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -464,6 +494,16 @@ __global__ void k_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32
     }
 }
 
+__global__ void k_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
+                             const int32_t *table, uint32_t *keys, int32_t *iota) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t rc = blk_rc[p];
+        keys[p] = (uint32_t)table[size_index[rc_rows(rc)] * ns + size_index[rc_cols(rc)]];
+        iota[p] = (int32_t)p;
+    }
+}
+
 inline int grid_for(int64_t n, int threads = kThreads) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -523,14 +563,14 @@ cudaError_t launch_symbolic_count(const SymbolicArgs &a, int64_t *prod_cnt, int6
     return cudaGetLastError();
 }
 
-int symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt) {
-    return (int)((2 * (int64_t)nwords + max_ccnt + 1) * sizeof(int32_t));
+int64_t symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt, int nchunk) {
+    return (2 * (int64_t)nwords + (int64_t)(nchunk + 1) * max_ccnt + 1) * (int64_t)sizeof(int32_t);
 }
 
 cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
                                  cudaStream_t s) {
     if (a.nbr == 0) return cudaSuccess;
-    const int smem = symbolic_fill_smem_bytes(a.nwords, o.max_ccnt);
+    const int smem = (int)symbolic_fill_smem_bytes(a.nwords, o.max_ccnt, o.nchunk);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_sym_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -617,6 +657,14 @@ cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *sr
 cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_iota_keys<<<grid_for(n), kThreads, 0, s>>>(n, src, keys, iota);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
+                              const int32_t *table, uint32_t *keys, int32_t *iota, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_class_keys<<<grid_for(n), kThreads, 0, s>>>(n, blk_rc, size_index, ns, table, keys, iota);
     count_launch(1);
     return cudaGetLastError();
 }
