@@ -67,8 +67,12 @@ typedef struct {
     int32_t prec;          /* bsm_prec                                              */
     int32_t post_filter;   /* 1: after the multiply drop C blocks with norm <= eps   */
     int32_t build_stacks;  /* 1: also bucket the products by (m,n,k) (bsm_get_stacks) */
-    int32_t flush_every;   /* split paths: block products per FP64 flush (0: default) */
-    int32_t reserved[4];   /* must be zero                                          */
+    int32_t flush_every;   /* split paths: 0 = compensated FP32-pair sum of the block
+                              products (FP64 at the end); F > 0 = FP64 running sum
+                              refreshed every F block products                     */
+    int32_t no_sync;       /* 1: no host synchronisation (CUDA-graph capturable); see
+                              bsm_multiply and bsm_add                               */
+    int32_t reserved[3];   /* must be zero                                          */
 } bsm_opts;
 
 /* Timing phases recorded when profiling is on (milliseconds, CUDA events on
@@ -161,6 +165,12 @@ bsm_status bsm_copy_data(bsm_t X, void *dst);
  * invalidates the cached block norms. */
 bsm_status bsm_set_data(bsm_t X, const void *src);
 
+/* Make X's element storage the caller's device buffer `dptr` (X's
+ * data_len elements of X's dtype, caller-owned, kept alive while X uses it);
+ * storage X owned is released (stream-ordered).  Lets a framework hold the
+ * values of a product in its own tensor without a second handle. */
+bsm_status bsm_borrow_data(bsm_t X, void *dptr);
+
 /* Device pointer of X's element storage (owned or borrowed). */
 bsm_status bsm_data_ptr(bsm_t X, void **dptr);
 
@@ -193,6 +203,14 @@ bsm_status bsm_block_norms(bsm_t X, double *out);
  *   with opts->build_stacks, the per-shape stacks for bsm_get_stacks.
  *   opts may be NULL (defaults).  The call synchronises the stream once,
  *   after the symbolic phase, to size C.
+ *   opts->no_sync = 1: nothing synchronises the host, so the call can be
+ *   captured in a CUDA graph.  It needs an earlier (eager) multiply of the same
+ *   A and B handles into C with the same filter_eps and precision, beta == 0
+ *   and no post filter; it recomputes the pattern and values on the device into
+ *   C's present storage, whose sizes come from that eager call.  If the
+ *   recomputed sizes differ, the device sets C's status word
+ *   (bsm_get_status -> BSM_ERR_CAPACITY) and writes nothing into C.  Stacks
+ *   are not rebuilt.
  */
 bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C,
                         double filter_eps, const bsm_opts *opts);
@@ -267,8 +285,23 @@ bsm_status bsm_count_products_static(bsm_t A, bsm_t B, double filter_eps, int64_
 /* Z = a*X + b*Y over the union of X's and Y's patterns; with
  * filter_eps > 0 a result block is kept iff its FP64 norm > filter_eps.
  * X, Y and Z share one blocking and dtype; Z differs from X and Y.  Z's
- * pattern and data are replaced. */
-bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps);
+ * pattern and data are replaced.  opts may be NULL; opts->no_sync = 1 works as
+ * for bsm_multiply (needs an earlier eager add of the same X, Y, a, b and
+ * filter_eps into Z).  Each element is one rounded product per term and one
+ * rounded sum (no fused multiply-add). */
+bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps, const bsm_opts *opts);
+
+/* Device status word of the last call that wrote X: BSM_OK, or
+ * BSM_ERR_CAPACITY when a no-sync call found sizes different from its eager
+ * call (then *status has bit 1 set).  Synchronises the stream. */
+bsm_status bsm_get_status(bsm_t X, int32_t *status);
+
+/* Adjoint of the last bsm_add that wrote Z (Z = a*X + b*Y, blocks with norm
+ * <= eps dropped), at that add's keep-decisions: dX = a*dZ on the X blocks
+ * that reached Z, dY = b*dZ likewise, zero elsewhere.  dZ_data has Z's
+ * layout; dX_data / dY_data have X's / Y's layout (overwritten; either may be
+ * NULL).  X and Y must be the handles of that add. */
+bsm_status bsm_add_backward(bsm_t Z, const void *dZ_data, bsm_t X, bsm_t Y, void *dX_data, void *dY_data);
 
 #ifdef __cplusplus
 }

@@ -34,7 +34,8 @@ EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_lau
            "bsm_create_empty", "bsm_create_like", "bsm_destroy", "bsm_get_info", "bsm_copy_pattern",
            "bsm_copy_data", "bsm_set_data", "bsm_data_ptr", "bsm_block_norms", "bsm_multiply",
            "bsm_multiply_backward", "bsm_get_counts", "bsm_get_timings", "bsm_get_products",
-           "bsm_get_stacks", "bsm_add", "bsm_count_products_static"]
+           "bsm_get_stacks", "bsm_add", "bsm_count_products_static", "bsm_borrow_data", "bsm_add_backward",
+           "bsm_get_status"]
 
 
 class BsmError(RuntimeError):
@@ -45,7 +46,7 @@ class BsmError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("post_filter", C.c_int32), ("build_stacks", C.c_int32),
-                ("flush_every", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("flush_every", C.c_int32), ("no_sync", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 _lib = None
@@ -84,8 +85,11 @@ def lib() -> C.CDLL:
         "bsm_get_timings": ([_vp, _P(_f64)], _i32),
         "bsm_get_products": ([_vp, _P(_i64), _vp, _vp, _vp], _i32),
         "bsm_get_stacks": ([_vp, _P(_i32), _P(_i64), _vp, _vp, _vp], _i32),
-        "bsm_add": ([_f64, _vp, _f64, _vp, _vp, _f64], _i32),
+        "bsm_add": ([_f64, _vp, _f64, _vp, _vp, _f64, _P(Opts)], _i32),
+        "bsm_get_status": ([_vp, _P(_i32)], _i32),
         "bsm_count_products_static": ([_vp, _vp, _f64, _vp, _vp, _vp], _i32),
+        "bsm_borrow_data": ([_vp, _vp], _i32),
+        "bsm_add_backward": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -115,13 +119,14 @@ def _sync_stream():
     _check(lib().bsm_set_stream(C.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
 
-def make_opts(prec="fp64", post_filter=False, build_stacks=True, flush_every=0) -> Opts:
+def make_opts(prec="fp64", post_filter=False, build_stacks=True, flush_every=0, no_sync=False) -> Opts:
     o = Opts()
     _check(lib().bsm_opts_default(C.byref(o)))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.post_filter = int(bool(post_filter))
     o.build_stacks = int(bool(build_stacks))
     o.flush_every = int(flush_every)
+    o.no_sync = int(bool(no_sync))
     return o
 
 
@@ -185,8 +190,16 @@ def bsm_multiply_backward(alpha, Cm: int, dC_ptr, A: int, B: int, dA_ptr, dB_ptr
                                        C.byref(opts) if opts is not None else None))
 
 
-def bsm_add(a, X: int, b, Y: int, Z: int, filter_eps):
-    _check(lib().bsm_add(float(a), X, float(b), Y, Z, float(filter_eps)))
+def bsm_add(a, X: int, b, Y: int, Z: int, filter_eps, opts: Opts | None = None):
+    _check(lib().bsm_add(float(a), X, float(b), Y, Z, float(filter_eps), C.byref(opts) if opts is not None else None))
+
+
+def bsm_get_status(X: int) -> int:
+    s = _i32()
+    st = lib().bsm_get_status(X, C.byref(s))
+    if st not in (BSM_OK, BSM_ERR_CAPACITY):
+        _check(st)
+    return s.value
 
 
 def bsm_get_counts(Cm: int):
@@ -296,6 +309,12 @@ class Matrix:
         _sync_stream()
         _check(lib().bsm_set_data(self.h, _ptr(src)))
 
+    def borrow(self, t):
+        """Make the handle's data the CUDA tensor t (kept alive by the handle)."""
+        _sync_stream()
+        _check(lib().bsm_borrow_data(self.h, _ptr(t)))
+        self._keep = t
+
     def data_ptr(self) -> int:
         p = C.c_void_p()
         _check(lib().bsm_data_ptr(self.h, C.byref(p)))
@@ -343,12 +362,12 @@ class Matrix:
 
 
 def multiply(alpha, A: Matrix, B: Matrix, beta=0.0, Cm: Matrix | None = None, eps=0.0, prec="fp64",
-             post_filter=False, build_stacks=True, flush_every=0) -> Matrix:
+             post_filter=False, build_stacks=True, flush_every=0, no_sync=False) -> Matrix:
     """C = alpha * A.B + beta * C with on-the-fly filtering at eps."""
     _sync_stream()
     if Cm is None:
         Cm = Matrix.empty(A.row_bs, B.col_bs, np.float64 if A.info().dtype == BSM_FP64 else np.float32)
-    bsm_multiply(alpha, A.h, B.h, beta, Cm.h, eps, make_opts(prec, post_filter, build_stacks, flush_every))
+    bsm_multiply(alpha, A.h, B.h, beta, Cm.h, eps, make_opts(prec, post_filter, build_stacks, flush_every, no_sync))
     return Cm
 
 
@@ -361,10 +380,16 @@ def multiply_backward(alpha, Cm: Matrix, dC, A: Matrix, B: Matrix, dA=None, dB=N
                           make_opts(prec, False, False, flush_every))
 
 
-def add(a, X: Matrix, b, Y: Matrix, Z: Matrix | None = None, eps=0.0) -> Matrix:
+def add_backward(Z: Matrix, dZ, X: Matrix, Y: Matrix, dX=None, dY=None):
+    """Adjoint of the last add into Z; tensors laid out like Z's/X's/Y's data."""
+    _sync_stream()
+    _check(lib().bsm_add_backward(Z.h, _ptr(dZ), X.h, Y.h, _ptr(dX), _ptr(dY)))
+
+
+def add(a, X: Matrix, b, Y: Matrix, Z: Matrix | None = None, eps=0.0, no_sync=False) -> Matrix:
     """Z = a*X + b*Y over the union pattern, blocks with norm <= eps dropped."""
     _sync_stream()
     if Z is None:
         Z = Matrix.empty(X.row_bs, X.col_bs, np.float64 if X.info().dtype == BSM_FP64 else np.float32)
-    bsm_add(a, X.h, b, Y.h, Z.h, eps)
+    bsm_add(a, X.h, b, Y.h, Z.h, eps, make_opts(no_sync=no_sync))
     return Z

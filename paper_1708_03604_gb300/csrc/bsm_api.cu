@@ -92,6 +92,11 @@ void free_results(bsm_mat *C) {
     C->prod_A = C->prod_B = nullptr;
     C->prod_A_nnzb = C->prod_B_nnzb = -1;
     C->timings_valid = false;
+    dfree(C->add_xsrc); C->add_xsrc = nullptr;
+    dfree(C->add_ysrc); C->add_ysrc = nullptr;
+    C->add_X = C->add_Y = nullptr;
+    C->add_X_nnzb = C->add_Y_nnzb = -1;
+    C->plan = bsm_mat::Plan{};
 }
 
 void free_pattern(bsm_mat *X) {
@@ -104,6 +109,7 @@ void free_pattern(bsm_mat *X) {
     X->own_data = false;
     dfree(X->norms); X->norms = nullptr;
     X->norms_valid = false;
+    dfree(X->item_order); X->item_order = nullptr;
     X->nnzb = 0;
     X->data_len = 0;
 }
@@ -114,7 +120,8 @@ bsm_status check_opts(const bsm_opts *o, bsm_opts *out) {
     *out = *o;
     if (o->prec < BSM_P_FP64 || o->prec > BSM_P_BF16x6) return set_error(BSM_ERR_ARG, "opts.prec out of range");
     if (o->flush_every < 0) return set_error(BSM_ERR_ARG, "opts.flush_every < 0");
-    for (int q = 0; q < 4; ++q)
+    if (o->no_sync != 0 && o->no_sync != 1) return set_error(BSM_ERR_ARG, "opts.no_sync must be 0 or 1");
+    for (int q = 0; q < 3; ++q)
         if (o->reserved[q] != 0) return set_error(BSM_ERR_ARG, "opts.reserved must be zero");
     return BSM_OK;
 }
@@ -143,7 +150,7 @@ bsm_status pack_fill(Scratch &sc, const bsm_mat *M, int role_y, int trans, int p
                      int64_t total_words) {
     bsm_status st;
     if ((st = sc.get(&pk.words, (size_t)total_words + 16)) != BSM_OK) return st;
-    return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, g_stream), "pack");
+    return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, nullptr, g_stream), "pack");
 }
 
 // Processing order of n output blocks for the numeric kernels: grouped by
@@ -231,16 +238,20 @@ void dfree(void *p) {
 }
 
 // --------------------------------------------------------------------------
-// shared step: drop blocks with norm <= eps from X (in place), compacting
+// Drop blocks with norm <= eps from X, compacting.  Eager: sizes read back,
+// new storage allocated and swapped in.  No-sync: the surviving blocks are
+// written into X's present storage, whose sizes (nnz_out, len_out) must be
+// what the filter leaves; the device checks that and flags `status`.
+// The provenance arrays of an add are compacted alongside.
 // --------------------------------------------------------------------------
-bsm_status norm_filter_compact(bsm_mat *X, double eps) {
-    if (X->nnzb == 0) return BSM_OK;
+bsm_status filter_compact(bsm_mat *X, double eps, bool no_sync, int32_t *status, int64_t nnz_out, int64_t len_out,
+                          bsm_mat *dst) {
     Scratch sc;
     bsm_status st;
+    const int64_t nb = X->nnzb;
     double *nrm = nullptr;
     int64_t *keep = nullptr, *kscan = nullptr, *tmp = nullptr, *rcnt = nullptr, *relem = nullptr,
             *nrow = nullptr, *nelem = nullptr;
-    const int64_t nb = X->nnzb;
     if ((st = sc.get(&nrm, nb)) || (st = sc.get(&keep, nb)) || (st = sc.get(&kscan, nb + 1)) ||
         (st = sc.get(&tmp, scan_tmp_elems(std::max<int64_t>(nb, X->nbr)))) || (st = sc.get(&rcnt, X->nbr)) ||
         (st = sc.get(&relem, X->nbr)) || (st = sc.get(&nrow, X->nbr + 1)) || (st = sc.get(&nelem, X->nbr + 1)))
@@ -252,20 +263,46 @@ bsm_status norm_filter_compact(bsm_mat *X, double eps) {
     if (e == cudaSuccess) e = launch_scan_i64(rcnt, nrow, X->nbr, tmp, g_stream);
     if (e == cudaSuccess) e = launch_scan_i64(relem, nelem, X->nbr, tmp, g_stream);
     if ((st = cuda_check(e, "norm filter"))) return st;
-    const int64_t *src[2] = {nrow + X->nbr, nelem + X->nbr};
-    if ((st = read_words(src, 2))) return st;
-    const int64_t nnz2 = g_host[0], len2 = g_host[1];
-    if (nnz2 == nb) return BSM_OK;  // nothing dropped
-    int32_t *ncol = nullptr, *nrc = nullptr;
-    int64_t *noff = nullptr;
-    void *ndata = nullptr;
-    if ((st = sc.get(&ncol, nnz2)) || (st = sc.get(&noff, nnz2)) || (st = sc.get(&nrc, nnz2))) return st;
-    if ((st = dalloc(&ndata, (size_t)len2 * esize(X->dtype)))) return st;
-    sc.ptrs.push_back(ndata);
+    int64_t nnz2, len2;
+    if (no_sync) {
+        PlanCheck pc{};
+        pc.actual[0] = nrow + X->nbr; pc.expected[0] = nnz_out;
+        pc.actual[1] = nelem + X->nbr; pc.expected[1] = len_out;
+        pc.n = 2;
+        if ((st = cuda_check(launch_check_plan(pc, status, g_stream), "plan check"))) return st;
+        nnz2 = nnz_out;
+        len2 = len_out;
+    } else {
+        const int64_t *src[2] = {nrow + X->nbr, nelem + X->nbr};
+        if ((st = read_words(src, 2))) return st;
+        nnz2 = g_host[0];
+        len2 = g_host[1];
+    }
+    // destination arrays
+    int32_t *ncol, *nrc;
+    int64_t *noff, *nxs = nullptr, *nys = nullptr, *nrowp;
+    void *ndata;
+    if (no_sync) {
+        ncol = dst->col_idx; nrc = dst->blk_rc; noff = dst->blk_off; ndata = dst->data; nrowp = dst->row_ptr;
+        nxs = dst->add_xsrc; nys = dst->add_ysrc;
+    } else {
+        if ((st = sc.get(&ncol, nnz2)) || (st = sc.get(&noff, nnz2)) || (st = sc.get(&nrc, nnz2))) return st;
+        if ((st = dalloc(&ndata, (size_t)len2 * esize(X->dtype)))) return st;
+        sc.ptrs.push_back(ndata);
+        nrowp = nrow;
+        if (X->add_xsrc && ((st = sc.get(&nxs, nnz2)) || (st = sc.get(&nys, nnz2)))) return st;
+    }
     CompactArgs c{X->nbr, X->row_ptr, X->col_idx, X->blk_off, X->blk_rc, kscan, nrow, nelem,
-                  X->data, X->dtype, ncol, noff, nrc, ndata};
-    if ((st = cuda_check(launch_compact(c, g_stream), "compact"))) return st;
-    // swap in
+                  X->data, X->dtype, ncol, noff, nrc, ndata, no_sync ? status : nullptr};
+    e = launch_compact(c, g_stream);
+    if (e == cudaSuccess && X->add_xsrc) {
+        e = launch_compact_i64(nb, kscan, X->add_xsrc, nxs, no_sync ? status : nullptr, g_stream);
+        if (e == cudaSuccess) e = launch_compact_i64(nb, kscan, X->add_ysrc, nys, no_sync ? status : nullptr, g_stream);
+    }
+    if (no_sync && e == cudaSuccess) e = launch_copy_i64_if_ok(X->nbr + 1, nrow, nrowp, status, g_stream);
+    if ((st = cuda_check(e, "compact"))) return st;
+    if (no_sync) return BSM_OK;
+    // eager: swap the compacted storage into X
     dfree(X->row_ptr); dfree(X->col_idx); dfree(X->blk_off); dfree(X->blk_rc);
     if (X->own_data) dfree(X->data);
     dfree(X->norms);
@@ -275,7 +312,21 @@ bsm_status norm_filter_compact(bsm_mat *X, double eps) {
     X->own_data = true;
     X->nnzb = nnz2; X->data_len = len2;
     for (void *p : {(void *)nrow, (void *)ncol, (void *)noff, (void *)nrc, ndata}) sc.release(p);
+    if (X->add_xsrc) {
+        dfree(X->add_xsrc);
+        dfree(X->add_ysrc);
+        X->add_xsrc = nxs;
+        X->add_ysrc = nys;
+        sc.release(nxs);
+        sc.release(nys);
+    }
     return BSM_OK;
+}
+
+// status word of a handle, allocated on its first use
+bsm_status ensure_status(bsm_mat *X) {
+    if (X->status) return BSM_OK;
+    return dalloc_t(&X->status, 1);
 }
 
 }  // namespace bsm
@@ -499,6 +550,7 @@ bsm_status bsm_destroy(bsm_t X) {
     free_pattern(X);
     dfree(X->row_bs);
     dfree(X->col_bs);
+    dfree(X->status);
     delete X;
     return BSM_OK;
 }
@@ -580,16 +632,30 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         return set_error(BSM_ERR_BLOCKING, "C's block columns do not match B's block columns");
     if (!std::isfinite(alpha) || !std::isfinite(beta) || std::isnan(filter_eps))
         return set_error(BSM_ERR_ARG, "alpha, beta and eps must be finite");
-    if ((st = ensure_globals())) return st;
+    const bool no_sync = opts.no_sync != 0;
+    const auto &pl = C->plan;
+    if (no_sync) {
+        if (pl.kind != 1 || pl.A != A || pl.B != B || pl.A_nnzb != A->nnzb || pl.B_nnzb != B->nnzb ||
+            pl.eps != filter_eps || pl.prec != opts.prec || !C->pa)
+            return set_error(BSM_ERR_ARG, "no_sync needs an earlier eager multiply of the same A and B (same eps "
+                                          "and precision) into C");
+        if (beta != 0.0) return set_error(BSM_ERR_UNSUPPORTED, "no_sync needs beta == 0");
+        if (opts.post_filter) return set_error(BSM_ERR_UNSUPPORTED, "no_sync excludes post_filter");
+    } else if ((st = ensure_globals())) {
+        return st;
+    }
+    if ((st = ensure_status(C))) return st;
 
     const int32_t nbr = A->nbr, nbk = A->nbc, nbc = B->nbc;
     const bool use_filter = filter_eps > 0.0;
     const bool use_old = beta != 0.0 && C->nnzb > 0;
     const int32_t nwords = (nbc + 31) / 32;
     Events ev;
-    ev.start();
+    if (!no_sync) ev.start();
     ev.mark(0);
     Scratch sc;
+    cudaError_t e = cudaMemsetAsync(C->status, 0, sizeof(int32_t), g_stream);
+    if ((st = cuda_check(e, "status"))) return st;
 
     // ---- a1: block norms (FP64) of A and B
     double *nA = nullptr, *nB = nullptr;
@@ -617,6 +683,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     sa.eps = filter_eps;
     sa.use_filter = use_filter ? 1 : 0;
     sa.nwords = nwords;
+    sa.status = no_sync ? C->status : nullptr;
     if ((size_t)nwords * 4 > 200 * 1024) return set_error(BSM_ERR_UNSUPPORTED, "too many block columns for the symbolic phase");
     int64_t *prod_cnt, *ccol_cnt, *celem_cnt, *prod_ptr, *crow_ptr, *celem_ptr, *stmp;
     uint32_t *bitmaps;
@@ -626,61 +693,82 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         (st = sc.get(&celem_ptr, (size_t)nbr + 1)) || (st = sc.get(&stmp, scan_tmp_elems(nbr))) ||
         (st = sc.get(&bitmaps, (size_t)nbr * nwords)) || (st = sc.get(&totals, 4)))
         return st;
-    cudaError_t e = cudaMemsetAsync(totals, 0, 4 * sizeof(unsigned long long), g_stream);
+    e = cudaMemsetAsync(totals, 0, 4 * sizeof(unsigned long long), g_stream);
     if (e == cudaSuccess) e = launch_symbolic_count(sa, prod_cnt, ccol_cnt, celem_cnt, bitmaps, totals, g_stream);
     if (e == cudaSuccess) e = launch_scan_i64(prod_cnt, prod_ptr, nbr, stmp, g_stream);
     if (e == cudaSuccess) e = launch_scan_i64(ccol_cnt, crow_ptr, nbr, stmp, g_stream);
     if (e == cudaSuccess) e = launch_scan_i64(celem_cnt, celem_ptr, nbr, stmp, g_stream);
     if ((st = cuda_check(e, "symbolic count"))) return st;
-    // pack sizes of the tensor-core operands, read with the symbolic totals
+    // pack sizes of the tensor-core operands, known with the symbolic totals
     Packed pkA, pkB;
     const bool tc = is_tc(opts.prec);
     if (tc) {
         if ((st = pack_prepare(sc, A, 0, 0, opts.prec, pkA))) return st;
         if ((st = pack_prepare(sc, B, 1, 0, opts.prec, pkB))) return st;
     }
-    // max C columns in a row: reuse a scan-free reduction on the host side
-    // (nbr values, small) -- read the whole ccol_cnt array
-    std::vector<int64_t> h_ccnt((size_t)nbr);
-    const int64_t zero = 0;
-    const int64_t *src[7] = {prod_ptr + nbr, crow_ptr + nbr, celem_ptr + nbr, (const int64_t *)totals,
-                             (const int64_t *)(totals + 1), tc ? pkA.off + A->nnzb : &zero,
-                             tc ? pkB.off + B->nnzb : &zero};
-    int nsrc = tc ? 7 : 5;
-    if (nbr > 0) {
-        e = cudaMemcpyAsync(h_ccnt.data(), ccol_cnt, sizeof(int64_t) * nbr, cudaMemcpyDeviceToHost, g_stream);
-        if ((st = cuda_check(e, "read counts"))) return st;
-    }
-    if ((st = read_words(src, nsrc))) return st;
-    const int64_t nprod = g_host[0], nnzbC = g_host[1], lenC = g_host[2];
-    const int64_t nfilt = g_host[3];
-    const int64_t mnk = g_host[4];
-    const int64_t packA_words = tc ? g_host[5] : 0, packB_words = tc ? g_host[6] : 0;
-    int64_t max_ccnt = 0;
-    for (int64_t v : h_ccnt) max_ccnt = std::max(max_ccnt, v);
-    if (nprod > INT32_MAX || nnzbC > INT32_MAX)
-        return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31-1 products or C blocks");
+    int64_t nprod, nnzbC, lenC, nfilt, mnk, packA_words = 0, packB_words = 0, max_ccnt = 0;
     int nchunk = 8;
-    while (nchunk > 1 && symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 160 * 1024) nchunk >>= 1;
-    if (symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 220 * 1024)
-        return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
+    if (no_sync) {
+        // sizes of the eager call; the device checks that they hold
+        nprod = pl.nprod; nnzbC = pl.nnzb; lenC = pl.len; nfilt = pl.nfilt; mnk = pl.mnk;
+        packA_words = pl.packA; packB_words = pl.packB; max_ccnt = pl.max_ccnt; nchunk = pl.nchunk;
+        PlanCheck pc{};
+        pc.actual[0] = prod_ptr + nbr; pc.expected[0] = nprod;
+        pc.actual[1] = crow_ptr + nbr; pc.expected[1] = nnzbC;
+        pc.actual[2] = celem_ptr + nbr; pc.expected[2] = lenC;
+        pc.actual[3] = (const int64_t *)(totals + 2); pc.expected[3] = max_ccnt; pc.at_most[3] = 1;
+        pc.n = 4;
+        if (tc) {
+            pc.actual[4] = pkA.off + A->nnzb; pc.expected[4] = packA_words;
+            pc.actual[5] = pkB.off + B->nnzb; pc.expected[5] = packB_words;
+            pc.n = 6;
+        }
+        if ((st = cuda_check(launch_check_plan(pc, C->status, g_stream), "plan check"))) return st;
+    } else {
+        std::vector<int64_t> h_ccnt((size_t)nbr);
+        const int64_t *src[7] = {prod_ptr + nbr, crow_ptr + nbr, celem_ptr + nbr, (const int64_t *)totals,
+                                 (const int64_t *)(totals + 1), tc ? pkA.off + A->nnzb : nullptr,
+                                 tc ? pkB.off + B->nnzb : nullptr};
+        if (nbr > 0) {
+            e = cudaMemcpyAsync(h_ccnt.data(), ccol_cnt, sizeof(int64_t) * nbr, cudaMemcpyDeviceToHost, g_stream);
+            if ((st = cuda_check(e, "read counts"))) return st;
+        }
+        if ((st = read_words(src, tc ? 7 : 5))) return st;
+        nprod = g_host[0]; nnzbC = g_host[1]; lenC = g_host[2]; nfilt = g_host[3]; mnk = g_host[4];
+        if (tc) {
+            packA_words = g_host[5];
+            packB_words = g_host[6];
+        }
+        for (int64_t v : h_ccnt) max_ccnt = std::max(max_ccnt, v);
+        if (nprod > INT32_MAX || nnzbC > INT32_MAX)
+            return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31-1 products or C blocks");
+        while (nchunk > 1 && symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 160 * 1024) nchunk >>= 1;
+        if (symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 220 * 1024)
+            return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
+    }
     ev.mark(2);
 
     // ---- a3: fill C's pattern and the product list
     int32_t *c_col = nullptr, *c_rc = nullptr, *pa = nullptr, *pb = nullptr, *pc = nullptr;
     int64_t *c_off = nullptr, *cptr = nullptr, *old_off = nullptr;
     void *c_data = nullptr;
-    if ((st = sc.get(&c_col, nnzbC)) || (st = sc.get(&c_off, nnzbC)) || (st = sc.get(&c_rc, nnzbC)) ||
-        (st = sc.get(&cptr, (size_t)nnzbC + 1)) || (st = sc.get(&pa, nprod)) || (st = sc.get(&pb, nprod)) ||
-        (st = sc.get(&pc, nprod)))
-        return st;
-    if (use_old && (st = sc.get(&old_off, nnzbC))) return st;
-    if ((st = dalloc(&c_data, (size_t)lenC * esize(C->dtype)))) return st;
-    sc.ptrs.push_back(c_data);
+    if (no_sync) {  // C's present storage has exactly these sizes
+        c_col = C->col_idx; c_off = C->blk_off; c_rc = C->blk_rc; cptr = C->cptr;
+        pa = C->pa; pb = C->pb; pc = C->pc; c_data = C->data;
+    } else {
+        if ((st = sc.get(&c_col, nnzbC)) || (st = sc.get(&c_off, nnzbC)) || (st = sc.get(&c_rc, nnzbC)) ||
+            (st = sc.get(&cptr, (size_t)nnzbC + 1)) || (st = sc.get(&pa, nprod)) || (st = sc.get(&pb, nprod)) ||
+            (st = sc.get(&pc, nprod)))
+            return st;
+        if (use_old && (st = sc.get(&old_off, nnzbC))) return st;
+        if ((st = dalloc(&c_data, (size_t)lenC * esize(C->dtype)))) return st;
+        sc.ptrs.push_back(c_data);
+    }
     FillOut fo{prod_ptr, crow_ptr, celem_ptr, c_col, c_off, c_rc, cptr, pa, pb, pc, old_off, (int32_t)max_ccnt, nchunk};
     e = launch_symbolic_fill(sa, bitmaps, fo, g_stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cptr + nnzbC, prod_ptr + nbr, sizeof(int64_t), cudaMemcpyDeviceToDevice, g_stream);
+    if (e == cudaSuccess && no_sync) e = launch_copy_i64_if_ok(nbr + 1, crow_ptr, C->row_ptr, C->status, g_stream);
     if ((st = cuda_check(e, "symbolic fill"))) return st;
     ev.mark(3);
 
@@ -688,7 +776,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     int32_t nshapes = 0;
     std::vector<int32_t> h_shapes;
     int64_t *stack_ptr = nullptr, *triples = nullptr;
-    if (opts.build_stacks && nprod > 0) {
+    if (!no_sync && opts.build_stacks && nprod > 0) {
         std::vector<int32_t> sizes;
         for (auto *v : {&A->h_row_bs, &A->h_col_bs, &B->h_col_bs}) sizes.insert(sizes.end(), v->begin(), v->end());
         std::sort(sizes.begin(), sizes.end());
@@ -742,8 +830,12 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
 
     // ---- a5/a6: numeric
     if (tc) {
-        if ((st = pack_fill(sc, A, 0, 0, opts.prec, pkA, packA_words))) return st;
-        if ((st = pack_fill(sc, B, 1, 0, opts.prec, pkB, packB_words))) return st;
+        if ((st = sc.get(&pkA.words, (size_t)packA_words + 16)) || (st = sc.get(&pkB.words, (size_t)packB_words + 16)))
+            return st;
+        e = launch_pack(A, 0, 0, opts.prec, pkA.off, pkA.words, no_sync ? C->status : nullptr, g_stream);
+        if (e == cudaSuccess)
+            e = launch_pack(B, 1, 0, opts.prec, pkB.off, pkB.words, no_sync ? C->status : nullptr, g_stream);
+        if ((st = cuda_check(e, "pack"))) return st;
     }
     NumericArgs na{};
     na.n_items = nnzbC;
@@ -764,17 +856,24 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.flush_every = opts.flush_every;
     na.x_pack = pkA.words; na.x_pack_off = pkA.off;
     na.y_pack = pkB.words; na.y_pack_off = pkB.off;
+    na.status = no_sync ? C->status : nullptr;
     if ((st = sc.get(&na.work_counter, 2))) return st;
     int32_t *order = nullptr;
-    if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order))) return st;
+    if (no_sync) {
+        order = C->item_order;
+    } else {
+        if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order))) return st;
+    }
     na.item_order = order;
     ev.mark(5);
     if ((st = cuda_check(launch_numeric(na, g_stream), "numeric"))) return st;
     ev.mark(6);
+    if (no_sync) return BSM_OK;  // C's storage, counts and plan are unchanged
 
     // ---- swap C's pattern (old arrays are freed stream-ordered after the numeric kernel)
     free_results(C);
     free_pattern(C);
+    C->item_order = order;
     C->row_ptr = crow_ptr;
     C->col_idx = c_col;
     C->blk_off = c_off;
@@ -795,13 +894,20 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     C->prod_A = A; C->prod_B = B;
     C->prod_A_nnzb = A->nnzb; C->prod_B_nnzb = B->nnzb;
     for (void *p : {(void *)crow_ptr, (void *)c_col, (void *)c_off, (void *)c_rc, c_data, (void *)cptr, (void *)pa,
-                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples})
+                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order})
         sc.release(p);
+    C->plan = bsm_mat::Plan{};
+    if (!use_old && !opts.post_filter) {
+        auto &P = C->plan;
+        P.kind = 1; P.A = A; P.B = B; P.A_nnzb = A->nnzb; P.B_nnzb = B->nnzb; P.eps = filter_eps;
+        P.prec = opts.prec; P.nprod = nprod; P.nnzb = nnzbC; P.len = lenC; P.max_ccnt = max_ccnt;
+        P.nfilt = nfilt; P.mnk = mnk; P.nchunk = nchunk; P.packA = packA_words; P.packB = packB_words;
+    }
 
     // ---- optional post filter (drops C blocks with norm <= eps)
     if (opts.post_filter && use_filter) {
         const int64_t before = C->nnzb;
-        if ((st = norm_filter_compact(C, filter_eps))) return st;
+        if ((st = filter_compact(C, filter_eps, false, nullptr, 0, 0, nullptr))) return st;
         if (C->nnzb != before) {
             // the product list no longer indexes C's blocks
             dfree(C->cptr); C->cptr = nullptr;
@@ -810,6 +916,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             dfree(C->pc); C->pc = nullptr;
             dfree(C->stack_ptr); C->stack_ptr = nullptr;
             dfree(C->triples); C->triples = nullptr;
+            dfree(C->item_order); C->item_order = nullptr;
             C->nshapes = 0;
             C->h_shapes.clear();
             C->prod_A = C->prod_B = nullptr;
@@ -987,9 +1094,12 @@ bsm_status bsm_get_stacks(bsm_t C, int32_t *nshapes, int64_t *nprod, int32_t *sh
 // --------------------------------------------------------------------------
 // add
 // --------------------------------------------------------------------------
-bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps) {
+bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps, const bsm_opts *opts_in) {
     if (!X || !Y || !Z) return set_error(BSM_ERR_ARG, "NULL matrix");
     if (Z == X || Z == Y) return set_error(BSM_ERR_ARG, "Z must differ from X and Y");
+    bsm_opts opts;
+    bsm_status st = check_opts(opts_in, &opts);
+    if (st) return st;
     if (X->dtype != Y->dtype || X->dtype != Z->dtype) return set_error(BSM_ERR_ARG, "X, Y and Z must share a dtype");
     if (X->nbr != Y->nbr || X->nbc != Y->nbc || X->nbr != Z->nbr || X->nbc != Z->nbc ||
         !same_vec(X->h_row_bs, Y->h_row_bs) || !same_vec(X->h_col_bs, Y->h_col_bs) ||
@@ -997,41 +1107,144 @@ bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_
         return set_error(BSM_ERR_BLOCKING, "X, Y and Z must share one blocking");
     if (!std::isfinite(a) || !std::isfinite(b) || std::isnan(filter_eps))
         return set_error(BSM_ERR_ARG, "a, b and eps must be finite");
-    bsm_status st = ensure_globals();
-    if (st) return st;
+    const bool no_sync = opts.no_sync != 0;
+    const auto &pl = Z->plan;
+    if (no_sync) {
+        if (pl.kind != 2 || pl.A != X || pl.B != Y || pl.A_nnzb != X->nnzb || pl.B_nnzb != Y->nnzb ||
+            pl.eps != filter_eps || !Z->add_xsrc || Z->add_a != a || Z->add_b != b)
+            return set_error(BSM_ERR_ARG, "no_sync needs an earlier eager add of the same X, Y, a, b and eps into Z");
+    } else if ((st = ensure_globals())) {
+        return st;
+    }
+    if ((st = ensure_status(Z))) return st;
     Scratch sc;
     const int32_t nbr = X->nbr;
+    const bool filt = filter_eps > 0.0;
     int64_t *ccnt, *celem, *zrow, *zelem, *stmp;
     if ((st = sc.get(&ccnt, nbr)) || (st = sc.get(&celem, nbr)) || (st = sc.get(&zrow, (size_t)nbr + 1)) ||
         (st = sc.get(&zelem, (size_t)nbr + 1)) || (st = sc.get(&stmp, scan_tmp_elems(nbr))))
         return st;
-    cudaError_t e = launch_add_count(X, Y, ccnt, celem, g_stream);
+    cudaError_t e = cudaMemsetAsync(Z->status, 0, sizeof(int32_t), g_stream);
+    if (e == cudaSuccess) e = launch_add_count(X, Y, ccnt, celem, g_stream);
     if (e == cudaSuccess) e = launch_scan_i64(ccnt, zrow, nbr, stmp, g_stream);
     if (e == cudaSuccess) e = launch_scan_i64(celem, zelem, nbr, stmp, g_stream);
     if ((st = cuda_check(e, "add count"))) return st;
-    const int64_t *src[2] = {zrow + nbr, zelem + nbr};
-    if ((st = read_words(src, 2))) return st;
-    const int64_t nnz = g_host[0], len = g_host[1];
+    int64_t nnz, len;
+    if (no_sync) {
+        nnz = pl.u_nnzb;
+        len = pl.u_len;
+        PlanCheck pc{};
+        pc.actual[0] = zrow + nbr; pc.expected[0] = nnz;
+        pc.actual[1] = zelem + nbr; pc.expected[1] = len;
+        pc.n = 2;
+        if ((st = cuda_check(launch_check_plan(pc, Z->status, g_stream), "plan check"))) return st;
+    } else {
+        const int64_t *src[2] = {zrow + nbr, zelem + nbr};
+        if ((st = read_words(src, 2))) return st;
+        nnz = g_host[0];
+        len = g_host[1];
+    }
+    // the union: straight into Z's storage when no filter follows in no-sync mode
+    const bool direct = no_sync && !filt;
     int32_t *zc, *zrc;
     int64_t *zo, *xs, *ys;
     void *zd;
-    if ((st = sc.get(&zc, nnz)) || (st = sc.get(&zo, nnz)) || (st = sc.get(&zrc, nnz)) || (st = sc.get(&xs, nnz)) ||
-        (st = sc.get(&ys, nnz)))
-        return st;
-    if ((st = dalloc(&zd, (size_t)len * esize(X->dtype)))) return st;
-    sc.ptrs.push_back(zd);
+    const int32_t *stat = no_sync ? Z->status : nullptr;
+    if (direct) {
+        zc = Z->col_idx; zrc = Z->blk_rc; zo = Z->blk_off; xs = Z->add_xsrc; ys = Z->add_ysrc; zd = Z->data;
+    } else {
+        if ((st = sc.get(&zc, nnz)) || (st = sc.get(&zo, nnz)) || (st = sc.get(&zrc, nnz)) || (st = sc.get(&xs, nnz)) ||
+            (st = sc.get(&ys, nnz)))
+            return st;
+        if ((st = dalloc(&zd, (size_t)len * esize(X->dtype)))) return st;
+        sc.ptrs.push_back(zd);
+        if (no_sync) {  // read by unguarded kernels of the filter even when the fill is skipped
+            e = cudaMemsetAsync(zo, 0, sizeof(int64_t) * nnz, g_stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(zrc, 0, sizeof(int32_t) * nnz, g_stream);
+            if ((st = cuda_check(e, "memset"))) return st;
+        }
+    }
     AddFill f{zrow, zelem, zc, zo, zrc, xs, ys};
-    e = launch_add_fill(X, Y, f, g_stream);
-    if (e == cudaSuccess) e = launch_add_values(nnz, zo, zrc, xs, ys, a, X->data, b, Y->data, zd, X->dtype, g_stream);
+    e = launch_add_fill(X, Y, f, stat, g_stream);
+    if (e == cudaSuccess) e = launch_add_values(nnz, zo, zrc, xs, ys, a, X->data, b, Y->data, zd, X->dtype, stat, g_stream);
+    if (e == cudaSuccess && direct) e = launch_copy_i64_if_ok(nbr + 1, zrow, Z->row_ptr, Z->status, g_stream);
     if ((st = cuda_check(e, "add fill"))) return st;
+    if (direct) return BSM_OK;
+    if (no_sync) {
+        // filter the union (scratch) into Z's storage; its row pointers are
+        // all zero (empty rows) unless the device check passed
+        int64_t *urow;
+        if ((st = sc.get(&urow, (size_t)nbr + 1))) return st;
+        e = cudaMemsetAsync(urow, 0, sizeof(int64_t) * (nbr + 1), g_stream);
+        if (e == cudaSuccess) e = launch_copy_i64_if_ok(nbr + 1, zrow, urow, Z->status, g_stream);
+        if ((st = cuda_check(e, "union rows"))) return st;
+        bsm_mat U;
+        U.nbr = nbr; U.nbc = X->nbc; U.dtype = X->dtype; U.nnzb = nnz; U.data_len = len;
+        U.row_bs = X->row_bs; U.col_bs = X->col_bs;
+        U.row_ptr = urow; U.col_idx = zc; U.blk_off = zo; U.blk_rc = zrc; U.data = zd;
+        U.add_xsrc = xs; U.add_ysrc = ys;
+        return filter_compact(&U, filter_eps, true, Z->status, pl.nnzb, pl.len, Z);
+    }
     free_results(Z);
     free_pattern(Z);
     Z->row_ptr = zrow; Z->col_idx = zc; Z->blk_off = zo; Z->blk_rc = zrc; Z->data = zd; Z->own_data = true;
     Z->nnzb = nnz; Z->data_len = len;
-    for (void *p : {(void *)zrow, (void *)zc, (void *)zo, (void *)zrc, zd}) sc.release(p);
-    if (filter_eps > 0.0) {
-        if ((st = norm_filter_compact(Z, filter_eps))) return st;
+    Z->add_xsrc = xs; Z->add_ysrc = ys;
+    Z->add_X = X; Z->add_Y = Y;
+    Z->add_X_nnzb = X->nnzb; Z->add_Y_nnzb = Y->nnzb;
+    Z->add_a = a; Z->add_b = b;
+    for (void *p : {(void *)zrow, (void *)zc, (void *)zo, (void *)zrc, zd, (void *)xs, (void *)ys}) sc.release(p);
+    if (filt && (st = filter_compact(Z, filter_eps, false, nullptr, 0, 0, nullptr))) return st;
+    auto &P = Z->plan;
+    P.kind = 2; P.A = X; P.B = Y; P.A_nnzb = X->nnzb; P.B_nnzb = Y->nnzb; P.eps = filter_eps;
+    P.u_nnzb = nnz; P.u_len = len; P.nnzb = Z->nnzb; P.len = Z->data_len;
+    return BSM_OK;
+}
+
+bsm_status bsm_add_backward(bsm_t Z, const void *dZ_data, bsm_t X, bsm_t Y, void *dX_data, void *dY_data) {
+    if (!Z || !X || !Y) return set_error(BSM_ERR_ARG, "NULL matrix");
+    if (!dX_data && !dY_data) return BSM_OK;
+    if (!dZ_data && Z->data_len) return set_error(BSM_ERR_ARG, "dZ_data is NULL");
+    if (Z->add_X != X || Z->add_Y != Y || Z->add_X_nnzb != X->nnzb || Z->add_Y_nnzb != Y->nnzb || !Z->add_xsrc)
+        return set_error(BSM_ERR_ARG, "Z does not hold the provenance of an add of these X and Y");
+    const size_t es = esize(Z->dtype);
+    cudaError_t e = cudaSuccess;
+    if (dX_data && X->data_len) e = cudaMemsetAsync(dX_data, 0, (size_t)X->data_len * es, g_stream);
+    if (e == cudaSuccess && dY_data && Y->data_len) e = cudaMemsetAsync(dY_data, 0, (size_t)Y->data_len * es, g_stream);
+    if (e == cudaSuccess)
+        e = launch_add_backward(Z->nnzb, Z->blk_off, Z->blk_rc, Z->add_xsrc, Z->add_ysrc, Z->add_a, Z->add_b, dZ_data,
+                                dX_data, dY_data, Z->dtype, g_stream);
+    return cuda_check(e, "add backward");
+}
+
+bsm_status bsm_get_status(bsm_t X, int32_t *status) {
+    if (!X || !status) return set_error(BSM_ERR_ARG, "NULL argument");
+    *status = 0;
+    if (!X->status) return BSM_OK;
+    cudaError_t e = cudaMemcpyAsync(g_host, X->status, sizeof(int32_t), cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    if (e != cudaSuccess) return cuda_check(e, "read status");
+    *status = *reinterpret_cast<int32_t *>(g_host);
+    if (*status & DEV_ERR_CAPACITY)
+        return set_error(BSM_ERR_CAPACITY, "the last no-sync call found sizes different from its eager call");
+    return BSM_OK;
+}
+
+bsm_status bsm_borrow_data(bsm_t X, void *dptr) {
+    if (!X) return set_error(BSM_ERR_ARG, "X is NULL");
+    if (!dptr && X->data_len) return set_error(BSM_ERR_ARG, "dptr is NULL");
+    if (dptr) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, dptr) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return set_error(BSM_ERR_ARG, "bsm_borrow_data needs a device pointer");
+        }
     }
+    if (X->own_data) dfree(X->data);
+    X->data = dptr;
+    X->own_data = false;
+    X->norms_valid = false;
     return BSM_OK;
 }
 

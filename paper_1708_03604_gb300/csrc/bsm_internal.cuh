@@ -71,6 +71,30 @@ struct bsm_mat {
     int64_t prod_A_nnzb = -1, prod_B_nnzb = -1;
     double timings[BSM_T_COUNT] = {0};
     bool timings_valid = false;
+
+    // device status word of the last call that wrote this matrix
+    int32_t *status = nullptr;
+    // sizes of the last eager call that wrote this matrix; a no-sync call
+    // with the same operands reuses them and this matrix's storage
+    struct Plan {
+        int kind = 0;  // 0 none, 1 multiply, 2 add
+        bsm_t A = nullptr, B = nullptr;
+        int64_t A_nnzb = -1, B_nnzb = -1;
+        double eps = 0.0;
+        int32_t prec = 0;
+        int64_t nprod = 0, nnzb = 0, len = 0, max_ccnt = 0, nfilt = 0, mnk = 0;
+        int32_t nchunk = 1;
+        int64_t packA = 0, packB = 0;
+        int64_t u_nnzb = 0, u_len = 0;  // add: union before the norm filter
+    } plan;
+    int32_t *item_order = nullptr;      // numeric processing order of the last eager multiply
+
+    // provenance of the last bsm_add that wrote this matrix (for its adjoint):
+    // per block, the element offset of the matching X / Y block or -1
+    int64_t *add_xsrc = nullptr, *add_ysrc = nullptr;
+    bsm_t add_X = nullptr, add_Y = nullptr;
+    int64_t add_X_nnzb = -1, add_Y_nnzb = -1;
+    double add_a = 0.0, add_b = 0.0;
 };
 
 namespace bsm {
@@ -116,10 +140,12 @@ struct SymbolicArgs {
     double eps;
     int use_filter;
     int32_t nwords;                      // ceil(nbc / 32)
+    const int32_t *status;               // nullable: kernels that read it do nothing when *status != 0
 };
 
 // Per block row: kept products, distinct C columns, C elements; bitmaps of
-// the C columns (nbr * nwords words); totals[0] += filtered, totals[1] += sum m*n*k.
+// the C columns (nbr * nwords words); totals[0] += filtered, totals[1] += sum m*n*k,
+// totals[2] = max over rows of the distinct C columns.
 cudaError_t launch_symbolic_count(const SymbolicArgs &a, int64_t *prod_cnt, int64_t *ccol_cnt,
                                   int64_t *celem_cnt, uint32_t *bitmaps,
                                   unsigned long long *totals, cudaStream_t s);
@@ -189,6 +215,7 @@ struct NumericArgs {
     const void *y_pack; const int64_t *y_pack_off;
     int32_t max_out_rows, max_out_cols;
     const int32_t *item_order;  // nullable: processing order of the items (grouped by block shape)
+    const int32_t *status;      // nullable: the kernel does nothing when *status != 0
     unsigned long long *work_counter;  // 8 bytes of device memory, zeroed by the launcher
 };
 cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s);
@@ -201,7 +228,19 @@ struct PackInfo {
 cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec, int64_t *pack_words,
                               cudaStream_t s);
 cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
-                        void *pack, cudaStream_t s);
+                        void *pack, const int32_t *status, cudaStream_t s);
+
+// *status |= DEV_ERR_CAPACITY unless, for q < n (n <= 8), actual[q] == expected[q]
+// (or actual[q] <= expected[q] where at_most[q] is set)
+struct PlanCheck {
+    const int64_t *actual[8];
+    int64_t expected[8];
+    int at_most[8];
+    int n;
+};
+cudaError_t launch_check_plan(const PlanCheck &c, int32_t *status, cudaStream_t s);
+// dst[0..n) = src[0..n) unless *status != 0
+cudaError_t launch_copy_i64_if_ok(int64_t n, const int64_t *src, int64_t *dst, const int32_t *status, cudaStream_t s);
 
 // ---------------------------------------------------------------- add
 cudaError_t launch_add_count(const bsm_mat *X, const bsm_mat *Y, int64_t *ccnt, int64_t *celem,
@@ -213,10 +252,12 @@ struct AddFill {
     int32_t *z_blk_rc;
     int64_t *x_src, *y_src;  // [nnzbZ] source block offsets or -1
 };
-cudaError_t launch_add_fill(const bsm_mat *X, const bsm_mat *Y, const AddFill &f, cudaStream_t s);
+cudaError_t launch_add_fill(const bsm_mat *X, const bsm_mat *Y, const AddFill &f, const int32_t *status,
+                            cudaStream_t s);
 cudaError_t launch_add_values(int64_t nnzb, const int64_t *z_blk_off, const int32_t *z_blk_rc,
                               const int64_t *x_src, const int64_t *y_src, double a, const void *x,
-                              double b, const void *y, void *z, int32_t dtype, cudaStream_t s);
+                              double b, const void *y, void *z, int32_t dtype, const int32_t *status,
+                              cudaStream_t s);
 
 // Post filter: keep flag per block (norm > eps), then compaction.
 cudaError_t launch_keep_flags(int64_t nnzb, const double *norms, double eps, int64_t *keep,
@@ -239,7 +280,15 @@ struct CompactArgs {
     int64_t *n_blk_off;
     int32_t *n_blk_rc;
     void *n_data;
+    const int32_t *status;      // nullable: nothing is written when *status != 0
 };
 cudaError_t launch_compact(const CompactArgs &c, cudaStream_t s);
+// dst[kscan[b]] = src[b] for every kept block b (kscan: exclusive scan of keep flags)
+cudaError_t launch_compact_i64(int64_t nnzb, const int64_t *kscan, const int64_t *src, int64_t *dst,
+                               const int32_t *status, cudaStream_t s);
+// adjoint of Z = a*X + b*Y: dX[xsrc+e] = a*dZ, dY[ysrc+e] = b*dZ (dX, dY zeroed by the caller)
+cudaError_t launch_add_backward(int64_t nnzb, const int64_t *z_blk_off, const int32_t *z_blk_rc,
+                                const int64_t *x_src, const int64_t *y_src, double a, double b, const void *dZ,
+                                void *dX, void *dY, int32_t dtype, cudaStream_t s);
 
 }  // namespace bsm

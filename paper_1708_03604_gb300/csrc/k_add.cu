@@ -82,8 +82,9 @@ __global__ void k_add_count(int32_t nbr, Pat x, Pat y, int64_t *ccnt, int64_t *c
 
 // per row: the union in column order (one lane merges the two sorted lists),
 // then element offsets by a warp scan
-__global__ void k_add_fill(int32_t nbr, Pat x, Pat y, AddFill f) {
+__global__ void k_add_fill(int32_t nbr, Pat x, Pat y, AddFill f, const int32_t *status) {
     const int lane = threadIdx.x & 31;
+    if (status && *status != 0) return;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = wid; i < nbr; i += nwarp) {
@@ -131,8 +132,10 @@ __global__ void k_add_fill(int32_t nbr, Pat x, Pat y, AddFill f) {
 // one rounded sum (no fused multiply-add)
 template <typename T>
 __global__ void k_add_values(int64_t nnzb, const int64_t *z_off, const int32_t *z_rc, const int64_t *xs,
-                             const int64_t *ys, double a, const T *x, double b, const T *y, T *z) {
+                             const int64_t *ys, double a, const T *x, double b, const T *y, T *z,
+                             const int32_t *status) {
     const int lane = threadIdx.x & 31;
+    if (status && *status != 0) return;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t q = wid; q < nnzb; q += nwarp) {
@@ -185,6 +188,7 @@ __global__ void k_row_keep_counts(int32_t nbr, const int64_t *row_ptr, const int
 template <typename T>
 __global__ void k_compact(CompactArgs c) {
     const int lane = threadIdx.x & 31;
+    if (c.status && *c.status != 0) return;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const T *src = static_cast<const T *>(c.data);
@@ -227,7 +231,58 @@ __global__ void k_compact(CompactArgs c) {
     }
 }
 
+__global__ void k_compact_i64(int64_t nnzb, const int64_t *kscan, const int64_t *src, int64_t *dst,
+                              const int32_t *status) {
+    if (status && *status != 0) return;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nnzb;
+         b += (int64_t)gridDim.x * blockDim.x)
+        if (kscan[b + 1] != kscan[b]) dst[kscan[b]] = src[b];
+}
+
+template <typename T>
+__global__ void k_add_backward(int64_t nnzb, const int64_t *z_off, const int32_t *z_rc, const int64_t *xs,
+                               const int64_t *ys, double a, double b, const T *dz, T *dx, T *dy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = wid; q < nnzb; q += nwarp) {
+        const int32_t rc = z_rc[q];
+        const int len = rc_rows(rc) * rc_cols(rc);
+        const int64_t xo = xs[q], yo = ys[q], zo = z_off[q];
+        for (int e = lane; e < len; e += 32) {
+            const double g = (double)dz[zo + e];
+            if (dx && xo >= 0) dx[xo + e] = (T)(a * g);
+            if (dy && yo >= 0) dy[yo + e] = (T)(b * g);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_compact_i64(int64_t nnzb, const int64_t *kscan, const int64_t *src, int64_t *dst,
+                               const int32_t *status, cudaStream_t s) {
+    if (nnzb == 0) return cudaSuccess;
+    k_compact_i64<<<grid_for(nnzb), kThreads, 0, s>>>(nnzb, kscan, src, dst, status);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_backward(int64_t nnzb, const int64_t *z_blk_off, const int32_t *z_blk_rc,
+                                const int64_t *x_src, const int64_t *y_src, double a, double b, const void *dZ,
+                                void *dX, void *dY, int32_t dtype, cudaStream_t s) {
+    if (nnzb == 0) return cudaSuccess;
+    const int g = grid_for(nnzb * 32);
+    if (dtype == BSM_FP64)
+        k_add_backward<double><<<g, kThreads, 0, s>>>(nnzb, z_blk_off, z_blk_rc, x_src, y_src, a, b,
+                                                       static_cast<const double *>(dZ), static_cast<double *>(dX),
+                                                       static_cast<double *>(dY));
+    else
+        k_add_backward<float><<<g, kThreads, 0, s>>>(nnzb, z_blk_off, z_blk_rc, x_src, y_src, a, b,
+                                                      static_cast<const float *>(dZ), static_cast<float *>(dX),
+                                                      static_cast<float *>(dY));
+    count_launch(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_add_count(const bsm_mat *X, const bsm_mat *Y, int64_t *ccnt, int64_t *celem,
                              cudaStream_t s) {
@@ -238,26 +293,29 @@ cudaError_t launch_add_count(const bsm_mat *X, const bsm_mat *Y, int64_t *ccnt, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_add_fill(const bsm_mat *X, const bsm_mat *Y, const AddFill &f, cudaStream_t s) {
+cudaError_t launch_add_fill(const bsm_mat *X, const bsm_mat *Y, const AddFill &f, const int32_t *status,
+                            cudaStream_t s) {
     if (X->nbr == 0) return cudaSuccess;
-    k_add_fill<<<grid_for((int64_t)X->nbr * 32), kThreads, 0, s>>>(X->nbr, pat_of(*X), pat_of(*Y), f);
+    k_add_fill<<<grid_for((int64_t)X->nbr * 32), kThreads, 0, s>>>(X->nbr, pat_of(*X), pat_of(*Y), f, status);
     count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_add_values(int64_t nnzb, const int64_t *z_blk_off, const int32_t *z_blk_rc,
                               const int64_t *x_src, const int64_t *y_src, double a, const void *x, double b,
-                              const void *y, void *z, int32_t dtype, cudaStream_t s) {
+                              const void *y, void *z, int32_t dtype, const int32_t *status, cudaStream_t s) {
     if (nnzb == 0) return cudaSuccess;
     const int g = grid_for(nnzb * 32);
     if (dtype == BSM_FP64)
         k_add_values<double><<<g, kThreads, 0, s>>>(nnzb, z_blk_off, z_blk_rc, x_src, y_src, a,
                                                      static_cast<const double *>(x), b,
-                                                     static_cast<const double *>(y), static_cast<double *>(z));
+                                                     static_cast<const double *>(y), static_cast<double *>(z),
+                                                     status);
     else
         k_add_values<float><<<g, kThreads, 0, s>>>(nnzb, z_blk_off, z_blk_rc, x_src, y_src, a,
                                                     static_cast<const float *>(x), b,
-                                                    static_cast<const float *>(y), static_cast<float *>(z));
+                                                    static_cast<const float *>(y), static_cast<float *>(z),
+                                                    status);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -130,6 +130,7 @@ __device__ __forceinline__ void cc_dispatch(const NumericArgs &a, int64_t q, int
 template <typename T>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
     const int lane = threadIdx.x & 31;
+    if (a.status && *a.status != 0) return;
     unsigned long long *ctr = a.work_counter;
     while (true) {
         int64_t q = 0;
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC>();
     unsigned long long *ctr = a.work_counter;
+    if (a.status && *a.status != 0) return;
     while (true) {
         int64_t q = 0;
         if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
@@ -514,8 +516,9 @@ __global__ void k_pack_sizes(int64_t nnzb, const int32_t *blk_rc, int role_y, in
 // one warp per block; lane L writes its fragment words of every tile
 template <typename T, int PREC>
 __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_rc, const T *data,
-                       int role_y, int trans, const int64_t *pack_off, uint32_t *pack) {
+                       int role_y, int trans, const int64_t *pack_off, uint32_t *pack, const int32_t *status) {
     using PT = PrecTraits<PREC>;
+    if (status && *status != 0) return;
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, t4 = lane & 3;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -656,7 +659,7 @@ cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec,
 }
 
 cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
-                        void *pack, cudaStream_t s) {
+                        void *pack, const int32_t *status, cudaStream_t s) {
     if (M->nnzb == 0) return cudaSuccess;
     int64_t g = (M->nnzb * 32 + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
@@ -666,11 +669,11 @@ cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const
     if (f64)                                                                                          \
         k_pack<double, PREC><<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc,              \
                                                          static_cast<const double *>(M->data), role_y, \
-                                                         trans, pack_off, p);                         \
+                                                         trans, pack_off, p, status);                         \
     else                                                                                              \
         k_pack<float, PREC><<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc,               \
                                                         static_cast<const float *>(M->data), role_y,   \
-                                                        trans, pack_off, p);
+                                                        trans, pack_off, p, status);
     if (prec == BSM_P_TF32x3) {
         BSM_PACK_CASE(BSM_P_TF32x3)
     } else if (prec == BSM_P_BF16x3) {

@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_count(SymbolicArgs a, int64_t 
         celem_cnt[i] = m * t[4];
         if (t[1]) atomicAdd(&totals[0], (unsigned long long)t[1]);
         if (t[2]) atomicAdd(&totals[1], (unsigned long long)(m * t[2]));
+        atomicMax(&totals[2], (unsigned long long)t[3]);
     }
 }
 
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) k_sym_fill(SymbolicArgs a, const uin
                                                        FillOut o) {
     extern __shared__ uint32_t smem[];
     __shared__ int32_t wtmp[32];
+    if (a.status && *a.status != 0) return;
     const int nw = a.nwords;
     uint32_t *bm = smem;
     int32_t *wpre = reinterpret_cast<int32_t *>(smem + nw);
@@ -494,6 +496,20 @@ __global__ void k_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32
     }
 }
 
+__global__ void k_check_plan(PlanCheck c, int32_t *status) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int q = 0; q < c.n; ++q)
+            if (c.at_most[q] ? (*c.actual[q] > c.expected[q]) : (*c.actual[q] != c.expected[q]))
+                atomicOr(status, (int32_t)DEV_ERR_CAPACITY);
+    }
+}
+
+__global__ void k_copy_i64_if_ok(int64_t n, const int64_t *src, int64_t *dst, const int32_t *status) {
+    if (*status != 0) return;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = src[p];
+}
+
 __global__ void k_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
                              const int32_t *table, uint32_t *keys, int32_t *iota) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
@@ -657,6 +673,20 @@ cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *sr
 cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_iota_keys<<<grid_for(n), kThreads, 0, s>>>(n, src, keys, iota);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_plan(const PlanCheck &c, int32_t *status, cudaStream_t s) {
+    k_check_plan<<<1, 32, 0, s>>>(c, status);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_i64_if_ok(int64_t n, const int64_t *src, int64_t *dst, const int32_t *status,
+                                  cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_copy_i64_if_ok<<<grid_for(n), kThreads, 0, s>>>(n, src, dst, status);
     count_launch(1);
     return cudaGetLastError();
 }
