@@ -156,17 +156,34 @@ def test_mcweeny_chain_vs_oracle(ag, oracle):
     assert xs_ref[-1].nnzb > w["X0"].nnzb
 
 
-def test_mcweeny_gradient_checkpointed(ag):
+def _chain_signature(ag, X0, steps, eps):
+    """Forward chain without autograd; returns the loss inputs and the keep
+    decisions of every step (kept products of both multiplies, blocks of X)."""
+    sig = []
+    X = X0
+    for _ in range(steps):
+        X2 = ag.matmul(X, X, eps=eps)
+        X3 = ag.matmul(X2, X, eps=eps)
+        X = ag.add(X2, X3, 3.0, -2.0, eps=eps)
+        sig.append((X2.handle.counts().products, X2.handle.counts().filtered, X3.handle.counts().products,
+                    X3.handle.counts().filtered, X.handle.nnzb))
+    return X, sig
+
+
+@pytest.mark.parametrize("eps_kind", ["unfiltered", "filtered"])
+def test_mcweeny_gradient_checkpointed(ag, eps_kind):
     """grad of trace(X_k.W) w.r.t. X0: checkpointing every 2 steps gives the
     same gradient as keeping every intermediate, and it matches central
-    finite differences."""
+    finite differences along directions whose +-h steps keep every filter
+    decision of the chain (the gradient is taken at fixed keep-decisions)."""
     import torch
     w = I.purification_start(nb=120)
-    steps, eps = 4, w["eps"]
+    steps = 4
+    eps = 0.0 if eps_kind == "unfiltered" else w["eps"]
     Wt = ag.BlockSparseTensor.from_bcsr(w["W"])
 
-    def loss_of(x0h, ckpt, grad=True):
-        X0 = ag.BlockSparseTensor.from_bcsr(x0h, requires_grad=grad)
+    def loss_of(x0h, ckpt):
+        X0 = ag.BlockSparseTensor.from_bcsr(x0h, requires_grad=True)
         Xk = ag.mcweeny(X0, steps, eps, checkpoint_every=ckpt)
         return ag.trace_product(Xk, Wt), X0
 
@@ -176,18 +193,28 @@ def test_mcweeny_gradient_checkpointed(ag):
     l2.backward()
     assert l1.item() == l2.item()
     torch.testing.assert_close(X1.data.grad, X2.data.grad, rtol=0, atol=0)
+    grad = X1.data.grad.cpu().numpy()
+    with torch.no_grad():
+        _, base_sig = _chain_signature(ag, ag.BlockSparseTensor.from_bcsr(w["X0"]), steps, eps)
     rng = np.random.default_rng(1)
-    h = 1e-6
-    an, fd = [], []
-    for _ in range(8):
+    # a smaller step where the chain filters: fewer near-threshold decisions flip
+    h = 1e-6 if eps == 0.0 else 1e-8
+    an, fd, skipped = [], [], 0
+    for _ in range(12):
         v = rng.standard_normal(len(w["X0"].data))
-        vals = []
-        for s in (1.0, -1.0):
+        vals, same = [], True
+        for sgn in (1.0, -1.0):
             xh = I.BCSR(w["X0"].row_bs, w["X0"].col_bs, w["X0"].row_ptr, w["X0"].col_idx, w["X0"].blk_off,
-                        w["X0"].data + s * h * v)
+                        w["X0"].data + sgn * h * v)
             with torch.no_grad():
-                vals.append(loss_of(xh, 0, grad=False)[0].item())
+                Xk, sig = _chain_signature(ag, ag.BlockSparseTensor.from_bcsr(xh), steps, eps)
+                vals.append(ag.trace_product(Xk, Wt).item())
+            same = same and sig == base_sig
+        if not same:
+            skipped += 1
+            continue
         fd.append((vals[0] - vals[1]) / (2 * h))
-        an.append(float((X1.data.grad.cpu().numpy() * v).sum()))
+        an.append(float((grad * v).sum()))
+    assert len(fd) >= 4, skipped
     an, fd = np.array(an), np.array(fd)
     assert np.linalg.norm(an - fd) / np.linalg.norm(fd) <= 1e-6
