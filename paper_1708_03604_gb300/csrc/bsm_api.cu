@@ -110,6 +110,9 @@ void free_pattern(bsm_mat *X) {
     dfree(X->norms); X->norms = nullptr;
     X->norms_valid = false;
     dfree(X->item_order); X->item_order = nullptr;
+    dfree(X->t_ptr); X->t_ptr = nullptr;
+    dfree(X->t_row); X->t_row = nullptr;
+    dfree(X->t_blk); X->t_blk = nullptr;
     X->nnzb = 0;
     X->data_len = 0;
 }
@@ -191,6 +194,42 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
     *order = out;
+    return BSM_OK;
+}
+
+// Column-major copy of X's pattern (kept on the handle until its pattern
+// changes): t_ptr[nbc+1], and for every block in column order (ascending
+// block row inside a column) its block row t_row and block index t_blk.
+bsm_status ensure_transpose(bsm_mat *X) {
+    if (X->t_ptr) return BSM_OK;
+    Scratch sc;
+    bsm_status st;
+    const int64_t n = X->nnzb;
+    int32_t *rows, *iota, *vals_alt;
+    uint32_t *keys, *keys_alt, *keys_sorted;
+    int64_t *rtmp, *counts, *stmp, *tptr;
+    int32_t *trow, *tblk;
+    if ((st = sc.get(&rows, n)) || (st = sc.get(&iota, n)) || (st = sc.get(&vals_alt, n)) || (st = sc.get(&keys, n)) ||
+        (st = sc.get(&keys_alt, n)) || (st = sc.get(&keys_sorted, n)) || (st = sc.get(&rtmp, radix_tmp_elems(n))) ||
+        (st = sc.get(&counts, X->nbc)) || (st = sc.get(&stmp, scan_tmp_elems(X->nbc))) ||
+        (st = sc.get(&tptr, (size_t)X->nbc + 1)) || (st = sc.get(&trow, n)) || (st = sc.get(&tblk, n)))
+        return st;
+    int bits = 1;
+    while ((1ll << bits) < (int64_t)X->nbc) ++bits;
+    cudaError_t e = launch_blk_rows(X, rows, g_stream);
+    if (e == cudaSuccess) e = launch_iota_keys(n, X->col_idx, keys, iota, g_stream);
+    if (e == cudaSuccess)
+        e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, tblk, n, bits, rtmp, g_stream);
+    if (e == cudaSuccess) e = launch_gather_i32(n, tblk, rows, trow, g_stream);
+    if (e == cudaSuccess) e = launch_histogram_u32(n, keys, X->nbc, counts, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(counts, tptr, X->nbc, stmp, g_stream);
+    if ((st = cuda_check(e, "transpose pattern"))) return st;
+    X->t_ptr = tptr;
+    X->t_row = trow;
+    X->t_blk = tblk;
+    sc.release(tptr);
+    sc.release(trow);
+    sc.release(tblk);
     return BSM_OK;
 }
 
@@ -765,7 +804,15 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         sc.ptrs.push_back(c_data);
     }
     FillOut fo{prod_ptr, crow_ptr, celem_ptr, c_col, c_off, c_rc, cptr, pa, pb, pc, old_off, (int32_t)max_ccnt, nchunk};
-    e = launch_symbolic_fill(sa, bitmaps, fo, g_stream);
+    // fill through B's columns when the k -> A block map fits in shared memory
+    const bool by_cols = symbolic_fill_cols_smem_bytes(nwords, (int32_t)max_ccnt, nbk) <= 200 * 1024;
+    if (by_cols) {
+        if (no_sync && !B->t_ptr) return set_error(BSM_ERR_ARG, "no_sync: B's column copy is missing");
+        if ((st = ensure_transpose(B))) return st;
+        e = launch_symbolic_fill_cols(sa, bitmaps, fo, B->t_ptr, B->t_row, B->t_blk, g_stream);
+    } else {
+        e = launch_symbolic_fill(sa, bitmaps, fo, g_stream);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cptr + nnzbC, prod_ptr + nbr, sizeof(int64_t), cudaMemcpyDeviceToDevice, g_stream);
     if (e == cudaSuccess && no_sync) e = launch_copy_i64_if_ok(nbr + 1, crow_ptr, C->row_ptr, C->status, g_stream);

@@ -88,6 +88,9 @@ struct bsm_mat {
         int64_t u_nnzb = 0, u_len = 0;  // add: union before the norm filter
     } plan;
     int32_t *item_order = nullptr;      // numeric processing order of the last eager multiply
+    // column-major copy of the pattern (built on demand, dropped with the pattern)
+    int64_t *t_ptr = nullptr;           // [nbc+1]
+    int32_t *t_row = nullptr, *t_blk = nullptr;  // [nnzb]
 
     // provenance of the last bsm_add that wrote this matrix (for its adjoint):
     // per block, the element offset of the matching X / Y block or -1
@@ -164,6 +167,13 @@ struct FillOut {
 cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
                                  cudaStream_t s);
 int64_t symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt, int nchunk);
+// Fill through B's columns (B transposed: bt_ptr[nbc+1], bt_k / bt_b = block row
+// and block index of every B block, column-major, ascending k inside a column).
+cudaError_t launch_symbolic_fill_cols(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
+                                      const int64_t *bt_ptr, const int32_t *bt_k, const int32_t *bt_b,
+                                      cudaStream_t s);
+int64_t symbolic_fill_cols_smem_bytes(int32_t nwords, int32_t max_ccnt, int32_t nbk);
+cudaError_t launch_blk_rows(const bsm_mat *X, int32_t *rows, cudaStream_t s);
 
 // Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits.
 // Buffers: keys/vals in and out may not alias; `tmp` needs

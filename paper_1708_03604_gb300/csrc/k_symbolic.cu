@@ -377,6 +377,126 @@ __global__ void __launch_bounds__(kThreads) k_sym_fill(SymbolicArgs a, const uin
     }
 }
 
+// Fill through B's columns.  Same outputs as k_sym_fill, but every C block
+// (i, j) is built by walking B's column j (B transposed: ascending k) against
+// a shared-memory map k -> A block of row i, so its products come out in
+// ascending k already and are written contiguously (coalesced) instead of
+// scattered across the row's C blocks.
+__global__ void __launch_bounds__(kThreads) k_sym_fill_cols(SymbolicArgs a, const uint32_t *bitmaps, FillOut o,
+                                                            const int64_t *bt_ptr, const int32_t *bt_k,
+                                                            const int32_t *bt_b) {
+    extern __shared__ uint32_t smem[];
+    __shared__ int32_t wtmp[32];
+    if (a.status && *a.status != 0) return;
+    const int nw = a.nwords;
+    uint32_t *bm = smem;
+    int32_t *wpre = reinterpret_cast<int32_t *>(smem + nw);
+    int32_t *cnt = wpre + nw;
+    int32_t *amap = cnt + o.max_ccnt;  // [nbk]: A block of row i in column k, or -1
+    const int i = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int64_t crow = o.crow_ptr[i];
+    const int32_t ccnt = (int32_t)(o.crow_ptr[i + 1] - crow);
+    const int64_t prow = o.prod_ptr[i];
+    const int32_t m = a.a_row_bs[i];
+
+    for (int w = tid; w < nw; w += blockDim.x) {
+        const uint32_t bits = bitmaps[(int64_t)i * nw + w];
+        bm[w] = bits;
+        wpre[w] = __popc(bits);
+    }
+    for (int32_t k = tid; k < a.nbk; k += blockDim.x) amap[k] = -1;
+    __syncthreads();
+    block_exscan_array(wpre, nw, wtmp);
+    const int64_t a_beg = a.a_row_ptr[i], a_end = a.a_row_ptr[i + 1];
+    for (int64_t ai = a_beg + tid; ai < a_end; ai += blockDim.x) amap[a.a_col_idx[ai]] = (int32_t)ai;
+    // C columns in ascending order, and their widths for the element offsets
+    for (int w = tid; w < nw; w += blockDim.x) {
+        uint32_t bits = bm[w];
+        int32_t r = wpre[w];
+        while (bits) {
+            const int bit = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int32_t j = w * 32 + bit;
+            o.c_col_idx[crow + r] = j;
+            cnt[r] = a.b_col_bs[j];
+            r++;
+        }
+    }
+    __syncthreads();
+    block_exscan_array(cnt, ccnt, wtmp);
+    const int64_t ebase = o.celem_ptr[i];
+    for (int32_t r = tid; r < ccnt; r += blockDim.x) {
+        const int32_t j = o.c_col_idx[crow + r];
+        const int32_t n = a.b_col_bs[j];
+        o.c_blk_off[crow + r] = ebase + (int64_t)m * cnt[r];
+        o.c_blk_rc[crow + r] = (m << 16) | n;
+        if (o.old_off) o.old_off[crow + r] = -1;
+    }
+    __syncthreads();
+    if (o.old_off) {
+        for (int64_t c = a.o_row_ptr[i] + tid; c < a.o_row_ptr[i + 1]; c += blockDim.x) {
+            const int32_t j = a.o_col_idx[c];
+            o.old_off[crow + col_rank(bm, wpre, j)] = a.o_blk_off[c];
+        }
+    }
+    // pass 1: kept products per C block (one warp per C block)
+    const unsigned lt = (1u << lane) - 1u;
+    for (int32_t r = warp; r < ccnt; r += nwarps) {
+        const int32_t j = o.c_col_idx[crow + r];
+        const int64_t cb = bt_ptr[j], ce = bt_ptr[j + 1];
+        int32_t total = 0;
+        for (int64_t e0 = cb; e0 < ce; e0 += 32) {
+            const int64_t e = e0 + lane;
+            bool keep = false;
+            if (e < ce) {
+                const int32_t ai = amap[bt_k[e]];
+                if (ai >= 0) keep = !a.use_filter || __dmul_rn(a.a_norm[ai], a.b_norm[bt_b[e]]) > a.eps;
+            }
+            total += __popc(__ballot_sync(0xffffffffu, keep));
+        }
+        if (lane == 0) cnt[r] = total;
+    }
+    __syncthreads();
+    block_exscan_array(cnt, ccnt, wtmp);
+    for (int32_t r = tid; r < ccnt; r += blockDim.x) o.cptr[crow + r] = prow + cnt[r];
+    // pass 2: write each C block's products contiguously, ascending k
+    for (int32_t r = warp; r < ccnt; r += nwarps) {
+        const int32_t j = o.c_col_idx[crow + r];
+        const int64_t cb = bt_ptr[j], ce = bt_ptr[j + 1];
+        int64_t cur = prow + cnt[r];
+        for (int64_t e0 = cb; e0 < ce; e0 += 32) {
+            const int64_t e = e0 + lane;
+            bool keep = false;
+            int32_t ai = -1, bi = -1;
+            if (e < ce) {
+                ai = amap[bt_k[e]];
+                if (ai >= 0) {
+                    bi = bt_b[e];
+                    keep = !a.use_filter || __dmul_rn(a.a_norm[ai], a.b_norm[bi]) > a.eps;
+                }
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int64_t pos = cur + __popc(msk & lt);
+                o.pa[pos] = ai;
+                o.pb[pos] = bi;
+                o.pc[pos] = (int32_t)(crow + r);
+            }
+            cur += __popc(msk);
+        }
+    }
+}
+
+// block row of every block
+__global__ void k_blk_rows(int32_t nbr, const int64_t *row_ptr, int32_t *rows) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = wid; i < nbr; i += nwarp)
+        for (int64_t b = row_ptr[i] + lane; b < row_ptr[i + 1]; b += 32) rows[b] = (int32_t)i;
+}
+
 // ------------------------------------------------------------- radix sort
 constexpr int kRadixRounds = 16;
 constexpr int kRadixTile = kThreads * kRadixRounds;
@@ -581,6 +701,31 @@ cudaError_t launch_symbolic_count(const SymbolicArgs &a, int64_t *prod_cnt, int6
 
 int64_t symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt, int nchunk) {
     return (2 * (int64_t)nwords + (int64_t)(nchunk + 1) * max_ccnt + 1) * (int64_t)sizeof(int32_t);
+}
+
+int64_t symbolic_fill_cols_smem_bytes(int32_t nwords, int32_t max_ccnt, int32_t nbk) {
+    return (2 * (int64_t)nwords + (int64_t)max_ccnt + nbk + 1) * (int64_t)sizeof(int32_t);
+}
+
+cudaError_t launch_symbolic_fill_cols(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
+                                      const int64_t *bt_ptr, const int32_t *bt_k, const int32_t *bt_b,
+                                      cudaStream_t s) {
+    if (a.nbr == 0) return cudaSuccess;
+    const int smem = (int)symbolic_fill_cols_smem_bytes(a.nwords, o.max_ccnt, a.nbk);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_sym_fill_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_sym_fill_cols<<<a.nbr, kThreads, smem, s>>>(a, bitmaps, o, bt_ptr, bt_k, bt_b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blk_rows(const bsm_mat *X, int32_t *rows, cudaStream_t s) {
+    if (X->nnzb == 0) return cudaSuccess;
+    k_blk_rows<<<grid_for((int64_t)X->nbr * 32), kThreads, 0, s>>>(X->nbr, X->row_ptr, rows);
+    count_launch(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
