@@ -110,6 +110,7 @@ void free_pattern(bsm_mat *X) {
     dfree(X->norms); X->norms = nullptr;
     X->norms_valid = false;
     dfree(X->item_order); X->item_order = nullptr;
+    dfree(X->row_rank); X->row_rank = nullptr;
     dfree(X->t_ptr); X->t_ptr = nullptr;
     dfree(X->t_row); X->t_row = nullptr;
     dfree(X->t_blk); X->t_blk = nullptr;
@@ -156,11 +157,78 @@ bsm_status pack_fill(Scratch &sc, const bsm_mat *M, int role_y, int trans, int p
     return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, nullptr, g_stream), "pack");
 }
 
+// Rank of every block row of X in a breadth-first order through shared block
+// columns: rows that have block columns in common come out close together (a
+// Cuthill-McKee-style ordering of the rows of X.X^T).  Only the numeric
+// kernels' schedule uses it, so that warps running at the same time read the
+// same operand blocks from L2.  Built on the host from X's pattern and kept
+// on the handle.
+bsm_status ensure_row_rank(bsm_mat *X) {
+    if (X->row_rank || X->nbr == 0) return BSM_OK;
+    const int32_t nbr = X->nbr, nbc = X->nbc;
+    std::vector<int64_t> rp((size_t)nbr + 1);
+    std::vector<int32_t> ci((size_t)X->nnzb);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), X->row_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess && X->nnzb)
+        e = cudaMemcpyAsync(ci.data(), X->col_idx, sizeof(int32_t) * X->nnzb, cudaMemcpyDeviceToHost, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    bsm_status st;
+    if ((st = cuda_check(e, "read pattern"))) return st;
+    // column -> rows
+    std::vector<int64_t> cp((size_t)nbc + 1, 0);
+    for (int32_t c : ci) cp[(size_t)c + 1]++;
+    for (int32_t c = 0; c < nbc; ++c) cp[c + 1] += cp[c];
+    std::vector<int32_t> cr((size_t)X->nnzb);
+    {
+        std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
+        for (int32_t r = 0; r < nbr; ++r)
+            for (int64_t b = rp[r]; b < rp[r + 1]; ++b) cr[pos[ci[b]]++] = r;
+    }
+    std::vector<int32_t> seed((size_t)nbr);
+    for (int32_t r = 0; r < nbr; ++r) seed[r] = r;
+    std::stable_sort(seed.begin(), seed.end(), [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] < rp[y + 1] - rp[y]; });
+    std::vector<char> vrow((size_t)nbr, 0), vcol((size_t)nbc, 0);
+    std::vector<int32_t> rank((size_t)nbr), queue;
+    queue.reserve(nbr);
+    int32_t next = 0;
+    for (int32_t s0 : seed) {
+        if (vrow[s0]) continue;
+        vrow[s0] = 1;
+        size_t head = queue.size();
+        queue.push_back(s0);
+        while (head < queue.size()) {
+            const int32_t r = queue[head++];
+            rank[r] = next++;
+            for (int64_t b = rp[r]; b < rp[r + 1]; ++b) {
+                const int32_t c = ci[b];
+                if (vcol[c]) continue;
+                vcol[c] = 1;
+                for (int64_t q = cp[c]; q < cp[c + 1]; ++q)
+                    if (!vrow[cr[q]]) {
+                        vrow[cr[q]] = 1;
+                        queue.push_back(cr[q]);
+                    }
+            }
+        }
+    }
+    int32_t *d = nullptr;
+    if ((st = dalloc_t(&d, nbr))) return st;
+    e = cudaMemcpyAsync(d, rank.data(), sizeof(int32_t) * nbr, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    if ((st = cuda_check(e, "upload row order"))) {
+        dfree(d);
+        return st;
+    }
+    X->row_rank = d;
+    return BSM_OK;
+}
+
 // Processing order of n output blocks for the numeric kernels: grouped by
 // block shape, larger blocks first, so that neighbouring warps run the same
 // code path and the heaviest items start early.
 bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std::vector<int32_t> &rsz,
-                       const std::vector<int32_t> &csz, int32_t **order) {
+                       const std::vector<int32_t> &csz, int32_t **order, const bsm_mat *rows_of = nullptr,
+                       const int32_t *row_rank = nullptr) {
     *order = nullptr;
     if (n <= 1) return BSM_OK;
     std::vector<int32_t> sizes(rsz);
@@ -176,20 +244,29 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
         for (int32_t c = 0; c < ns; ++c) cls.emplace_back(-(int64_t)sizes[r] * sizes[c], r * ns + c);
     std::sort(cls.begin(), cls.end());
     for (size_t q = 0; q < cls.size(); ++q) table[cls[q].second] = (int32_t)q;
+    const int32_t nbr = rows_of ? rows_of->nbr : 0;
+    if (row_rank && (int64_t)table.size() * std::max(nbr, 1) >= (int64_t(1) << 31)) row_rank = nullptr;
     int bits = 1;
-    while ((1ll << bits) < (int64_t)table.size()) ++bits;
+    while ((1ll << bits) < (int64_t)table.size() * (row_rank ? nbr : 1)) ++bits;
     bsm_status st;
-    int32_t *d_sidx, *d_table, *iota, *vals_alt, *out;
+    int32_t *d_sidx, *d_table, *iota, *vals_alt, *out, *brow = nullptr;
     uint32_t *keys, *keys_alt, *keys_sorted;
     int64_t *rtmp;
     if ((st = sc.get(&d_sidx, sidx.size())) || (st = sc.get(&d_table, table.size())) || (st = sc.get(&iota, n)) ||
         (st = sc.get(&vals_alt, n)) || (st = sc.get(&out, n)) || (st = sc.get(&keys, n)) ||
         (st = sc.get(&keys_alt, n)) || (st = sc.get(&keys_sorted, n)) || (st = sc.get(&rtmp, radix_tmp_elems(n))))
         return st;
+    if (row_rank && (st = sc.get(&brow, n))) return st;
     cudaError_t e = cudaMemcpyAsync(d_sidx, sidx.data(), sizeof(int32_t) * sidx.size(), cudaMemcpyHostToDevice, g_stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_table, table.data(), sizeof(int32_t) * table.size(), cudaMemcpyHostToDevice, g_stream);
-    if (e == cudaSuccess) e = launch_class_keys(n, blk_rc, d_sidx, ns, d_table, keys, iota, g_stream);
+    if (e == cudaSuccess && row_rank) {
+        bsm_mat view;  // rows of the output blocks
+        view.nbr = rows_of->nbr; view.nnzb = n; view.row_ptr = rows_of->row_ptr;
+        e = launch_blk_rows(&view, brow, g_stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_class_keys(n, blk_rc, d_sidx, ns, d_table, brow, row_rank, nbr, keys, iota, g_stream);
     if (e == cudaSuccess)
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
@@ -909,7 +986,11 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (no_sync) {
         order = C->item_order;
     } else {
-        if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order))) return st;
+        if ((st = ensure_row_rank(A))) return st;
+        bsm_mat rows_view;
+        rows_view.nbr = nbr;
+        rows_view.row_ptr = crow_ptr;
+        if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank))) return st;
     }
     na.item_order = order;
     ev.mark(5);

@@ -88,6 +88,9 @@ struct bsm_mat {
         int64_t u_nnzb = 0, u_len = 0;  // add: union before the norm filter
     } plan;
     int32_t *item_order = nullptr;      // numeric processing order of the last eager multiply
+    // rank of every block row in a breadth-first order through shared block
+    // columns (built on demand, dropped with the pattern); schedules numeric work
+    int32_t *row_rank = nullptr;        // [nbr]
     // column-major copy of the pattern (built on demand, dropped with the pattern)
     int64_t *t_ptr = nullptr;           // [nbc+1]
     int32_t *t_row = nullptr, *t_blk = nullptr;  // [nnzb]
@@ -198,9 +201,11 @@ cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *sr
                               cudaStream_t s);
 cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota,
                              cudaStream_t s);
-// Shape-class key of every block: table[size_index[rows] * ns + size_index[cols]].
+// Scheduling key of every block: table[size_index[rows] * ns + size_index[cols]] * nbr
+// + row_rank[block row] (row_rank may be null: key = class only).
 cudaError_t launch_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
-                              const int32_t *table, uint32_t *keys, int32_t *iota, cudaStream_t s);
+                              const int32_t *table, const int32_t *blk_row, const int32_t *row_rank, int32_t nbr,
+                              uint32_t *keys, int32_t *iota, cudaStream_t s);
 
 // ---------------------------------------------------------------- numeric
 struct NumericArgs {
