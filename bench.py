@@ -298,7 +298,8 @@ def main():
     if not args.no_split:
         ref_norm = torch.linalg.vector_norm(C64).item()
         for key, prec, fl in (("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
-                              ("tf32x3_fp64sum", "tf32x3", 1)):
+                              ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2),
+                              ("tf32x3_pair4", "tf32x3", -4), ("bf16x6_pair4", "bf16x6", -4)):
             step(prec, fl)
             torch.cuda.synchronize()
             bsm.bsm_set_profiling(True)

@@ -67,9 +67,12 @@ typedef struct {
     int32_t prec;          /* bsm_prec                                              */
     int32_t post_filter;   /* 1: after the multiply drop C blocks with norm <= eps   */
     int32_t build_stacks;  /* 1: also bucket the products by (m,n,k) (bsm_get_stacks) */
-    int32_t flush_every;   /* split paths: 0 = compensated FP32-pair sum of the block
-                              products (FP64 at the end); F > 0 = FP64 running sum
-                              refreshed every F block products                     */
+    int32_t flush_every;   /* split paths: how the FP32 partial sums of the block
+                              products are combined.  F > 0: FP64 running sum
+                              refreshed every F block products; F < 0:
+                              compensated FP32 pair (TwoSum) refreshed every -F
+                              products, converted to FP64 at the end; 0: as -1.
+                              Range [-1024, 1024].                                 */
     int32_t no_sync;       /* 1: no host synchronisation (CUDA-graph capturable); see
                               bsm_multiply and bsm_add                               */
     int32_t reserved[3];   /* must be zero                                          */

@@ -123,7 +123,7 @@ bsm_status check_opts(const bsm_opts *o, bsm_opts *out) {
     if (!o) return BSM_OK;
     *out = *o;
     if (o->prec < BSM_P_FP64 || o->prec > BSM_P_BF16x6) return set_error(BSM_ERR_ARG, "opts.prec out of range");
-    if (o->flush_every < 0) return set_error(BSM_ERR_ARG, "opts.flush_every < 0");
+    if (o->flush_every < -1024 || o->flush_every > 1024) return set_error(BSM_ERR_ARG, "opts.flush_every outside [-1024, 1024]");
     if (o->no_sync != 0 && o->no_sync != 1) return set_error(BSM_ERR_ARG, "opts.no_sync must be 0 or 1");
     for (int q = 0; q < 3; ++q)
         if (o->reserved[q] != 0) return set_error(BSM_ERR_ARG, "opts.reserved must be zero");

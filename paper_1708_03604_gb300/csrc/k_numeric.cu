@@ -217,8 +217,8 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
 
 // One pass over a super tile of MTC x NTC (at most 2 x 3) fragment tiles
 // starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
-// FF: cross-product sum as a float-float pair (TwoSum after every block
-// product); otherwise an FP64 sum refreshed every `flush_every` products.
+// FF: cross-product sum as a float-float pair (TwoSum after every |F| block
+// products); otherwise an FP64 sum refreshed every F products.
 template <int PREC, int MTC, int NTC, bool FF>
 __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
                                         uint32_t *ring) {
@@ -231,7 +231,9 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
     const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
     const uint32_t *XP = static_cast<const uint32_t *>(a.x_pack);
     const uint32_t *YP = static_cast<const uint32_t *>(a.y_pack);
-    const int F = a.flush_every > 0 ? a.flush_every : 1;
+    // FP64 mode: flush_every > 0 products per FP64 add; compensated mode:
+    // |flush_every| products per TwoSum (0 means 1)
+    const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
     uint32_t *myring = ring + lane * SW;          // stage st at myring + st * 32 * SW
     const uint32_t ring_s = smem_addr(myring);
 
