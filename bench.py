@@ -293,9 +293,13 @@ def main():
                 "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2070 MHz"}
     C64 = Cm.data_tensor()
 
-    # ---------------- split-precision legs
+    # ---------------- split-precision legs (variants per block shape autotuned first)
     split = {}
+    tuned = {}
     if not args.no_split:
+        from paper_1708_03604_gb300 import autotune
+        for prec in ("tf32x3", "bf16x6", "bf16x3"):
+            tuned[prec] = autotune.tune(A, B, eps, prec=prec, reps=2)
         ref_norm = torch.linalg.vector_norm(C64).item()
         for key, prec, fl in (("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
                               ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2),
@@ -396,7 +400,7 @@ def main():
                 "config": config({"products": cnt.products, "filtered": cnt.filtered, "useful_flop": flop,
                                   "c_blocks": Cm.nnzb, "parallelism": "replicas" if world > 1 else "single GPU"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk, "split_precision": split, "parity_sample": parity,
+                "clocks": clk, "split_precision": split, "split_autotune": tuned, "parity_sample": parity,
                 "phase_ms_last_fp64_step": phases}
         print(json.dumps(line), flush=True)
     if world > 1:

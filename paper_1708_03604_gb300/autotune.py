@@ -1,0 +1,87 @@
+"""Autotuner for the split-precision numeric kernel.
+
+For every output block shape (m, n) that a multiply produces, the split
+paths can run the block products either as tensor-core MMAs on packed
+fragments (variant 0) or as the same narrow pieces multiplied with FP32 FMA
+on CUDA cores (variant 1).  Which is faster depends on the shape (small
+blocks leave most of an MMA tile idle) and on the product mix, so it is
+measured: starting from all-MMA, each shape in turn is switched to the
+CUDA-core variant and kept there if the numeric kernel (timed with CUDA
+events by the library) gets faster.  The table is process-wide in libbsm
+and can be saved to / loaded from JSON.
+"""
+from __future__ import annotations
+
+import json
+import statistics
+
+import numpy as np
+
+from . import bsm
+
+
+def _shapes(A: bsm.Matrix, B: bsm.Matrix):
+    ms = sorted(set(int(x) for x in np.asarray(A.row_bs)))
+    ns = sorted(set(int(x) for x in np.asarray(B.col_bs)))
+    return sorted(((m, n) for m in ms for n in ns), key=lambda t: (t[0] * t[1], t))
+
+
+def _numeric_ms(A, B, eps, prec, reps, Cm):
+    t = []
+    for _ in range(reps):
+        bsm.multiply(1.0, A, B, 0.0, Cm, eps, prec=prec, build_stacks=False)
+        t.append(Cm.timings()["numeric"])
+    return statistics.median(t)
+
+
+def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", reps: int = 3,
+         gain: float = 0.01) -> dict:
+    """Choose the variant of every output shape of A.B for `prec`; returns
+    {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}."""
+    shapes = _shapes(A, B)
+    for m, n in shapes:
+        bsm.bsm_set_variant(prec, m, n, 0)
+    Cm = bsm.Matrix.empty(A.row_bs, B.col_bs)
+    bsm.bsm_set_profiling(True)
+    try:
+        _numeric_ms(A, B, eps, prec, 1, Cm)  # warm-up
+        best = _numeric_ms(A, B, eps, prec, reps, Cm)
+        start = best
+        chosen = {}
+        for m, n in shapes:
+            bsm.bsm_set_variant(prec, m, n, 1)
+            t = _numeric_ms(A, B, eps, prec, reps, Cm)
+            if t < best * (1.0 - gain):
+                best = t
+                chosen[f"{m}x{n}"] = 1
+            else:
+                bsm.bsm_set_variant(prec, m, n, 0)
+                chosen[f"{m}x{n}"] = 0
+    finally:
+        bsm.bsm_set_profiling(False)
+    return {"prec": prec, "variants": chosen, "numeric_ms": {"all_mma": start, "tuned": best}}
+
+
+def apply(table: dict):
+    for key, v in table["variants"].items():
+        m, n = (int(x) for x in key.split("x"))
+        bsm.bsm_set_variant(table["prec"], m, n, int(v))
+
+
+def reset(prec: str, sizes):
+    for m in sizes:
+        for n in sizes:
+            bsm.bsm_set_variant(prec, int(m), int(n), 0)
+
+
+def save(tables, path: str):
+    with open(path, "w") as f:
+        json.dump(tables, f, indent=1, sort_keys=True)
+
+
+def load(path: str):
+    with open(path) as f:
+        tables = json.load(f)
+    for t in (tables if isinstance(tables, list) else [tables]):
+        apply(t)
+    return tables

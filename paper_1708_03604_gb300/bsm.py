@@ -35,7 +35,7 @@ EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_lau
            "bsm_copy_data", "bsm_set_data", "bsm_data_ptr", "bsm_block_norms", "bsm_multiply",
            "bsm_multiply_backward", "bsm_get_counts", "bsm_get_timings", "bsm_get_products",
            "bsm_get_stacks", "bsm_add", "bsm_count_products_static", "bsm_borrow_data", "bsm_add_backward",
-           "bsm_get_status"]
+           "bsm_get_status", "bsm_set_variant", "bsm_get_variant"]
 
 
 class BsmError(RuntimeError):
@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
         "bsm_get_stacks": ([_vp, _P(_i32), _P(_i64), _vp, _vp, _vp], _i32),
         "bsm_add": ([_f64, _vp, _f64, _vp, _vp, _f64, _P(Opts)], _i32),
         "bsm_get_status": ([_vp, _P(_i32)], _i32),
+        "bsm_set_variant": ([_i32, _i32, _i32, _i32], _i32),
+        "bsm_get_variant": ([_i32, _i32, _i32, _P(_i32)], _i32),
         "bsm_count_products_static": ([_vp, _vp, _f64, _vp, _vp, _vp], _i32),
         "bsm_borrow_data": ([_vp, _vp], _i32),
         "bsm_add_backward": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
@@ -192,6 +194,16 @@ def bsm_multiply_backward(alpha, Cm: int, dC_ptr, A: int, B: int, dA_ptr, dB_ptr
 
 def bsm_add(a, X: int, b, Y: int, Z: int, filter_eps, opts: Opts | None = None):
     _check(lib().bsm_add(float(a), X, float(b), Y, Z, float(filter_eps), C.byref(opts) if opts is not None else None))
+
+
+def bsm_set_variant(prec, m: int, n: int, variant: int):
+    _check(lib().bsm_set_variant(PREC[prec] if isinstance(prec, str) else int(prec), int(m), int(n), int(variant)))
+
+
+def bsm_get_variant(prec, m: int, n: int) -> int:
+    v = _i32()
+    _check(lib().bsm_get_variant(PREC[prec] if isinstance(prec, str) else int(prec), int(m), int(n), C.byref(v)))
+    return v.value
 
 
 def bsm_get_status(X: int) -> int:

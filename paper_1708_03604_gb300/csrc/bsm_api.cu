@@ -21,6 +21,9 @@ cudaStream_t g_stream = nullptr;
 bool g_prof = false;
 bool g_pool_configured = false;
 int64_t *g_host = nullptr;  // pinned host words for small device->host reads
+// numeric variant of the split paths per (precision, rows, cols) of the output
+// block: 0 = tensor-core fragments, 1 = CUDA-core split arithmetic
+int8_t g_variant[5][kMaxBlockDim + 1][kMaxBlockDim + 1] = {};
 std::atomic<int64_t> g_launches{0};
 
 struct Scratch {
@@ -228,7 +231,8 @@ bsm_status ensure_row_rank(bsm_mat *X) {
 // code path and the heaviest items start early.
 bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std::vector<int32_t> &rsz,
                        const std::vector<int32_t> &csz, int32_t **order, const bsm_mat *rows_of = nullptr,
-                       const int32_t *row_rank = nullptr) {
+                       const int32_t *row_rank = nullptr, int prec = -1, bool *uses_cores = nullptr) {
+    if (uses_cores) *uses_cores = false;
     *order = nullptr;
     if (n <= 1) return BSM_OK;
     std::vector<int32_t> sizes(rsz);
@@ -270,6 +274,24 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     if (e == cudaSuccess)
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
+    if (prec >= 0 && uses_cores) {
+        std::vector<int8_t> var((size_t)ns * ns, 0);
+        bool any = false;
+        for (int32_t r = 0; r < ns; ++r)
+            for (int32_t c = 0; c < ns; ++c) {
+                var[(size_t)r * ns + c] = g_variant[prec][sizes[r]][sizes[c]];
+                any = any || var[(size_t)r * ns + c];
+            }
+        if (any) {
+            int8_t *d_var;
+            if ((st = sc.get(&d_var, var.size()))) return st;
+            e = cudaMemcpyAsync(d_var, var.data(), var.size(), cudaMemcpyHostToDevice, g_stream);
+            if (e == cudaSuccess) e = launch_mark_variant(n, out, blk_rc, d_sidx, ns, d_var, g_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);  // var is pageable and local
+            if ((st = cuda_check(e, "variant marks"))) return st;
+            *uses_cores = true;
+        }
+    }
     *order = out;
     return BSM_OK;
 }
@@ -983,14 +1005,31 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.status = no_sync ? C->status : nullptr;
     if ((st = sc.get(&na.work_counter, 2))) return st;
     int32_t *order = nullptr;
+    bool uses_cores = false;
     if (no_sync) {
         order = C->item_order;
+        uses_cores = pl.uses_cores;
     } else {
         if ((st = ensure_row_rank(A))) return st;
         bsm_mat rows_view;
         rows_view.nbr = nbr;
         rows_view.row_ptr = crow_ptr;
-        if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank))) return st;
+        if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
+                              tc ? opts.prec : -1, &uses_cores)))
+            return st;
+    }
+    if (tc && uses_cores) {  // unpacked pieces for the CUDA-core variant
+        const int np = split_pieces(opts.prec);
+        float *xp = nullptr, *yp = nullptr;
+        if ((st = sc.get(&xp, (size_t)A->data_len * np))) return st;
+        e = launch_split_plain(A, opts.prec, xp, g_stream);
+        if (e == cudaSuccess && B != A) {
+            if ((st = sc.get(&yp, (size_t)B->data_len * np))) return st;
+            e = launch_split_plain(B, opts.prec, yp, g_stream);
+        }
+        if ((st = cuda_check(e, "split pieces"))) return st;
+        na.x_plain = xp;
+        na.y_plain = B == A ? xp : yp;
     }
     na.item_order = order;
     ev.mark(5);
@@ -1029,6 +1068,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         auto &P = C->plan;
         P.kind = 1; P.A = A; P.B = B; P.A_nnzb = A->nnzb; P.B_nnzb = B->nnzb; P.eps = filter_eps;
         P.prec = opts.prec; P.nprod = nprod; P.nnzb = nnzbC; P.len = lenC; P.max_ccnt = max_ccnt;
+        P.uses_cores = uses_cores;
         P.nfilt = nfilt; P.mnk = mnk; P.nchunk = nchunk; P.packA = packA_words; P.packB = packB_words;
     }
 
@@ -1166,7 +1206,21 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;
         if ((st = sc.get(&na.work_counter, 2))) return st;
         int32_t *item_order = nullptr;
-        if ((st = shape_order(sc, OUT->nnzb, OUT->blk_rc, OUT->h_row_bs, OUT->h_col_bs, &item_order))) return st;
+        bool uses_cores = false;
+        if ((st = shape_order(sc, OUT->nnzb, OUT->blk_rc, OUT->h_row_bs, OUT->h_col_bs, &item_order, nullptr, nullptr,
+                              tc ? opts.prec : -1, &uses_cores)))
+            return st;
+        if (tc && uses_cores && nprod > 0) {
+            const int np = split_pieces(opts.prec);
+            float *xp = nullptr, *yp = nullptr;
+            cudaError_t e;
+            if ((st = sc.get(&xp, (size_t)X->data_len * np)) || (st = sc.get(&yp, (size_t)Y->data_len * np))) return st;
+            e = launch_split_plain(X, opts.prec, xp, g_stream);
+            if (e == cudaSuccess) e = launch_split_plain(Y, opts.prec, yp, g_stream);
+            if ((st = cuda_check(e, "split pieces"))) return st;
+            na.x_plain = xp;
+            na.y_plain = yp;
+        }
         na.item_order = item_order;
         if ((st = cuda_check(launch_numeric(na, g_stream), "adjoint numeric"))) return st;
     }
@@ -1343,6 +1397,21 @@ bsm_status bsm_add_backward(bsm_t Z, const void *dZ_data, bsm_t X, bsm_t Y, void
         e = launch_add_backward(Z->nnzb, Z->blk_off, Z->blk_rc, Z->add_xsrc, Z->add_ysrc, Z->add_a, Z->add_b, dZ_data,
                                 dX_data, dY_data, Z->dtype, g_stream);
     return cuda_check(e, "add backward");
+}
+
+bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant) {
+    if (prec < BSM_P_FP64 || prec > BSM_P_BF16x6 || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim ||
+        variant < 0 || variant > 1)
+        return set_error(BSM_ERR_ARG, "bsm_set_variant: argument out of range");
+    g_variant[prec][m][n] = (int8_t)variant;
+    return BSM_OK;
+}
+
+bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant) {
+    if (!variant || prec < BSM_P_FP64 || prec > BSM_P_BF16x6 || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim)
+        return set_error(BSM_ERR_ARG, "bsm_get_variant: argument out of range");
+    *variant = g_variant[prec][m][n];
+    return BSM_OK;
 }
 
 bsm_status bsm_get_status(bsm_t X, int32_t *status) {

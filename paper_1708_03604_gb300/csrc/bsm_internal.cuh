@@ -85,6 +85,7 @@ struct bsm_mat {
         int64_t nprod = 0, nnzb = 0, len = 0, max_ccnt = 0, nfilt = 0, mnk = 0;
         int32_t nchunk = 1;
         int64_t packA = 0, packB = 0;
+        bool uses_cores = false;  // some items run the CUDA-core split variant
         int64_t u_nnzb = 0, u_len = 0;  // add: union before the norm filter
     } plan;
     int32_t *item_order = nullptr;      // numeric processing order of the last eager multiply
@@ -228,6 +229,8 @@ struct NumericArgs {
     // pre-split operand planes (tensor-core paths)
     const void *x_pack; const int64_t *x_pack_off;
     const void *y_pack; const int64_t *y_pack_off;
+    // unpacked split pieces (CUDA-core variant of the split paths)
+    const float *x_plain, *y_plain;
     int32_t max_out_rows, max_out_cols;
     const int32_t *item_order;  // nullable: processing order of the items (grouped by block shape)
     const int32_t *status;      // nullable: the kernel does nothing when *status != 0
@@ -244,6 +247,12 @@ cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec,
                               cudaStream_t s);
 cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
                         void *pack, const int32_t *status, cudaStream_t s);
+// Unpacked split pieces of M's data (split_pieces(prec) floats per element).
+int split_pieces(int prec);
+cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStream_t s);
+// Mark the items of the classes that run the CUDA-core split variant (bit 31).
+cudaError_t launch_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
+                                const int8_t *variant_of_class, cudaStream_t s);
 
 // *status |= DEV_ERR_CAPACITY unless, for q < n (n <= 8), actual[q] == expected[q]
 // (or actual[q] <= expected[q] where at_most[q] is set)

@@ -433,6 +433,114 @@ __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lan
     }
 }
 
+// CUDA-core variant of the split arithmetic, for small block shapes where a
+// 16 x 8 MMA tile would be mostly padding: the same narrow pieces (stored
+// unpacked, NP floats per element: the pieces' exact values) multiplied with
+// FP32 FMA -- a product of two TF32 or BF16 pieces is exact in FP32 -- one
+// lane per output element, FP32 sum inside a block product, the same
+// compensated (or FP64) sum across products.
+template <int PREC, int Q, bool FF>
+__device__ __forceinline__ void cs_item(const NumericArgs &a, int64_t q, int lane) {
+    constexpr int NP = PrecTraits<PREC>::NP;
+    const float *__restrict__ X = static_cast<const float *>(a.x_plain);
+    const float *__restrict__ Y = static_cast<const float *>(a.y_plain);
+    const int32_t orc = a.out_blk_rc[q];
+    const int R = rc_rows(orc), S = rc_cols(orc);
+    const int RS = R * S;
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+    const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
+    for (int e0 = 0; e0 < RS; e0 += 32 * Q) {
+        int rr[Q], ss[Q];
+        float acc[Q], shi[FF ? Q : 1], slo[FF ? Q : 1];
+        double s64[FF ? 1 : Q];
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+            const int e = e0 + lane + 32 * u;
+            const bool v = e < RS;
+            rr[u] = v ? e / S : 0;
+            ss[u] = v ? e % S : 0;
+            acc[u] = 0.f;
+            if constexpr (FF) {
+                shi[u] = 0.f;
+                slo[u] = 0.f;
+            } else {
+                s64[u] = 0.0;
+            }
+        }
+        int since = 0;
+        for (int64_t p = p0; p < p1; ++p) {
+            const int32_t ix = a.px[p], iy = a.py[p];
+            const float *xb = X + a.x_blk_off[ix] * NP;
+            const float *yb = Y + a.y_blk_off[iy] * NP;
+            const int32_t xrc = a.x_blk_rc[ix];
+            const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+            const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+            const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+            for (int t = 0; t < Tn; ++t) {
+#pragma unroll
+                for (int u = 0; u < Q; ++u) {
+                    const float *xe = xb + (int64_t)(rr[u] * xs_r + t * xs_t) * NP;
+                    const float *ye = yb + (int64_t)(t * ys_t + ss[u] * ys_s) * NP;
+                    if constexpr (NP == 2) {
+                        const float2 xv = __ldg(reinterpret_cast<const float2 *>(xe));
+                        const float2 yv = __ldg(reinterpret_cast<const float2 *>(ye));
+                        acc[u] = fmaf(xv.y, yv.x, acc[u]);
+                        acc[u] = fmaf(xv.x, yv.y, acc[u]);
+                        acc[u] = fmaf(xv.x, yv.x, acc[u]);
+                    } else {
+                        const float x0 = __ldg(xe), x1 = __ldg(xe + 1), x2 = __ldg(xe + 2);
+                        const float y0 = __ldg(ye), y1 = __ldg(ye + 1), y2 = __ldg(ye + 2);
+                        acc[u] = fmaf(x2, y0, acc[u]);
+                        acc[u] = fmaf(x1, y1, acc[u]);
+                        acc[u] = fmaf(x0, y2, acc[u]);
+                        acc[u] = fmaf(x1, y0, acc[u]);
+                        acc[u] = fmaf(x0, y1, acc[u]);
+                        acc[u] = fmaf(x0, y0, acc[u]);
+                    }
+                }
+            }
+            if (++since == F) {
+                since = 0;
+#pragma unroll
+                for (int u = 0; u < Q; ++u) {
+                    if constexpr (FF) two_sum_acc(shi[u], slo[u], acc[u]);
+                    else s64[u] += (double)acc[u];
+                    acc[u] = 0.f;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < Q; ++u) {
+            const int e = e0 + lane + 32 * u;
+            if (e < RS) {
+                double sum;
+                if constexpr (FF) sum = ((double)shi[u] + (double)slo[u]) + (double)acc[u];
+                else sum = s64[u] + (double)acc[u];
+                double val = a.alpha * sum;
+                if (a.dtype == BSM_FP64) {
+                    if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
+                    static_cast<double *>(a.out_data)[out_off + e] = val;
+                } else {
+                    if (old >= 0) val = fma(a.beta, (double)static_cast<const float *>(a.old_data)[old + e], val);
+                    static_cast<float *>(a.out_data)[out_off + e] = (float)val;
+                }
+            }
+        }
+    }
+}
+
+template <int PREC, bool FF>
+__device__ __forceinline__ void cs_dispatch(const NumericArgs &a, int64_t q, int lane) {
+    const int32_t orc = a.out_blk_rc[q];
+    const int need = (rc_rows(orc) * rc_cols(orc) + 31) >> 5;
+    if (need <= 1) cs_item<PREC, 1, FF>(a, q, lane);
+    else if (need <= 2) cs_item<PREC, 2, FF>(a, q, lane);
+    else if (need <= 4) cs_item<PREC, 4, FF>(a, q, lane);
+    else cs_item<PREC, 8, FF>(a, q, lane);
+}
+
 template <int PREC, bool FF>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t tc_smem[];
@@ -445,8 +553,14 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
         if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= a.n_items) break;
-        if (a.item_order) q = a.item_order[q];
-        tc_item<PREC, FF>(a, q, lane, ring);
+        bool on_cores = false;
+        if (a.item_order) {
+            const uint32_t code = (uint32_t)a.item_order[q];
+            on_cores = (code >> 31) != 0;  // variant bit: CUDA-core split arithmetic
+            q = (int64_t)(code & 0x7fffffffu);
+        }
+        if (on_cores) cs_dispatch<PREC, FF>(a, q, lane);
+        else tc_item<PREC, FF>(a, q, lane, ring);
     }
 }
 
@@ -588,6 +702,35 @@ __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_
     }
 }
 
+// Unpacked pieces: out[e*NP + p] = piece p of element e (as an FP32 value)
+template <typename T, int PREC>
+__global__ void k_split_plain(int64_t n, const T *data, float *out) {
+    constexpr int NP = PrecTraits<PREC>::NP;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t sp[3];
+        split_value<PREC>((double)data[e], sp);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float v;
+            if constexpr (PREC == BSM_P_TF32x3) v = __uint_as_float(sp[p]);
+            else v = __bfloat162float(__ushort_as_bfloat16((unsigned short)sp[p]));
+            out[e * NP + p] = v;
+        }
+    }
+}
+
+// Set bit 31 of order[t] when the block order[t] is computed by the CUDA-core
+// variant: variant_of_class[size_index[rows] * ns + size_index[cols]] != 0.
+__global__ void k_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index,
+                               int32_t ns, const int8_t *variant_of_class) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = order[t] & 0x7fffffff;
+        const int32_t rc = blk_rc[q];
+        if (variant_of_class[size_index[rc_rows(rc)] * ns + size_index[rc_cols(rc)]])
+            order[t] = (int32_t)((uint32_t)q | 0x80000000u);
+    }
+}
+
 int g_num_sms = 0;
 int num_sms() {
     if (g_num_sms == 0) {
@@ -646,6 +789,37 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
         e = launch_tc<BSM_P_BF16x6>(a, s);
     }
     if (e != cudaSuccess) return e;
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStream_t s) {
+    if (M->data_len == 0) return cudaSuccess;
+    int64_t g = (M->data_len + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    const bool f64 = M->dtype == BSM_FP64;
+    if (prec == BSM_P_TF32x3) {
+        if (f64) k_split_plain<double, BSM_P_TF32x3><<<(unsigned)g, 256, 0, s>>>(M->data_len, static_cast<const double *>(M->data), out);
+        else k_split_plain<float, BSM_P_TF32x3><<<(unsigned)g, 256, 0, s>>>(M->data_len, static_cast<const float *>(M->data), out);
+    } else if (prec == BSM_P_BF16x3) {
+        if (f64) k_split_plain<double, BSM_P_BF16x3><<<(unsigned)g, 256, 0, s>>>(M->data_len, static_cast<const double *>(M->data), out);
+        else k_split_plain<float, BSM_P_BF16x3><<<(unsigned)g, 256, 0, s>>>(M->data_len, static_cast<const float *>(M->data), out);
+    } else {
+        if (f64) k_split_plain<double, BSM_P_BF16x6><<<(unsigned)g, 256, 0, s>>>(M->data_len, static_cast<const double *>(M->data), out);
+        else k_split_plain<float, BSM_P_BF16x6><<<(unsigned)g, 256, 0, s>>>(M->data_len, static_cast<const float *>(M->data), out);
+    }
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+int split_pieces(int prec) { return prec == BSM_P_BF16x6 ? 3 : 2; }
+
+cudaError_t launch_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
+                                const int8_t *variant_of_class, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_mark_variant<<<(unsigned)g, 256, 0, s>>>(n, order, blk_rc, size_index, ns, variant_of_class);
     count_launch(1);
     return cudaGetLastError();
 }

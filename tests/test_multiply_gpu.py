@@ -97,6 +97,57 @@ def test_split_with_fp64_sum(bsm, oracle, prec, flush):
     assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x6", "bf16x3"])
+def test_cuda_core_split_variant(bsm, oracle, prec):
+    """Every output shape on the CUDA-core variant of the split arithmetic."""
+    rng = np.random.default_rng(2)
+    bs = rng.integers(1, 30, size=40).astype(np.int32)
+    A, B = random_bcsr(bs, bs, 0.2, seed=141), random_bcsr(bs, bs, 0.2, seed=142)
+    sizes = sorted(set(int(x) for x in bs))
+    try:
+        for m in sizes:
+            for n in sizes:
+                bsm.bsm_set_variant(prec, m, n, 1)
+        for fl in (0, 1):
+            Cg, ref, gA, gB = _run(bsm, oracle, A, B, 0.0, prec=prec, flush_every=fl)
+            _check_pattern(Cg, ref.C)
+            assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
+        # adjoints through the same variant
+        import torch
+        G = np.random.default_rng(3).standard_normal(ref.C.data_len)
+        dA_ref, dB_ref = oracle.multiply_backward(1.0, A, B, ref.C, G, ref.prods)
+        dA = torch.empty(len(A.data), dtype=torch.float64, device="cuda")
+        dB = torch.empty(len(B.data), dtype=torch.float64, device="cuda")
+        bsm.multiply_backward(1.0, Cg, torch.tensor(G, device="cuda"), gA, gB, dA, dB, prec=prec)
+        assert rel_fro(dA.cpu().numpy(), dA_ref) <= TOL[prec]
+        assert rel_fro(dB.cpu().numpy(), dB_ref) <= TOL[prec]
+    finally:
+        for m in sizes:
+            for n in sizes:
+                bsm.bsm_set_variant(prec, m, n, 0)
+
+
+def test_autotune_table_roundtrip(bsm, oracle, tmp_path):
+    from paper_1708_03604_gb300 import autotune
+    w = I.mixed_banded(nb=300, occ=0.1, eps=1e-6)
+    A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+    try:
+        table = autotune.tune(A, B, w["eps"], prec="tf32x3", reps=1)
+        assert set(table["variants"]) == {f"{m}x{n}" for m in (5, 13, 23) for n in (5, 13, 23)}
+        path = str(tmp_path / "tune.json")
+        autotune.save([table], path)
+        autotune.reset("tf32x3", (5, 13, 23))
+        autotune.load(path)
+        for key, v in table["variants"].items():
+            m, n = (int(x) for x in key.split("x"))
+            assert bsm.bsm_get_variant("tf32x3", m, n) == v
+        Cg = bsm.multiply(1.0, A, B, eps=w["eps"], prec="tf32x3")
+        ref = oracle.multiply(1.0, w["A"], w["B"], eps=w["eps"])
+        assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-6
+    finally:
+        autotune.reset("tf32x3", (5, 13, 23))
+
+
 def test_ragged_sizes_and_large_blocks(bsm, oracle):
     # block sizes 1..40 (several fragment tiles and element passes per block)
     rng = np.random.default_rng(5)
