@@ -56,6 +56,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
     p.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                    help="block rows/cols (smaller cases for profiling; the metric is quoted at 3000)")
+    p.add_argument("--workload", default="mixed3000",
+                   choices=["mixed3000", "uniform23_200", "banded23_6912", "diff13_800", "purify_2000"],
+                   help="mixed3000 is the headline line; the others measure the remaining configurations")
     a = p.parse_args()
     if a.nb != WORKLOAD["nb"]:
         WORKLOAD["nb"] = a.nb
@@ -214,6 +217,91 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------
+# the other configurations (one GPU)
+# --------------------------------------------------------------------------
+def _timed(torch, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_other(args):
+    import torch
+    from paper_1708_03604_gb300 import bsm, chain
+    torch.cuda.set_device(0)
+    name = args.workload
+    out = {"metric": "block-SpGEMM useful TFLOP/s", "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic", "vs_baseline": None}
+    if name in ("uniform23_200", "banded23_6912"):
+        w = I.uniform_23() if name == "uniform23_200" else I.large_banded_23()
+        A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+        Cm = bsm.Matrix.empty(w["A"].row_bs, w["B"].col_bs)
+        legs = {}
+        ref = None
+        # error over the first 2^28 elements of C (the whole C of the 6912-block case is 38 GB)
+        nref = 1 << 28
+        for key, prec in (("fp64", "fp64"), ("tf32x3", "tf32x3"), ("bf16x6", "bf16x6"), ("bf16x3", "bf16x3")):
+            ms = _timed(torch, lambda: bsm.multiply(1.0, A, B, 0.0, Cm, w["eps"], prec=prec, build_stacks=False),
+                        args.steps, args.warmup)
+            flop = Cm.counts().useful_flop
+            c = Cm.data_tensor()[:nref].clone()
+            torch.cuda.empty_cache()
+            if ref is None:
+                ref = c
+            err = (torch.linalg.vector_norm(c - ref) / torch.linalg.vector_norm(ref)).item()
+            legs[key] = {"value": flop / ms * 1e-9, "ms_per_step": ms, "rel_fro_err_vs_fp64_path": err,
+                         "err_sample_elements": int(c.numel())}
+            del c
+            torch.cuda.empty_cache()
+        out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
+                   config={"workload": name, "products": Cm.counts().products, "useful_flop": flop,
+                           "filtered": Cm.counts().filtered, "c_blocks": Cm.nnzb}, split_precision=legs)
+    elif name == "diff13_800":
+        w = I.differentiation_13()
+        A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+        Cm = bsm.multiply(1.0, A, B)
+        dC = torch.randn(Cm.info().data_len, dtype=torch.float64, device="cuda")
+        dA = torch.empty(len(w["A"].data), dtype=torch.float64, device="cuda")
+        dB = torch.empty(len(w["B"].data), dtype=torch.float64, device="cuda")
+        legs = {}
+        for prec in ("fp64", "tf32x3"):
+            def step():
+                bsm.multiply(1.0, A, B, 0.0, Cm, 0.0, prec=prec)
+                bsm.multiply_backward(1.0, Cm, dC, A, B, dA, dB, prec=prec)
+            ms = _timed(torch, step, args.steps, args.warmup)
+            flop = 3 * Cm.counts().useful_flop      # forward + two adjoint products
+            legs[prec] = {"value": flop / ms * 1e-9, "ms_per_step": ms}
+        out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
+                   config={"workload": name, "step": "multiply + both adjoints", "products": Cm.counts().products,
+                           "useful_flop_per_step": flop}, split_precision={"tf32x3": legs["tf32x3"]})
+    else:  # purify_2000: the 10-step McWeeny chain as one CUDA graph
+        w = I.purification_start(nb=2000)
+        X0 = bsm.Matrix.from_host(w["X0"])
+        legs = {}
+        for prec in ("fp64", "tf32x3"):
+            g = chain.McWeenyGraph(X0, w["steps"], w["eps"], prec=prec)
+            flop = sum(h.counts().useful_flop for h in g.X2 + g.X3)
+            ms = _timed(torch, g.replay, args.steps, args.warmup)
+            assert g.status() == 0
+            occ = [h.nnzb / 2000 ** 2 for h in g.X]
+            legs[prec] = {"value": flop / ms * 1e-9, "ms_per_step": ms, "useful_flop": flop,
+                          "block_occupancy_per_iterate": [round(o, 4) for o in occ]}
+            del g
+        out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
+                   config={"workload": name, "step": "replay of the graph-captured 10-step chain (20 multiplies, "
+                                                    "10 filtered adds)", "eps": w["eps"]},
+                   split_precision={"tf32x3": legs["tf32x3"]}, chain=legs)
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
 # GB300 arm
 # --------------------------------------------------------------------------
 def main():
@@ -223,6 +311,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "mixed3000":
+        return run_other(args)
 
     import torch
     import torch.distributed as dist

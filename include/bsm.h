@@ -103,13 +103,16 @@ bsm_status bsm_set_profiling(int32_t on);
  * (all handles, all streams). */
 bsm_status bsm_get_launch_count(int64_t *count);
 
-/* Numeric variant of the split-precision paths (TF32x3, BF16x3, BF16x6) for
- * output blocks of m rows and n columns: 0 = tensor-core MMA on packed
- * fragments (default), 1 = the same split pieces multiplied with FP32 FMA on
- * CUDA cores (exact piece products; faster for small blocks, where an MMA
- * tile is mostly padding).  Process-wide; set by the autotuner
- * (paper_1708_03604_gb300/autotune.py) from measurements.  Applies to
- * multiplies issued afterwards (a no-sync multiply keeps its eager choice). */
+/* Numeric variant per precision and output block shape (m rows, n columns).
+ * Split paths (TF32x3, BF16x3, BF16x6): 0 = tensor-core MMA on packed
+ * fragments, 1 = the same split pieces multiplied with FP32 FMA on CUDA cores
+ * (exact piece products).  FP64 paths: 0 = one warp per output block, lanes
+ * over its elements; 1 = one lane per output block (only for m*n <= 16;
+ * larger shapes always use 0).  -1 restores the library default (FP64: 1 for
+ * m*n <= 16, split paths: 0); bsm_get_variant returns the variant in effect.
+ * Process-wide; the autotuner (paper_1708_03604_gb300/autotune.py) sets it
+ * from measurements.  Applies to multiplies issued afterwards (a no-sync
+ * multiply keeps the choice of its eager call). */
 bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant);
 bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant);
 

@@ -1,14 +1,19 @@
-"""Autotuner for the split-precision numeric kernel.
+"""Autotuner of the numeric kernels' per-shape variants.
 
-For every output block shape (m, n) that a multiply produces, the split
-paths can run the block products either as tensor-core MMAs on packed
-fragments (variant 0) or as the same narrow pieces multiplied with FP32 FMA
-on CUDA cores (variant 1).  Which is faster depends on the shape (small
-blocks leave most of an MMA tile idle) and on the product mix, so it is
-measured: starting from all-MMA, each shape in turn is switched to the
-CUDA-core variant and kept there if the numeric kernel (timed with CUDA
-events by the library) gets faster.  The table is process-wide in libbsm
-and can be saved to / loaded from JSON.
+For every output block shape (m, n) that a multiply produces there are two
+ways to compute its block products:
+
+* split paths: tensor-core MMAs on packed fragments (variant 0) or the same
+  narrow pieces multiplied with FP32 FMA on CUDA cores (variant 1);
+* FP64 path: one warp per output block with lanes over its elements
+  (variant 0) or, for blocks of at most 16 elements, one lane per block
+  (variant 1).
+
+Which is faster depends on the shape and the product mix, so it is measured:
+starting from variant 0 everywhere, each shape in turn is switched to
+variant 1 and kept there if the numeric kernel (timed with CUDA events by
+the library) gets faster.  The table is process-wide in libbsm and can be
+saved to / loaded from JSON.
 """
 from __future__ import annotations
 
@@ -39,6 +44,8 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
     """Choose the variant of every output shape of A.B for `prec`; returns
     {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}."""
     shapes = _shapes(A, B)
+    if prec in ("fp64", "fp64_dmma"):
+        shapes = [(m, n) for m, n in shapes if m * n <= 16]  # larger FP64 shapes have one variant
     for m, n in shapes:
         bsm.bsm_set_variant(prec, m, n, 0)
     Cm = bsm.Matrix.empty(A.row_bs, B.col_bs)
@@ -69,9 +76,10 @@ def apply(table: dict):
 
 
 def reset(prec: str, sizes):
+    """Back to the library's default variants for these block sizes."""
     for m in sizes:
         for n in sizes:
-            bsm.bsm_set_variant(prec, int(m), int(n), 0)
+            bsm.bsm_set_variant(prec, int(m), int(n), -1)
 
 
 def save(tables, path: str):

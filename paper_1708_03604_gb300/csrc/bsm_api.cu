@@ -21,9 +21,25 @@ cudaStream_t g_stream = nullptr;
 bool g_prof = false;
 bool g_pool_configured = false;
 int64_t *g_host = nullptr;  // pinned host words for small device->host reads
-// numeric variant of the split paths per (precision, rows, cols) of the output
-// block: 0 = tensor-core fragments, 1 = CUDA-core split arithmetic
-int8_t g_variant[5][kMaxBlockDim + 1][kMaxBlockDim + 1] = {};
+// numeric variant per (precision, rows, cols) of the output block; -1 = the
+// library default (see variant_of)
+int8_t g_variant[5][kMaxBlockDim + 1][kMaxBlockDim + 1];
+bool g_variant_init = false;
+
+int variant_of(int prec, int m, int n) {
+    if (!g_variant_init) {
+        std::memset(g_variant, -1, sizeof(g_variant));
+        g_variant_init = true;
+    }
+    const int v = g_variant[prec][m][n];
+    const bool fp64 = prec == BSM_P_FP64 || prec == BSM_P_FP64_DMMA;
+    if (fp64) {
+        // variant 1 of the FP64 path: one lane per output block, up to 16 elements
+        if (m * n > 16) return 0;
+        return v < 0 ? 1 : v;
+    }
+    return v < 0 ? 0 : v;
+}
 std::atomic<int64_t> g_launches{0};
 
 struct Scratch {
@@ -113,6 +129,7 @@ void free_pattern(bsm_mat *X) {
     dfree(X->norms); X->norms = nullptr;
     X->norms_valid = false;
     dfree(X->item_order); X->item_order = nullptr;
+    dfree(X->n_marked); X->n_marked = nullptr;
     dfree(X->row_rank); X->row_rank = nullptr;
     dfree(X->t_ptr); X->t_ptr = nullptr;
     dfree(X->t_row); X->t_row = nullptr;
@@ -231,7 +248,8 @@ bsm_status ensure_row_rank(bsm_mat *X) {
 // code path and the heaviest items start early.
 bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std::vector<int32_t> &rsz,
                        const std::vector<int32_t> &csz, int32_t **order, const bsm_mat *rows_of = nullptr,
-                       const int32_t *row_rank = nullptr, int prec = -1, bool *uses_cores = nullptr) {
+                       const int32_t *row_rank = nullptr, int prec = -1, bool *uses_cores = nullptr,
+                       int64_t **n_marked = nullptr) {
     if (uses_cores) *uses_cores = false;
     *order = nullptr;
     if (n <= 1) return BSM_OK;
@@ -242,16 +260,28 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     const int32_t ns = (int32_t)sizes.size();
     if ((int64_t)ns * ns > (1 << 16)) return BSM_OK;  // too many shapes: natural order
     std::vector<int32_t> sidx(kMaxBlockDim + 1, 0), table((size_t)ns * ns);
+    if (n_marked) *n_marked = nullptr;
     for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
     std::vector<std::pair<int64_t, int32_t>> cls;
     for (int32_t r = 0; r < ns; ++r)
         for (int32_t c = 0; c < ns; ++c) cls.emplace_back(-(int64_t)sizes[r] * sizes[c], r * ns + c);
     std::sort(cls.begin(), cls.end());
-    for (size_t q = 0; q < cls.size(); ++q) table[cls[q].second] = (int32_t)q;
+    // per-class variant; second-variant classes sort after all others
+    std::vector<int8_t> var((size_t)ns * ns, 0);
+    bool any_var = false;
+    if (prec >= 0) {
+        for (int32_t r = 0; r < ns; ++r)
+            for (int32_t c = 0; c < ns; ++c) {
+                var[(size_t)r * ns + c] = (int8_t)variant_of(prec, sizes[r], sizes[c]);
+                any_var = any_var || var[(size_t)r * ns + c];
+            }
+    }
+    for (size_t q = 0; q < cls.size(); ++q)
+        table[cls[q].second] = (int32_t)q + (var[cls[q].second] ? (int32_t)cls.size() : 0);
     const int32_t nbr = rows_of ? rows_of->nbr : 0;
-    if (row_rank && (int64_t)table.size() * std::max(nbr, 1) >= (int64_t(1) << 31)) row_rank = nullptr;
+    if (row_rank && 2 * (int64_t)table.size() * std::max(nbr, 1) >= (int64_t(1) << 31)) row_rank = nullptr;
     int bits = 1;
-    while ((1ll << bits) < (int64_t)table.size() * (row_rank ? nbr : 1)) ++bits;
+    while ((1ll << bits) < 2 * (int64_t)table.size() * (row_rank ? nbr : 1)) ++bits;
     bsm_status st;
     int32_t *d_sidx, *d_table, *iota, *vals_alt, *out, *brow = nullptr;
     uint32_t *keys, *keys_alt, *keys_sorted;
@@ -274,23 +304,19 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     if (e == cudaSuccess)
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
-    if (prec >= 0 && uses_cores) {
-        std::vector<int8_t> var((size_t)ns * ns, 0);
-        bool any = false;
-        for (int32_t r = 0; r < ns; ++r)
-            for (int32_t c = 0; c < ns; ++c) {
-                var[(size_t)r * ns + c] = g_variant[prec][sizes[r]][sizes[c]];
-                any = any || var[(size_t)r * ns + c];
-            }
-        if (any) {
-            int8_t *d_var;
-            if ((st = sc.get(&d_var, var.size()))) return st;
-            e = cudaMemcpyAsync(d_var, var.data(), var.size(), cudaMemcpyHostToDevice, g_stream);
-            if (e == cudaSuccess) e = launch_mark_variant(n, out, blk_rc, d_sidx, ns, d_var, g_stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);  // var is pageable and local
-            if ((st = cuda_check(e, "variant marks"))) return st;
-            *uses_cores = true;
-        }
+    if (any_var) {
+        int8_t *d_var;
+        int64_t *cnt;
+        if ((st = sc.get(&d_var, var.size())) || (st = sc.get(&cnt, 1))) return st;
+        e = cudaMemcpyAsync(d_var, var.data(), var.size(), cudaMemcpyHostToDevice, g_stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int64_t), g_stream);
+        if (e == cudaSuccess)
+            e = launch_mark_variant(n, out, blk_rc, d_sidx, ns, d_var, reinterpret_cast<unsigned long long *>(cnt),
+                                    g_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);  // var is pageable and local
+        if ((st = cuda_check(e, "variant marks"))) return st;
+        if (uses_cores) *uses_cores = true;
+        if (n_marked) *n_marked = cnt;
     }
     *order = out;
     return BSM_OK;
@@ -1005,9 +1031,11 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.status = no_sync ? C->status : nullptr;
     if ((st = sc.get(&na.work_counter, 2))) return st;
     int32_t *order = nullptr;
+    int64_t *n_marked = nullptr;
     bool uses_cores = false;
     if (no_sync) {
         order = C->item_order;
+        n_marked = C->n_marked;
         uses_cores = pl.uses_cores;
     } else {
         if ((st = ensure_row_rank(A))) return st;
@@ -1015,10 +1043,11 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         rows_view.nbr = nbr;
         rows_view.row_ptr = crow_ptr;
         if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
-                              tc ? opts.prec : -1, &uses_cores)))
+                              opts.prec, &uses_cores, &n_marked)))
             return st;
     }
-    if (tc && uses_cores) {  // unpacked pieces for the CUDA-core variant
+    if (!tc) na.n_lane_items = n_marked;
+    if (tc && uses_cores) {  // unpacked pieces for the CUDA-core variant (tensor-core paths)
         const int np = split_pieces(opts.prec);
         float *xp = nullptr, *yp = nullptr;
         if ((st = sc.get(&xp, (size_t)A->data_len * np))) return st;
@@ -1041,6 +1070,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     free_results(C);
     free_pattern(C);
     C->item_order = order;
+    C->n_marked = n_marked;
     C->row_ptr = crow_ptr;
     C->col_idx = c_col;
     C->blk_off = c_off;
@@ -1061,7 +1091,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     C->prod_A = A; C->prod_B = B;
     C->prod_A_nnzb = A->nnzb; C->prod_B_nnzb = B->nnzb;
     for (void *p : {(void *)crow_ptr, (void *)c_col, (void *)c_off, (void *)c_rc, c_data, (void *)cptr, (void *)pa,
-                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order})
+                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order, (void *)n_marked})
         sc.release(p);
     C->plan = bsm_mat::Plan{};
     if (!use_old && !opts.post_filter) {
@@ -1085,6 +1115,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             dfree(C->stack_ptr); C->stack_ptr = nullptr;
             dfree(C->triples); C->triples = nullptr;
             dfree(C->item_order); C->item_order = nullptr;
+            dfree(C->n_marked); C->n_marked = nullptr;
             C->nshapes = 0;
             C->h_shapes.clear();
             C->prod_A = C->prod_B = nullptr;
@@ -1206,10 +1237,12 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;
         if ((st = sc.get(&na.work_counter, 2))) return st;
         int32_t *item_order = nullptr;
+        int64_t *n_marked = nullptr;
         bool uses_cores = false;
         if ((st = shape_order(sc, OUT->nnzb, OUT->blk_rc, OUT->h_row_bs, OUT->h_col_bs, &item_order, nullptr, nullptr,
-                              tc ? opts.prec : -1, &uses_cores)))
+                              opts.prec, &uses_cores, &n_marked)))
             return st;
+        if (!tc) na.n_lane_items = n_marked;
         if (tc && uses_cores && nprod > 0) {
             const int np = split_pieces(opts.prec);
             float *xp = nullptr, *yp = nullptr;
@@ -1401,8 +1434,9 @@ bsm_status bsm_add_backward(bsm_t Z, const void *dZ_data, bsm_t X, bsm_t Y, void
 
 bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant) {
     if (prec < BSM_P_FP64 || prec > BSM_P_BF16x6 || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim ||
-        variant < 0 || variant > 1)
+        variant < -1 || variant > 1)
         return set_error(BSM_ERR_ARG, "bsm_set_variant: argument out of range");
+    variant_of(prec, m, n);  // initialises the table
     g_variant[prec][m][n] = (int8_t)variant;
     return BSM_OK;
 }
@@ -1410,7 +1444,7 @@ bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant) 
 bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant) {
     if (!variant || prec < BSM_P_FP64 || prec > BSM_P_BF16x6 || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim)
         return set_error(BSM_ERR_ARG, "bsm_get_variant: argument out of range");
-    *variant = g_variant[prec][m][n];
+    *variant = variant_of(prec, m, n);
     return BSM_OK;
 }
 

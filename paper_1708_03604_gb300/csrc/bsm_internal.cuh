@@ -89,6 +89,7 @@ struct bsm_mat {
         int64_t u_nnzb = 0, u_len = 0;  // add: union before the norm filter
     } plan;
     int32_t *item_order = nullptr;      // numeric processing order of the last eager multiply
+    int64_t *n_marked = nullptr;        // device count of its second-variant items (or null)
     // rank of every block row in a breadth-first order through shared block
     // columns (built on demand, dropped with the pattern); schedules numeric work
     int32_t *row_rank = nullptr;        // [nbr]
@@ -232,7 +233,10 @@ struct NumericArgs {
     // unpacked split pieces (CUDA-core variant of the split paths)
     const float *x_plain, *y_plain;
     int32_t max_out_rows, max_out_cols;
-    const int32_t *item_order;  // nullable: processing order of the items (grouped by block shape)
+    const int32_t *item_order;  // nullable: processing order of the items (grouped by block shape);
+                                // bit 31 marks the second variant of the item's shape
+    const int64_t *n_lane_items;  // nullable (CUDA-core FP64 path): the last *n_lane_items items of
+                                  // item_order are tiny blocks computed one per lane
     const int32_t *status;      // nullable: the kernel does nothing when *status != 0
     unsigned long long *work_counter;  // 8 bytes of device memory, zeroed by the launcher
 };
@@ -252,7 +256,7 @@ int split_pieces(int prec);
 cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStream_t s);
 // Mark the items of the classes that run the CUDA-core split variant (bit 31).
 cudaError_t launch_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
-                                const int8_t *variant_of_class, cudaStream_t s);
+                                const int8_t *variant_of_class, unsigned long long *marked, cudaStream_t s);
 
 // *status |= DEV_ERR_CAPACITY unless, for q < n (n <= 8), actual[q] == expected[q]
 // (or actual[q] <= expected[q] where at_most[q] is set)

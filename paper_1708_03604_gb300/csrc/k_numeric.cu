@@ -127,18 +127,89 @@ __device__ __forceinline__ void cc_dispatch(const NumericArgs &a, int64_t q, int
     else cc_item<T, 24>(a, q, lane);
 }
 
+// Tiny output blocks (at most 16 elements): one lane owns a whole block, so a
+// warp advances 32 blocks at once instead of leaving most lanes idle.
+template <typename T>
+__device__ __forceinline__ void cc_lane_item(const NumericArgs &a, int64_t q) {
+    constexpr int L = 16;
+    const T *__restrict__ X = static_cast<const T *>(a.x_data);
+    const T *__restrict__ Y = static_cast<const T *>(a.y_data);
+    T *__restrict__ O = static_cast<T *>(a.out_data);
+    const int32_t orc = a.out_blk_rc[q];
+    const int R = rc_rows(orc), S = rc_cols(orc);
+    const int RS = R * S;
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+    double acc[L];
+    T acc_n[L];
+#pragma unroll
+    for (int e = 0; e < L; ++e) {
+        acc[e] = 0.0;
+        acc_n[e] = T(0);
+    }
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t ix = a.px[p], iy = a.py[p];
+        const T *xb = X + a.x_blk_off[ix];
+        const T *yb = Y + a.y_blk_off[iy];
+        const int32_t xrc = a.x_blk_rc[ix];
+        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+        const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+        const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+        for (int t = 0; t < Tn; ++t) {
+#pragma unroll
+            for (int e = 0; e < L; ++e) {
+                if (e < RS) {
+                    const int r = e / S, c = e - r * S;
+                    acc_n[e] = fma(__ldg(xb + r * xs_r + t * xs_t), __ldg(yb + t * ys_t + c * ys_s), acc_n[e]);
+                }
+            }
+        }
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int e = 0; e < L; ++e) {
+                acc[e] += (double)acc_n[e];
+                acc_n[e] = T(0);
+            }
+        }
+    }
+    const T *OLD = static_cast<const T *>(a.old_data);
+#pragma unroll
+    for (int e = 0; e < L; ++e) {
+        if (e < RS) {
+            double v = (sizeof(T) == 8) ? (double)acc_n[e] : acc[e];
+            v = a.alpha * v;
+            if (old >= 0) v = fma(a.beta, (double)OLD[old + e], v);
+            O[out_off + e] = (T)v;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
     const int lane = threadIdx.x & 31;
     if (a.status && *a.status != 0) return;
     unsigned long long *ctr = a.work_counter;
+    // items [0, n0): a warp each; items [n0, n_items): marked tiny blocks, 32 per ticket
+    const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
+    const int64_t n0 = a.n_items - n_lane;
+    const int64_t tickets = n0 + (n_lane + 31) / 32;
     while (true) {
-        int64_t q = 0;
-        if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= a.n_items) break;
-        if (a.item_order) q = a.item_order[q];
-        cc_dispatch<T>(a, q, lane);
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tickets) break;
+        if (t < n0) {
+            int64_t q = t;
+            if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            cc_dispatch<T>(a, q, lane);
+        } else {
+            const int64_t idx = n0 + (t - n0) * 32 + lane;
+            if (idx < a.n_items) {
+                const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
+                cc_lane_item<T>(a, q);
+            }
+        }
     }
 }
 
@@ -722,13 +793,17 @@ __global__ void k_split_plain(int64_t n, const T *data, float *out) {
 // Set bit 31 of order[t] when the block order[t] is computed by the CUDA-core
 // variant: variant_of_class[size_index[rows] * ns + size_index[cols]] != 0.
 __global__ void k_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index,
-                               int32_t ns, const int8_t *variant_of_class) {
+                               int32_t ns, const int8_t *variant_of_class, unsigned long long *marked) {
+    unsigned long long cnt = 0;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t q = order[t] & 0x7fffffff;
         const int32_t rc = blk_rc[q];
-        if (variant_of_class[size_index[rc_rows(rc)] * ns + size_index[rc_cols(rc)]])
+        if (variant_of_class[size_index[rc_rows(rc)] * ns + size_index[rc_cols(rc)]]) {
             order[t] = (int32_t)((uint32_t)q | 0x80000000u);
+            cnt++;
+        }
     }
+    if (marked && cnt) atomicAdd(marked, cnt);
 }
 
 int g_num_sms = 0;
@@ -815,11 +890,11 @@ cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStrea
 int split_pieces(int prec) { return prec == BSM_P_BF16x6 ? 3 : 2; }
 
 cudaError_t launch_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
-                                const int8_t *variant_of_class, cudaStream_t s) {
+                                const int8_t *variant_of_class, unsigned long long *marked, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     int64_t g = (n + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
-    k_mark_variant<<<(unsigned)g, 256, 0, s>>>(n, order, blk_rc, size_index, ns, variant_of_class);
+    k_mark_variant<<<(unsigned)g, 256, 0, s>>>(n, order, blk_rc, size_index, ns, variant_of_class, marked);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -124,7 +124,40 @@ def test_cuda_core_split_variant(bsm, oracle, prec):
     finally:
         for m in sizes:
             for n in sizes:
-                bsm.bsm_set_variant(prec, m, n, 0)
+                bsm.bsm_set_variant(prec, m, n, -1)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_fp64_tiny_blocks_both_variants(bsm, oracle, variant):
+    """Blocks of 1..4 rows/columns: one warp per output block (0) or one lane
+    per output block (1), forward and adjoints, against the oracle."""
+    import torch
+    bs = I.mixed_sizes(120, (1, 2, 4), (0.4, 0.3, 0.3), seed=5)
+    A, B = random_bcsr(bs, bs, 0.1, seed=151), random_bcsr(bs, bs, 0.1, seed=152)
+    try:
+        for m in (1, 2, 4):
+            for n in (1, 2, 4):
+                bsm.bsm_set_variant("fp64", m, n, variant)
+                assert bsm.bsm_get_variant("fp64", m, n) == variant
+        Cg, ref, gA, gB = _run(bsm, oracle, A, B, 1e-3, beta=0.5, C0=random_bcsr(bs, bs, 0.05, seed=153))
+        _check_pattern(Cg, ref.C)
+        assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-12
+        Cg, ref, gA, gB = _run(bsm, oracle, A, B, 0.0)
+        G = np.random.default_rng(4).standard_normal(ref.C.data_len)
+        dA_ref, dB_ref = oracle.multiply_backward(1.0, A, B, ref.C, G, ref.prods)
+        dA = torch.empty(len(A.data), dtype=torch.float64, device="cuda")
+        dB = torch.empty(len(B.data), dtype=torch.float64, device="cuda")
+        bsm.multiply_backward(1.0, Cg, torch.tensor(G, device="cuda"), gA, gB, dA, dB)
+        assert rel_fro(dA.cpu().numpy(), dA_ref) <= 1e-12
+        assert rel_fro(dB.cpu().numpy(), dB_ref) <= 1e-12
+        # FP32 data through the same variant
+        A32, B32 = A.astype(np.float32), B.astype(np.float32)
+        Cg, ref, _, _ = _run(bsm, oracle, A32, B32, 0.0)
+        assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-5
+    finally:
+        for m in (1, 2, 4):
+            for n in (1, 2, 4):
+                bsm.bsm_set_variant("fp64", m, n, -1)
 
 
 def test_autotune_table_roundtrip(bsm, oracle, tmp_path):
