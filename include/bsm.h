@@ -103,13 +103,13 @@ bsm_status bsm_set_profiling(int32_t on);
  * (all handles, all streams). */
 bsm_status bsm_get_launch_count(int64_t *count);
 
-/* Numeric variant per precision and output block shape (m rows, n columns).
- * Split paths (TF32x3, BF16x3, BF16x6): 0 = tensor-core MMA on packed
- * fragments, 1 = the same split pieces multiplied with FP32 FMA on CUDA cores
- * (exact piece products).  FP64 paths: 0 = one warp per output block, lanes
- * over its elements; 1 = one lane per output block (only for m*n <= 16;
- * larger shapes always use 0).  -1 restores the library default (FP64: 1 for
- * m*n <= 16, split paths: 0); bsm_get_variant returns the variant in effect.
+/* Numeric variant per precision and output block shape (m rows, n columns),
+ * for tiny blocks (m*n <= 16; larger shapes always use variant 0):
+ * 0 = one warp per output block (FP64: lanes over its elements; split paths:
+ * tensor-core MMA on packed fragments), 1 = one lane per output block on CUDA
+ * cores (split paths: the same split pieces multiplied with FP32 FMA, exact
+ * piece products).  -1 restores the library default (1);
+ * bsm_get_variant returns the variant in effect.
  * Process-wide; the autotuner (paper_1708_03604_gb300/autotune.py) sets it
  * from measurements.  Applies to multiplies issued afterwards (a no-sync
  * multiply keeps the choice of its eager call). */

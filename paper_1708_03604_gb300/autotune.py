@@ -3,11 +3,10 @@
 For every output block shape (m, n) that a multiply produces there are two
 ways to compute its block products:
 
-* split paths: tensor-core MMAs on packed fragments (variant 0) or the same
-  narrow pieces multiplied with FP32 FMA on CUDA cores (variant 1);
-* FP64 path: one warp per output block with lanes over its elements
-  (variant 0) or, for blocks of at most 16 elements, one lane per block
-  (variant 1).
+* variant 0: one warp per output block (FP64: lanes over its elements;
+  split paths: tensor-core MMAs on packed fragments);
+* variant 1, for blocks of at most 16 elements: one lane per output block on
+  CUDA cores (split paths: the same narrow pieces multiplied with FP32 FMA).
 
 Which is faster depends on the shape and the product mix, so it is measured:
 starting from variant 0 everywhere, each shape in turn is switched to
@@ -43,9 +42,7 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
          gain: float = 0.01) -> dict:
     """Choose the variant of every output shape of A.B for `prec`; returns
     {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}."""
-    shapes = _shapes(A, B)
-    if prec in ("fp64", "fp64_dmma"):
-        shapes = [(m, n) for m, n in shapes if m * n <= 16]  # larger FP64 shapes have one variant
+    shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16]  # larger shapes have one variant
     for m, n in shapes:
         bsm.bsm_set_variant(prec, m, n, 0)
     Cm = bsm.Matrix.empty(A.row_bs, B.col_bs)

@@ -32,13 +32,9 @@ int variant_of(int prec, int m, int n) {
         g_variant_init = true;
     }
     const int v = g_variant[prec][m][n];
-    const bool fp64 = prec == BSM_P_FP64 || prec == BSM_P_FP64_DMMA;
-    if (fp64) {
-        // variant 1 of the FP64 path: one lane per output block, up to 16 elements
-        if (m * n > 16) return 0;
-        return v < 0 ? 1 : v;
-    }
-    return v < 0 ? 0 : v;
+    // variant 1: one lane per output block (CUDA cores), for up to 16 elements
+    if (m * n > 16) return 0;
+    return v < 0 ? 1 : v;
 }
 std::atomic<int64_t> g_launches{0};
 
@@ -1046,7 +1042,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
                               opts.prec, &uses_cores, &n_marked)))
             return st;
     }
-    if (!tc) na.n_lane_items = n_marked;
+    na.n_lane_items = n_marked;
     if (tc && uses_cores) {  // unpacked pieces for the CUDA-core variant (tensor-core paths)
         const int np = split_pieces(opts.prec);
         float *xp = nullptr, *yp = nullptr;
@@ -1242,7 +1238,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         if ((st = shape_order(sc, OUT->nnzb, OUT->blk_rc, OUT->h_row_bs, OUT->h_col_bs, &item_order, nullptr, nullptr,
                               opts.prec, &uses_cores, &n_marked)))
             return st;
-        if (!tc) na.n_lane_items = n_marked;
+        na.n_lane_items = n_marked;
         if (tc && uses_cores && nprod > 0) {
             const int np = split_pieces(opts.prec);
             float *xp = nullptr, *yp = nullptr;

@@ -504,17 +504,17 @@ __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lan
     }
 }
 
-// CUDA-core variant of the split arithmetic, for small block shapes where a
-// 16 x 8 MMA tile would be mostly padding: the same narrow pieces (stored
-// unpacked, NP floats per element: the pieces' exact values) multiplied with
-// FP32 FMA -- a product of two TF32 or BF16 pieces is exact in FP32 -- one
-// lane per output element, FP32 sum inside a block product, the same
-// compensated (or FP64) sum across products.
-template <int PREC, int Q, bool FF>
-__device__ __forceinline__ void cs_item(const NumericArgs &a, int64_t q, int lane) {
+// Tiny output blocks (at most 16 elements) on the split paths: one lane owns
+// a whole block and multiplies the same narrow pieces with FP32 FMA on CUDA
+// cores (a product of two TF32 or BF16 pieces is exact in FP32), FP32 sum
+// inside a block product, the same compensated (or FP64) sum across products.
+// A 16 x 8 MMA tile would be almost all padding for such blocks.
+template <int PREC, bool FF>
+__device__ __forceinline__ void cs_lane_item(const NumericArgs &a, int64_t q) {
     constexpr int NP = PrecTraits<PREC>::NP;
-    const float *__restrict__ X = static_cast<const float *>(a.x_plain);
-    const float *__restrict__ Y = static_cast<const float *>(a.y_plain);
+    constexpr int L = 16;
+    const float *__restrict__ X = a.x_plain;
+    const float *__restrict__ Y = a.y_plain;
     const int32_t orc = a.out_blk_rc[q];
     const int R = rc_rows(orc), S = rc_cols(orc);
     const int RS = R * S;
@@ -522,94 +522,79 @@ __device__ __forceinline__ void cs_item(const NumericArgs &a, int64_t q, int lan
     const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
     const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
     const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
-    for (int e0 = 0; e0 < RS; e0 += 32 * Q) {
-        int rr[Q], ss[Q];
-        float acc[Q], shi[FF ? Q : 1], slo[FF ? Q : 1];
-        double s64[FF ? 1 : Q];
+    float acc[L], shi[FF ? L : 1], slo[FF ? L : 1];
+    double s64[FF ? 1 : L];
 #pragma unroll
-        for (int u = 0; u < Q; ++u) {
-            const int e = e0 + lane + 32 * u;
-            const bool v = e < RS;
-            rr[u] = v ? e / S : 0;
-            ss[u] = v ? e % S : 0;
-            acc[u] = 0.f;
-            if constexpr (FF) {
-                shi[u] = 0.f;
-                slo[u] = 0.f;
-            } else {
-                s64[u] = 0.0;
-            }
+    for (int e = 0; e < L; ++e) {
+        acc[e] = 0.f;
+        if constexpr (FF) {
+            shi[e] = 0.f;
+            slo[e] = 0.f;
+        } else {
+            s64[e] = 0.0;
         }
-        int since = 0;
-        for (int64_t p = p0; p < p1; ++p) {
-            const int32_t ix = a.px[p], iy = a.py[p];
-            const float *xb = X + a.x_blk_off[ix] * NP;
-            const float *yb = Y + a.y_blk_off[iy] * NP;
-            const int32_t xrc = a.x_blk_rc[ix];
-            const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
-            const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
-            const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
-            for (int t = 0; t < Tn; ++t) {
+    }
+    int since = 0;
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t ix = a.px[p], iy = a.py[p];
+        const float *xb = X + a.x_blk_off[ix] * NP;
+        const float *yb = Y + a.y_blk_off[iy] * NP;
+        const int32_t xrc = a.x_blk_rc[ix];
+        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+        const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+        const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+        for (int t = 0; t < Tn; ++t) {
 #pragma unroll
-                for (int u = 0; u < Q; ++u) {
-                    const float *xe = xb + (int64_t)(rr[u] * xs_r + t * xs_t) * NP;
-                    const float *ye = yb + (int64_t)(t * ys_t + ss[u] * ys_s) * NP;
+            for (int e = 0; e < L; ++e) {
+                if (e < RS) {
+                    const int r = e / S, c = e - r * S;
+                    const float *xe = xb + (int64_t)(r * xs_r + t * xs_t) * NP;
+                    const float *ye = yb + (int64_t)(t * ys_t + c * ys_s) * NP;
                     if constexpr (NP == 2) {
                         const float2 xv = __ldg(reinterpret_cast<const float2 *>(xe));
                         const float2 yv = __ldg(reinterpret_cast<const float2 *>(ye));
-                        acc[u] = fmaf(xv.y, yv.x, acc[u]);
-                        acc[u] = fmaf(xv.x, yv.y, acc[u]);
-                        acc[u] = fmaf(xv.x, yv.x, acc[u]);
+                        acc[e] = fmaf(xv.y, yv.x, acc[e]);
+                        acc[e] = fmaf(xv.x, yv.y, acc[e]);
+                        acc[e] = fmaf(xv.x, yv.x, acc[e]);
                     } else {
                         const float x0 = __ldg(xe), x1 = __ldg(xe + 1), x2 = __ldg(xe + 2);
                         const float y0 = __ldg(ye), y1 = __ldg(ye + 1), y2 = __ldg(ye + 2);
-                        acc[u] = fmaf(x2, y0, acc[u]);
-                        acc[u] = fmaf(x1, y1, acc[u]);
-                        acc[u] = fmaf(x0, y2, acc[u]);
-                        acc[u] = fmaf(x1, y0, acc[u]);
-                        acc[u] = fmaf(x0, y1, acc[u]);
-                        acc[u] = fmaf(x0, y0, acc[u]);
+                        acc[e] = fmaf(x2, y0, acc[e]);
+                        acc[e] = fmaf(x1, y1, acc[e]);
+                        acc[e] = fmaf(x0, y2, acc[e]);
+                        acc[e] = fmaf(x1, y0, acc[e]);
+                        acc[e] = fmaf(x0, y1, acc[e]);
+                        acc[e] = fmaf(x0, y0, acc[e]);
                     }
                 }
             }
-            if (++since == F) {
-                since = 0;
-#pragma unroll
-                for (int u = 0; u < Q; ++u) {
-                    if constexpr (FF) two_sum_acc(shi[u], slo[u], acc[u]);
-                    else s64[u] += (double)acc[u];
-                    acc[u] = 0.f;
-                }
-            }
         }
+        if (++since == F) {
+            since = 0;
 #pragma unroll
-        for (int u = 0; u < Q; ++u) {
-            const int e = e0 + lane + 32 * u;
-            if (e < RS) {
-                double sum;
-                if constexpr (FF) sum = ((double)shi[u] + (double)slo[u]) + (double)acc[u];
-                else sum = s64[u] + (double)acc[u];
-                double val = a.alpha * sum;
-                if (a.dtype == BSM_FP64) {
-                    if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
-                    static_cast<double *>(a.out_data)[out_off + e] = val;
-                } else {
-                    if (old >= 0) val = fma(a.beta, (double)static_cast<const float *>(a.old_data)[old + e], val);
-                    static_cast<float *>(a.out_data)[out_off + e] = (float)val;
-                }
+            for (int e = 0; e < L; ++e) {
+                if constexpr (FF) two_sum_acc(shi[e], slo[e], acc[e]);
+                else s64[e] += (double)acc[e];
+                acc[e] = 0.f;
             }
         }
     }
-}
-
-template <int PREC, bool FF>
-__device__ __forceinline__ void cs_dispatch(const NumericArgs &a, int64_t q, int lane) {
-    const int32_t orc = a.out_blk_rc[q];
-    const int need = (rc_rows(orc) * rc_cols(orc) + 31) >> 5;
-    if (need <= 1) cs_item<PREC, 1, FF>(a, q, lane);
-    else if (need <= 2) cs_item<PREC, 2, FF>(a, q, lane);
-    else if (need <= 4) cs_item<PREC, 4, FF>(a, q, lane);
-    else cs_item<PREC, 8, FF>(a, q, lane);
+#pragma unroll
+    for (int e = 0; e < L; ++e) {
+        if (e < RS) {
+            double sum;
+            if constexpr (FF) sum = ((double)shi[e] + (double)slo[e]) + (double)acc[e];
+            else sum = s64[e] + (double)acc[e];
+            double val = a.alpha * sum;
+            if (a.dtype == BSM_FP64) {
+                if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
+                static_cast<double *>(a.out_data)[out_off + e] = val;
+            } else {
+                if (old >= 0) val = fma(a.beta, (double)static_cast<const float *>(a.old_data)[old + e], val);
+                static_cast<float *>(a.out_data)[out_off + e] = (float)val;
+            }
+        }
+    }
 }
 
 template <int PREC, bool FF>
@@ -619,19 +604,24 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC>();
     unsigned long long *ctr = a.work_counter;
     if (a.status && *a.status != 0) return;
+    // items [0, n0): a warp each on the tensor cores; items [n0, n_items):
+    // tiny blocks marked for the CUDA-core variant, 32 per ticket
+    const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
+    const int64_t n0 = a.n_items - n_lane;
+    const int64_t tickets = n0 + (n_lane + 31) / 32;
     while (true) {
-        int64_t q = 0;
-        if (lane == 0) q = (int64_t)atomicAdd(ctr, 1ull);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= a.n_items) break;
-        bool on_cores = false;
-        if (a.item_order) {
-            const uint32_t code = (uint32_t)a.item_order[q];
-            on_cores = (code >> 31) != 0;  // variant bit: CUDA-core split arithmetic
-            q = (int64_t)(code & 0x7fffffffu);
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tickets) break;
+        if (t < n0) {
+            int64_t q = t;
+            if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            tc_item<PREC, FF>(a, q, lane, ring);
+        } else {
+            const int64_t idx = n0 + (t - n0) * 32 + lane;
+            if (idx < a.n_items) cs_lane_item<PREC, FF>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
         }
-        if (on_cores) cs_dispatch<PREC, FF>(a, q, lane);
-        else tc_item<PREC, FF>(a, q, lane, ring);
     }
 }
 

@@ -99,9 +99,10 @@ def test_split_with_fp64_sum(bsm, oracle, prec, flush):
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x6", "bf16x3"])
 def test_cuda_core_split_variant(bsm, oracle, prec):
-    """Every output shape on the CUDA-core variant of the split arithmetic."""
+    """Tiny output shapes on the CUDA-core (lane per block) variant of the
+    split arithmetic, larger ones on the tensor cores, in one launch."""
     rng = np.random.default_rng(2)
-    bs = rng.integers(1, 30, size=40).astype(np.int32)
+    bs = rng.integers(1, 9, size=60).astype(np.int32)
     A, B = random_bcsr(bs, bs, 0.2, seed=141), random_bcsr(bs, bs, 0.2, seed=142)
     sizes = sorted(set(int(x) for x in bs))
     try:
@@ -162,23 +163,27 @@ def test_fp64_tiny_blocks_both_variants(bsm, oracle, variant):
 
 def test_autotune_table_roundtrip(bsm, oracle, tmp_path):
     from paper_1708_03604_gb300 import autotune
-    w = I.mixed_banded(nb=300, occ=0.1, eps=1e-6)
-    A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+    bs = I.mixed_sizes(200, (1, 2, 4, 7), (0.3, 0.3, 0.3, 0.1), seed=8)
+    Ah, Bh = random_bcsr(bs, bs, 0.05, seed=161), random_bcsr(bs, bs, 0.05, seed=162)
+    A, B = bsm.Matrix.from_host(Ah), bsm.Matrix.from_host(Bh)
+    sizes = (1, 2, 4, 7)
     try:
-        table = autotune.tune(A, B, w["eps"], prec="tf32x3", reps=1)
-        assert set(table["variants"]) == {f"{m}x{n}" for m in (5, 13, 23) for n in (5, 13, 23)}
-        path = str(tmp_path / "tune.json")
-        autotune.save([table], path)
-        autotune.reset("tf32x3", (5, 13, 23))
-        autotune.load(path)
-        for key, v in table["variants"].items():
-            m, n = (int(x) for x in key.split("x"))
-            assert bsm.bsm_get_variant("tf32x3", m, n) == v
-        Cg = bsm.multiply(1.0, A, B, eps=w["eps"], prec="tf32x3")
-        ref = oracle.multiply(1.0, w["A"], w["B"], eps=w["eps"])
-        assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-6
+        for prec in ("tf32x3", "fp64"):
+            table = autotune.tune(A, B, 0.0, prec=prec, reps=1)
+            assert set(table["variants"]) == {f"{m}x{n}" for m in sizes for n in sizes if m * n <= 16}
+            path = str(tmp_path / f"tune_{prec}.json")
+            autotune.save([table], path)
+            autotune.reset(prec, sizes)
+            autotune.load(path)
+            for key, v in table["variants"].items():
+                m, n = (int(x) for x in key.split("x"))
+                assert bsm.bsm_get_variant(prec, m, n) == v
+            Cg = bsm.multiply(1.0, A, B, prec=prec)
+            ref = oracle.multiply(1.0, Ah, Bh)
+            assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
     finally:
-        autotune.reset("tf32x3", (5, 13, 23))
+        autotune.reset("tf32x3", sizes)
+        autotune.reset("fp64", sizes)
 
 
 def test_ragged_sizes_and_large_blocks(bsm, oracle):
