@@ -185,6 +185,84 @@ __device__ __forceinline__ void cc_lane_item(const NumericArgs &a, int64_t q) {
     }
 }
 
+// Fixed shapes of the lane-per-block mode: column t of the X block and row t
+// of the Y block are loaded once per k and applied as a rank-1 update.
+template <typename T, int R, int S>
+__device__ __forceinline__ void cc_lane_fixed(const NumericArgs &a, int64_t q) {
+    const T *__restrict__ X = static_cast<const T *>(a.x_data);
+    const T *__restrict__ Y = static_cast<const T *>(a.y_data);
+    T *__restrict__ O = static_cast<T *>(a.out_data);
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+    double acc[R][S];
+    T acc_n[R][S];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            acc[r][c] = 0.0;
+            acc_n[r][c] = T(0);
+        }
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t ix = a.px[p], iy = a.py[p];
+        const T *xb = X + a.x_blk_off[ix];
+        const T *yb = Y + a.y_blk_off[iy];
+        const int32_t xrc = a.x_blk_rc[ix];
+        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+        const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+        const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+        for (int t = 0; t < Tn; ++t) {
+            T xv[R], yv[S];
+#pragma unroll
+            for (int r = 0; r < R; ++r) xv[r] = __ldg(xb + r * xs_r + t * xs_t);
+#pragma unroll
+            for (int c = 0; c < S; ++c) yv[c] = __ldg(yb + t * ys_t + c * ys_s);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < S; ++c) acc_n[r][c] = fma(xv[r], yv[c], acc_n[r][c]);
+        }
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < S; ++c) {
+                    acc[r][c] += (double)acc_n[r][c];
+                    acc_n[r][c] = T(0);
+                }
+        }
+    }
+    const T *OLD = static_cast<const T *>(a.old_data);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            const int e = r * S + c;
+            double v = (sizeof(T) == 8) ? (double)acc_n[r][c] : acc[r][c];
+            v = a.alpha * v;
+            if (old >= 0) v = fma(a.beta, (double)OLD[old + e], v);
+            O[out_off + e] = (T)v;
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void cc_lane_dispatch(const NumericArgs &a, int64_t q) {
+    const int32_t orc = a.out_blk_rc[q];
+    switch ((rc_rows(orc) << 8) | rc_cols(orc)) {
+        case 0x101: cc_lane_fixed<T, 1, 1>(a, q); break;
+        case 0x102: cc_lane_fixed<T, 1, 2>(a, q); break;
+        case 0x201: cc_lane_fixed<T, 2, 1>(a, q); break;
+        case 0x202: cc_lane_fixed<T, 2, 2>(a, q); break;
+        case 0x104: cc_lane_fixed<T, 1, 4>(a, q); break;
+        case 0x401: cc_lane_fixed<T, 4, 1>(a, q); break;
+        case 0x204: cc_lane_fixed<T, 2, 4>(a, q); break;
+        case 0x402: cc_lane_fixed<T, 4, 2>(a, q); break;
+        case 0x404: cc_lane_fixed<T, 4, 4>(a, q); break;
+        default: cc_lane_item<T>(a, q); break;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
     const int lane = threadIdx.x & 31;
@@ -207,7 +285,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
             if (idx < a.n_items) {
                 const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                cc_lane_item<T>(a, q);
+                cc_lane_dispatch<T>(a, q);
             }
         }
     }
@@ -597,6 +675,110 @@ __device__ __forceinline__ void cs_lane_item(const NumericArgs &a, int64_t q) {
     }
 }
 
+template <int PREC, bool FF, int R, int S>
+__device__ __forceinline__ void cs_lane_fixed(const NumericArgs &a, int64_t q) {
+    constexpr int NP = PrecTraits<PREC>::NP;
+    const float *__restrict__ X = a.x_plain;
+    const float *__restrict__ Y = a.y_plain;
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+    const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
+    float acc[R][S], shi[FF ? R : 1][FF ? S : 1], slo[FF ? R : 1][FF ? S : 1];
+    double s64[FF ? 1 : R][FF ? 1 : S];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            acc[r][c] = 0.f;
+            if constexpr (FF) {
+                shi[r][c] = 0.f;
+                slo[r][c] = 0.f;
+            } else {
+                s64[r][c] = 0.0;
+            }
+        }
+    int since = 0;
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t ix = a.px[p], iy = a.py[p];
+        const float *xb = X + a.x_blk_off[ix] * NP;
+        const float *yb = Y + a.y_blk_off[iy] * NP;
+        const int32_t xrc = a.x_blk_rc[ix];
+        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+        const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+        const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+        for (int t = 0; t < Tn; ++t) {
+            float xv[R][NP], yv[S][NP];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int pc = 0; pc < NP; ++pc) xv[r][pc] = __ldg(xb + (int64_t)(r * xs_r + t * xs_t) * NP + pc);
+#pragma unroll
+            for (int c = 0; c < S; ++c)
+#pragma unroll
+                for (int pc = 0; pc < NP; ++pc) yv[c][pc] = __ldg(yb + (int64_t)(t * ys_t + c * ys_s) * NP + pc);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < S; ++c) {
+                    if constexpr (NP == 2) {
+                        acc[r][c] = fmaf(xv[r][1], yv[c][0], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][0], yv[c][1], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][0], yv[c][0], acc[r][c]);
+                    } else {
+                        acc[r][c] = fmaf(xv[r][2], yv[c][0], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][1], yv[c][1], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][0], yv[c][2], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][1], yv[c][0], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][0], yv[c][1], acc[r][c]);
+                        acc[r][c] = fmaf(xv[r][0], yv[c][0], acc[r][c]);
+                    }
+                }
+        }
+        if (++since == F) {
+            since = 0;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < S; ++c) {
+                    if constexpr (FF) two_sum_acc(shi[r][c], slo[r][c], acc[r][c]);
+                    else s64[r][c] += (double)acc[r][c];
+                    acc[r][c] = 0.f;
+                }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            const int e = r * S + c;
+            double sum;
+            if constexpr (FF) sum = ((double)shi[r][c] + (double)slo[r][c]) + (double)acc[r][c];
+            else sum = s64[r][c] + (double)acc[r][c];
+            double val = a.alpha * sum;
+            if (a.dtype == BSM_FP64) {
+                if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
+                static_cast<double *>(a.out_data)[out_off + e] = val;
+            } else {
+                if (old >= 0) val = fma(a.beta, (double)static_cast<const float *>(a.old_data)[old + e], val);
+                static_cast<float *>(a.out_data)[out_off + e] = (float)val;
+            }
+        }
+}
+
+template <int PREC, bool FF>
+__device__ __forceinline__ void cs_lane_dispatch(const NumericArgs &a, int64_t q) {
+    const int32_t orc = a.out_blk_rc[q];
+    switch ((rc_rows(orc) << 8) | rc_cols(orc)) {
+        case 0x101: cs_lane_fixed<PREC, FF, 1, 1>(a, q); break;
+        case 0x104: cs_lane_fixed<PREC, FF, 1, 4>(a, q); break;
+        case 0x401: cs_lane_fixed<PREC, FF, 4, 1>(a, q); break;
+        case 0x404: cs_lane_fixed<PREC, FF, 4, 4>(a, q); break;
+        case 0x202: cs_lane_fixed<PREC, FF, 2, 2>(a, q); break;
+        default: cs_lane_item<PREC, FF>(a, q); break;
+    }
+}
+
 template <int PREC, bool FF>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t tc_smem[];
@@ -620,7 +802,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
             tc_item<PREC, FF>(a, q, lane, ring);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
-            if (idx < a.n_items) cs_lane_item<PREC, FF>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
+            if (idx < a.n_items) cs_lane_dispatch<PREC, FF>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
         }
     }
 }
