@@ -167,6 +167,23 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power)}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Maximum of a per-rank scalar (the step time) over all ranks; the
+    whole-job rate divides the units every rank processed by it."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput of `world` replicas (weak scaling), in units/ms."""
+    return world * units_per_rank / max_ms
+
+
 def traffic_from_profile():
     """DRAM bytes per launch of the numeric kernel from the committed ncu
     summary (None when absent or marked stale)."""
@@ -325,12 +342,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ms(x: float) -> float:
+        return max_over_ranks(x, world, "cuda")
 
     from paper_1708_03604_gb300 import bsm
 
@@ -370,10 +383,10 @@ def main():
     launches = bsm.bsm_get_launch_count() - launches0
     clk = clocks.stop()
     bsm.bsm_set_profiling(False)
-    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    ms = max_ms(e0.elapsed_time(e1)) / args.steps
     cnt = Cm.counts()
     flop = cnt.useful_flop
-    value = world * flop / (ms * 1e-3) / 1e12
+    value = job_rate(flop, world, ms) * 1e-9
     num_ms = statistics.mean(numeric_ms)
     achieved = flop / (num_ms * 1e-3) / 1e12
     traffic = traffic_from_profile()
@@ -407,7 +420,7 @@ def main():
             f1.record(stream)
             torch.cuda.synchronize()
             bsm.bsm_set_profiling(False)
-            sms = max_over_ranks(f0.elapsed_time(f1)) / ks
+            sms = max_ms(f0.elapsed_time(f1)) / ks
             err = (torch.linalg.vector_norm(Cm.data_tensor() - C64).item() / ref_norm)
             split[key] = {"value": world * flop / (sms * 1e-3) / 1e12, "ms_per_step": sms,
                            "numeric_ms": statistics.mean(num), "speedup_vs_fp64": ms / sms,
@@ -453,7 +466,7 @@ def main():
             d2h = inf.data_len * 8 + rp.nbytes + ci.nbytes + bo.nbytes
             if it > 0:
                 times.append(dt)
-        et = max_over_ranks(statistics.mean(times))
+        et = max_ms(statistics.mean(times))
         e2e = {"value": world * flop / et / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": et * 1e3,
                "includes": "host pattern validation, H2D of A and B from pinned memory, multiply, "
