@@ -57,7 +57,7 @@ def parse_args():
     p.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                    help="block rows/cols (smaller cases for profiling; the metric is quoted at 3000)")
     p.add_argument("--workload", default="mixed3000",
-                   choices=["mixed3000", "uniform23_200", "banded23_6912", "diff13_800", "purify_2000"],
+                   choices=["mixed3000", "uniform23_200", "banded23_6912", "diff13_800", "purify_2000", "smm_sweep"],
                    help="mixed3000 is the headline line; the others measure the remaining configurations")
     a = p.parse_args()
     if a.nb != WORKLOAD["nb"]:
@@ -298,6 +298,35 @@ def run_other(args):
         out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
                    config={"workload": name, "step": "multiply + both adjoints", "products": Cm.counts().products,
                            "useful_flop_per_step": flop}, split_precision={"tf32x3": legs["tf32x3"]})
+    elif name == "smm_sweep":
+        # square blocks m = n = k = s over the range of the paper's Fig. 1 (4..78):
+        # uniform random patterns sized so that A + B hold about 1 GB of FP64 data
+        rows = []
+        for s_ in (4, 5, 6, 8, 9, 12, 13, 16, 22, 23, 26, 32, 45, 64, 78):
+            nb = int(round((2.0e6 / (s_ * s_)) ** 0.5 / 0.1)) if s_ < 16 else int(round((1.0e9 / 8 / (s_ * s_) / 0.1) ** 0.5))
+            nb = max(40, min(nb, 6000))
+            bs = I.uniform_sizes(nb, s_)
+            occ = 0.1
+            Ah = I.assemble(bs, bs, *I.uniform_pattern(nb, nb, occ, I.SEED_A), seed=I.SEED_A + 100)
+            Bh = I.assemble(bs, bs, *I.uniform_pattern(nb, nb, occ, I.SEED_B), seed=I.SEED_B + 100)
+            A, B = bsm.Matrix.from_host(Ah), bsm.Matrix.from_host(Bh)
+            Cm = bsm.Matrix.empty(bs, bs)
+            row = {"s": s_, "nb": nb, "occupancy": occ}
+            bsm.bsm_set_profiling(True)
+            for prec in ("fp64", "tf32x3"):
+                num = []
+                ms = _timed(torch, lambda: (bsm.multiply(1.0, A, B, 0.0, Cm, 0.0, prec=prec, build_stacks=False),
+                                            num.append(Cm.timings()["numeric"])), args.steps, args.warmup)
+                flop = Cm.counts().useful_flop
+                nm = statistics.median(num[args.warmup:] or num)
+                row[prec] = {"step_tflops": flop / ms * 1e-9, "numeric_tflops": flop / nm * 1e-9, "numeric_ms": nm}
+            bsm.bsm_set_profiling(False)
+            row["products"] = Cm.counts().products
+            rows.append(row)
+            del A, B, Cm
+            torch.cuda.empty_cache()
+        out.update(value=None, config={"workload": name, "occupancy": 0.1,
+                                       "note": "per block size: one multiply of uniform s x s blocks"}, sweep=rows)
     else:  # purify_2000: the 10-step McWeeny chain as one CUDA graph
         w = I.purification_start(nb=2000)
         X0 = bsm.Matrix.from_host(w["X0"])

@@ -199,3 +199,21 @@ def test_purification_2000(env, oracle):
     torch.cuda.synchronize()
     assert g.status() == 0
     np.testing.assert_array_equal(g.result.data_host(), eager)
+
+
+@pytest.mark.parametrize("s", [4, 32, 45, 78])
+def test_square_block_sizes_sweep(env, oracle, s):
+    """Uniform s x s blocks over the range of the paper's kernel sweep
+    (4..78): several MMA tiles and super-tile passes per block for s > 32."""
+    bsm, torch = env
+    nb = 24 if s > 40 else 40
+    bs = I.uniform_sizes(nb, s)
+    Ah = I.assemble(bs, bs, *I.uniform_pattern(nb, nb, 0.25, I.SEED_A), seed=I.SEED_A + 100)
+    Bh = I.assemble(bs, bs, *I.uniform_pattern(nb, nb, 0.25, I.SEED_B), seed=I.SEED_B + 100)
+    A, B = bsm.Matrix.from_host(Ah), bsm.Matrix.from_host(Bh)
+    ref = oracle.multiply(1.0, Ah, Bh)
+    for prec, tol in (("fp64", 1e-12), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
+        Cm = bsm.multiply(1.0, A, B, prec=prec, build_stacks=False)
+        rp, ci, bo = Cm.pattern()
+        np.testing.assert_array_equal(ci, ref.C.col_idx)
+        assert rel_fro(Cm.data_host(), ref.C.data) <= tol, prec
