@@ -104,11 +104,13 @@ bsm_status bsm_set_profiling(int32_t on);
 bsm_status bsm_get_launch_count(int64_t *count);
 
 /* Numeric variant per precision and output block shape (m rows, n columns),
- * for tiny blocks (m*n <= 16; larger shapes always use variant 0):
+ * for tiny blocks (m*n <= 16, and on the FP64 paths 5 x 5 and 6 x 6; other
+ * shapes always use variant 0):
  * 0 = one warp per output block (FP64: lanes over its elements; split paths:
  * tensor-core MMA on packed fragments), 1 = one lane per output block on CUDA
  * cores (split paths: the same split pieces multiplied with FP32 FMA, exact
- * piece products).  -1 restores the library default (1);
+ * piece products).  -1 restores the library default (1 for m*n <= 16, 0 for
+ * 5 x 5 and 6 x 6);
  * bsm_get_variant returns the variant in effect.
  * Process-wide; the autotuner (paper_1708_03604_gb300/autotune.py) sets it
  * from measurements.  Applies to multiplies issued afterwards (a no-sync

@@ -5,8 +5,9 @@ ways to compute its block products:
 
 * variant 0: one warp per output block (FP64: lanes over its elements;
   split paths: tensor-core MMAs on packed fragments);
-* variant 1, for blocks of at most 16 elements: one lane per output block on
-  CUDA cores (split paths: the same narrow pieces multiplied with FP32 FMA).
+* variant 1, for blocks of at most 16 elements (FP64 also 5 x 5 and 6 x 6):
+  one lane per output block on CUDA cores (split paths: the same narrow
+  pieces multiplied with FP32 FMA).
 
 Which is faster depends on the shape and the product mix, so it is measured:
 starting from variant 0 everywhere, each shape in turn is switched to
@@ -42,7 +43,9 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
          gain: float = 0.01) -> dict:
     """Choose the variant of every output shape of A.B for `prec`; returns
     {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}."""
-    shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16]  # larger shapes have one variant
+    # larger shapes have one variant
+    fp64 = prec in ("fp64", "fp64_dmma")
+    shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16 or (fp64 and (m, n) in ((5, 5), (6, 6)))]
     for m, n in shapes:
         bsm.bsm_set_variant(prec, m, n, 0)
     Cm = bsm.Matrix.empty(A.row_bs, B.col_bs)

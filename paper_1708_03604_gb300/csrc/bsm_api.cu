@@ -26,15 +26,24 @@ int64_t *g_host = nullptr;  // pinned host words for small device->host reads
 int8_t g_variant[5][kMaxBlockDim + 1][kMaxBlockDim + 1];
 bool g_variant_init = false;
 
+// shapes the lane-per-block variant takes: up to 16 elements, plus 5 x 5 and
+// 6 x 6 on the FP64 paths
+bool lane_eligible(int prec, int m, int n) {
+    const bool fp64 = prec == BSM_P_FP64 || prec == BSM_P_FP64_DMMA;
+    return m * n <= 16 || (fp64 && ((m == 5 && n == 5) || (m == 6 && n == 6)));
+}
+
 int variant_of(int prec, int m, int n) {
     if (!g_variant_init) {
         std::memset(g_variant, -1, sizeof(g_variant));
         g_variant_init = true;
     }
     const int v = g_variant[prec][m][n];
-    // variant 1: one lane per output block (CUDA cores), for up to 16 elements
-    if (m * n > 16) return 0;
-    return v < 0 ? 1 : v;
+    // variant 1: one lane per output block (CUDA cores), for blocks of up to 16
+    // elements (default) and for 5 x 5 and 6 x 6 blocks (on request)
+    if (!lane_eligible(prec, m, n)) return 0;
+    if (v >= 0) return v;
+    return m * n <= 16 ? 1 : 0;
 }
 std::atomic<int64_t> g_launches{0};
 

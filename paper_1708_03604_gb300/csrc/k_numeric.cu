@@ -259,6 +259,8 @@ __device__ __forceinline__ void cc_lane_dispatch(const NumericArgs &a, int64_t q
         case 0x204: cc_lane_fixed<T, 2, 4>(a, q); break;
         case 0x402: cc_lane_fixed<T, 4, 2>(a, q); break;
         case 0x404: cc_lane_fixed<T, 4, 4>(a, q); break;
+        case 0x505: cc_lane_fixed<T, 5, 5>(a, q); break;
+        case 0x606: cc_lane_fixed<T, 6, 6>(a, q); break;
         default: cc_lane_item<T>(a, q); break;
     }
 }

@@ -130,16 +130,19 @@ def test_cuda_core_split_variant(bsm, oracle, prec):
 
 @pytest.mark.parametrize("variant", [0, 1])
 def test_fp64_tiny_blocks_both_variants(bsm, oracle, variant):
-    """Blocks of 1..4 rows/columns: one warp per output block (0) or one lane
-    per output block (1), forward and adjoints, against the oracle."""
+    """Blocks of 1, 2, 4, 5 and 6 rows/columns: one warp per output block (0)
+    or one lane per output block (1, where eligible), forward and adjoints,
+    against the oracle."""
     import torch
-    bs = I.mixed_sizes(120, (1, 2, 4), (0.4, 0.3, 0.3), seed=5)
+    bs = I.mixed_sizes(120, (1, 2, 4, 5, 6), (0.3, 0.2, 0.2, 0.15, 0.15), seed=5)
     A, B = random_bcsr(bs, bs, 0.1, seed=151), random_bcsr(bs, bs, 0.1, seed=152)
+    sz = (1, 2, 4, 5, 6)
     try:
-        for m in (1, 2, 4):
-            for n in (1, 2, 4):
+        for m in sz:
+            for n in sz:
                 bsm.bsm_set_variant("fp64", m, n, variant)
-                assert bsm.bsm_get_variant("fp64", m, n) == variant
+                eligible = m * n <= 16 or (m, n) in ((5, 5), (6, 6))
+                assert bsm.bsm_get_variant("fp64", m, n) == (variant if eligible else 0)
         Cg, ref, gA, gB = _run(bsm, oracle, A, B, 1e-3, beta=0.5, C0=random_bcsr(bs, bs, 0.05, seed=153))
         _check_pattern(Cg, ref.C)
         assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-12
@@ -156,8 +159,8 @@ def test_fp64_tiny_blocks_both_variants(bsm, oracle, variant):
         Cg, ref, _, _ = _run(bsm, oracle, A32, B32, 0.0)
         assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-5
     finally:
-        for m in (1, 2, 4):
-            for n in (1, 2, 4):
+        for m in sz:
+            for n in sz:
                 bsm.bsm_set_variant("fp64", m, n, -1)
 
 
@@ -171,6 +174,7 @@ def test_autotune_table_roundtrip(bsm, oracle, tmp_path):
         for prec in ("tf32x3", "fp64"):
             table = autotune.tune(A, B, 0.0, prec=prec, reps=1)
             assert set(table["variants"]) == {f"{m}x{n}" for m in sizes for n in sizes if m * n <= 16}
+            assert "7x7" not in table["variants"]
             path = str(tmp_path / f"tune_{prec}.json")
             autotune.save([table], path)
             autotune.reset(prec, sizes)
