@@ -587,8 +587,10 @@ bsm_status bsm_create(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_b
     // pattern checks (host, before any launch)
     if (nbr > 0 && !row_bs) return set_error(BSM_ERR_ARG, "row_bs is NULL");
     if (nbc > 0 && !col_bs) return set_error(BSM_ERR_ARG, "col_bs is NULL");
-    std::vector<std::pair<int64_t, int64_t>> spans;
-    spans.reserve((size_t)nnzb);
+    // one pass; blocks laid out in CSR order with increasing offsets (the
+    // usual layout) are proven disjoint on the way, anything else is sorted
+    bool in_order = true;
+    int64_t prev_end = 0;
     for (int32_t i = 0; i < nbr; ++i) {
         for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
             const int32_t j = col_idx[b];
@@ -598,12 +600,20 @@ bsm_status bsm_create(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_b
                 return set_error(BSM_ERR_ARG, "block size outside [1, 256]");
             const int64_t len = (int64_t)row_bs[i] * col_bs[j];
             if (blk_off[b] < 0 || blk_off[b] + len > data_len) return set_error(BSM_ERR_ARG, "block outside data_len");
-            spans.emplace_back(blk_off[b], len);
+            if (blk_off[b] < prev_end) in_order = false;
+            prev_end = blk_off[b] + len;
         }
     }
-    std::sort(spans.begin(), spans.end());
-    for (size_t q = 1; q < spans.size(); ++q)
-        if (spans[q - 1].first + spans[q - 1].second > spans[q].first) return set_error(BSM_ERR_ARG, "blocks overlap");
+    if (!in_order) {
+        std::vector<std::pair<int64_t, int64_t>> spans;
+        spans.reserve((size_t)nnzb);
+        for (int32_t i = 0; i < nbr; ++i)
+            for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b)
+                spans.emplace_back(blk_off[b], (int64_t)row_bs[i] * col_bs[col_idx[b]]);
+        std::sort(spans.begin(), spans.end());
+        for (size_t q = 1; q < spans.size(); ++q)
+            if (spans[q - 1].first + spans[q - 1].second > spans[q].first) return set_error(BSM_ERR_ARG, "blocks overlap");
+    }
     if (data_mode == BSM_DATA_BORROW && data) {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, data) != cudaSuccess ||
