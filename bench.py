@@ -433,10 +433,11 @@ def main():
     tuned = {"fp64": tuned_fp64}
     if not args.no_split:
         from paper_1708_03604_gb300 import autotune
-        for prec in ("tf32x3", "bf16x6", "bf16x3"):
+        for prec in ("ozaki", "tf32x3", "bf16x6", "bf16x3"):
             tuned[prec] = autotune.tune(A, B, eps, prec=prec, reps=2)
         ref_norm = torch.linalg.vector_norm(C64).item()
-        for key, prec, fl in (("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
+        for key, prec, fl in (("ozaki", "ozaki", 0), ("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0),
+                              ("bf16x3", "bf16x3", 0),
                               ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2),
                               ("tf32x3_pair4", "tf32x3", -4), ("bf16x6_pair4", "bf16x6", -4)):
             step(prec, fl)

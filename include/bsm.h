@@ -60,7 +60,19 @@ typedef enum {
     BSM_P_FP64_DMMA = 1,  /* accepted; runs the FP64 FMA path (same FP64 pipe rate) */
     BSM_P_TF32x3 = 2,     /* hi/lo TF32 split, 3 tensor-core products, FP32 accumulate, FP64 sum */
     BSM_P_BF16x3 = 3,     /* hi/lo BF16 split, 3 products                    */
-    BSM_P_BF16x6 = 4      /* hi/mid/lo BF16 split, 6 products                */
+    BSM_P_BF16x6 = 4,     /* hi/mid/lo BF16 split, 6 products                */
+    BSM_P_OZAKI = 5       /* error-free slicing after Ozaki et al. (2012): every
+                             row of the left operand and every column of the
+                             right one is put on its own power-of-two fixed-point
+                             grid and cut into 6 BF16 slices of at most 9 bits;
+                             the 21 slice products with slice levels p + q <= 5
+                             run on the tensor cores, levels 0..3 summed exactly
+                             in FP32 (the sum is flushed to FP64 before 64 terms
+                             of k), levels 4..5 in one rounded FP32 sum.  Error
+                             per term of k below 2^-44 of the product of the
+                             row's and the column's largest |x|; FP64 data only
+                             (BSM_ERR_UNSUPPORTED for FP32).  Non-finite inputs
+                             give non-finite outputs in their rows / columns.  */
 } bsm_prec;
 
 typedef struct {
@@ -72,7 +84,8 @@ typedef struct {
                               refreshed every F block products; F < 0:
                               compensated FP32 pair (TwoSum) refreshed every -F
                               products, converted to FP64 at the end; 0: as -1.
-                              Range [-1024, 1024].                                 */
+                              Range [-1024, 1024].  BSM_P_OZAKI ignores it (its
+                              flushes follow from the exact-sum bound).            */
     int32_t no_sync;       /* 1: no host synchronisation (CUDA-graph capturable); see
                               bsm_multiply and bsm_add                               */
     int32_t reserved[3];   /* must be zero                                          */
@@ -104,13 +117,13 @@ bsm_status bsm_set_profiling(int32_t on);
 bsm_status bsm_get_launch_count(int64_t *count);
 
 /* Numeric variant per precision and output block shape (m rows, n columns),
- * for tiny blocks (m*n <= 16, and on the FP64 paths 5 x 5 and 6 x 6; other
- * shapes always use variant 0):
- * 0 = one warp per output block (FP64: lanes over its elements; split paths:
- * tensor-core MMA on packed fragments), 1 = one lane per output block on CUDA
- * cores (split paths: the same split pieces multiplied with FP32 FMA, exact
- * piece products).  -1 restores the library default (1 for m*n <= 16, 0 for
- * 5 x 5 and 6 x 6);
+ * for tiny blocks (m*n <= 16, and on the FP64 and Ozaki paths 5 x 5 and
+ * 6 x 6; other shapes always use variant 0):
+ * 0 = one warp per output block (FP64: lanes over its elements; split and
+ * Ozaki paths: tensor-core MMA on packed fragments), 1 = one lane per output
+ * block on CUDA cores (split paths: the same split pieces multiplied with FP32
+ * FMA, exact piece products; Ozaki path: plain FP64 FMA).  -1 restores the
+ * library default (1 for m*n <= 16, 0 for 5 x 5 and 6 x 6);
  * bsm_get_variant returns the variant in effect.
  * Process-wide; the autotuner (paper_1708_03604_gb300/autotune.py) sets it
  * from measurements.  Applies to multiplies issued afterwards (a no-sync

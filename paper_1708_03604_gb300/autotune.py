@@ -44,7 +44,7 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
     """Choose the variant of every output shape of A.B for `prec`; returns
     {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}."""
     # larger shapes have one variant
-    fp64 = prec in ("fp64", "fp64_dmma")
+    fp64 = prec in ("fp64", "fp64_dmma", "ozaki")  # lane variant = plain FP64 FMA
     shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16 or (fp64 and (m, n) in ((5, 5), (6, 6)))]
     for m, n in shapes:
         bsm.bsm_set_variant(prec, m, n, 0)

@@ -24,9 +24,9 @@ BSM_OK, BSM_ERR_ARG, BSM_ERR_BLOCKING, BSM_ERR_CAPACITY, BSM_ERR_ALLOC, BSM_ERR_
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_BLOCKING", "ERR_CAPACITY", "ERR_ALLOC", "ERR_CUDA", "ERR_TIMEOUT",
                 "ERR_UNSUPPORTED"]
 BSM_FP64, BSM_FP32 = 0, 1
-BSM_P_FP64, BSM_P_FP64_DMMA, BSM_P_TF32x3, BSM_P_BF16x3, BSM_P_BF16x6 = range(5)
+BSM_P_FP64, BSM_P_FP64_DMMA, BSM_P_TF32x3, BSM_P_BF16x3, BSM_P_BF16x6, BSM_P_OZAKI = range(6)
 PREC = {"fp64": BSM_P_FP64, "fp64_dmma": BSM_P_FP64_DMMA, "tf32x3": BSM_P_TF32x3, "bf16x3": BSM_P_BF16x3,
-        "bf16x6": BSM_P_BF16x6}
+        "bf16x6": BSM_P_BF16x6, "ozaki": BSM_P_OZAKI}
 BSM_DATA_COPY, BSM_DATA_BORROW = 0, 1
 TIMING_PHASES = ["norms", "symbolic", "fill", "stacks", "numeric", "post", "total"]
 

@@ -23,13 +23,13 @@ bool g_pool_configured = false;
 int64_t *g_host = nullptr;  // pinned host words for small device->host reads
 // numeric variant per (precision, rows, cols) of the output block; -1 = the
 // library default (see variant_of)
-int8_t g_variant[5][kMaxBlockDim + 1][kMaxBlockDim + 1];
+int8_t g_variant[6][kMaxBlockDim + 1][kMaxBlockDim + 1];
 bool g_variant_init = false;
 
 // shapes the lane-per-block variant takes: up to 16 elements, plus 5 x 5 and
-// 6 x 6 on the FP64 paths
+// 6 x 6 on the paths whose lane variant is plain FP64 FMA
 bool lane_eligible(int prec, int m, int n) {
-    const bool fp64 = prec == BSM_P_FP64 || prec == BSM_P_FP64_DMMA;
+    const bool fp64 = prec == BSM_P_FP64 || prec == BSM_P_FP64_DMMA || prec == BSM_P_OZAKI;
     return m * n <= 16 || (fp64 && ((m == 5 && n == 5) || (m == 6 && n == 6)));
 }
 
@@ -147,7 +147,7 @@ bsm_status check_opts(const bsm_opts *o, bsm_opts *out) {
     bsm_opts_default(out);
     if (!o) return BSM_OK;
     *out = *o;
-    if (o->prec < BSM_P_FP64 || o->prec > BSM_P_BF16x6) return set_error(BSM_ERR_ARG, "opts.prec out of range");
+    if (o->prec < BSM_P_FP64 || o->prec > BSM_P_OZAKI) return set_error(BSM_ERR_ARG, "opts.prec out of range");
     if (o->flush_every < -1024 || o->flush_every > 1024) return set_error(BSM_ERR_ARG, "opts.flush_every outside [-1024, 1024]");
     if (o->no_sync != 0 && o->no_sync != 1) return set_error(BSM_ERR_ARG, "opts.no_sync must be 0 or 1");
     for (int q = 0; q < 3; ++q)
@@ -155,7 +155,66 @@ bsm_status check_opts(const bsm_opts *o, bsm_opts *out) {
     return BSM_OK;
 }
 
-bool is_tc(int prec) { return prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6; }
+bool is_tc(int prec) {
+    return prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6 || prec == BSM_P_OZAKI;
+}
+// split paths whose lane variant multiplies unpacked FP32 pieces
+bool needs_plain(int prec) { return is_tc(prec) && prec != BSM_P_OZAKI; }
+
+// first global row / column of every block row / column, on the device
+bsm_status ensure_starts(bsm_mat *M) {
+    if (M->row_start && M->col_start) return BSM_OK;
+    std::vector<int32_t> rs((size_t)M->nbr + 1), cs((size_t)M->nbc + 1);
+    int64_t t = 0;
+    for (int32_t i = 0; i < M->nbr; ++i) {
+        rs[i] = (int32_t)t;
+        t += M->h_row_bs[i];
+        if (t > INT32_MAX) return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31 - 1 rows");
+    }
+    rs[M->nbr] = (int32_t)t;
+    t = 0;
+    for (int32_t j = 0; j < M->nbc; ++j) {
+        cs[j] = (int32_t)t;
+        t += M->h_col_bs[j];
+        if (t > INT32_MAX) return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31 - 1 columns");
+    }
+    cs[M->nbc] = (int32_t)t;
+    bsm_status st;
+    int32_t *r = nullptr, *c = nullptr;
+    if ((st = dalloc_t(&r, rs.size()))) return st;
+    if ((st = dalloc_t(&c, cs.size()))) {
+        dfree(r);
+        return st;
+    }
+    // pageable sources: the calls return once the host data has been taken
+    cudaError_t e = cudaMemcpyAsync(r, rs.data(), sizeof(int32_t) * rs.size(), cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c, cs.data(), sizeof(int32_t) * cs.size(), cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    if (e != cudaSuccess) {
+        dfree(r);
+        dfree(c);
+        return cuda_check(e, "copy block starts");
+    }
+    M->row_start = r;
+    M->col_start = c;
+    return BSM_OK;
+}
+
+// Ozaki path: per-line exponents of M in a role (X lines = logical rows, Y
+// lines = logical columns; stored rows when role_y == trans)
+struct OzLines {
+    int32_t *line0 = nullptr, *exps = nullptr;
+};
+bsm_status oz_lines(Scratch &sc, const bsm_mat *M, int role_y, int trans, OzLines &ol) {
+    const int by_rows = role_y == trans ? 1 : 0;
+    int64_t nlines = 0;
+    for (int32_t v : (by_rows ? M->h_row_bs : M->h_col_bs)) nlines += v;
+    bsm_status st;
+    if ((st = sc.get(&ol.line0, (size_t)M->nnzb)) || (st = sc.get(&ol.exps, (size_t)nlines))) return st;
+    cudaError_t e = cudaMemsetAsync(ol.exps, 0, sizeof(int32_t) * (size_t)nlines, g_stream);
+    if (e == cudaSuccess) e = launch_oz_lines(M, by_rows, ol.line0, ol.exps, g_stream);
+    return cuda_check(e, "line exponents");
+}
 
 // packed fragment planes of one operand (tensor-core paths)
 struct Packed {
@@ -176,10 +235,13 @@ bsm_status pack_prepare(Scratch &sc, const bsm_mat *M, int role_y, int trans, in
 }
 
 bsm_status pack_fill(Scratch &sc, const bsm_mat *M, int role_y, int trans, int prec, Packed &pk,
-                     int64_t total_words) {
+                     int64_t total_words, OzLines *ol = nullptr) {
     bsm_status st;
     if ((st = sc.get(&pk.words, (size_t)total_words + 16)) != BSM_OK) return st;
-    return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, nullptr, g_stream), "pack");
+    if (prec == BSM_P_OZAKI && (st = oz_lines(sc, M, role_y, trans, *ol))) return st;
+    return cuda_check(launch_pack(M, role_y, trans, prec, pk.off, pk.words, nullptr, g_stream,
+                                  ol ? ol->line0 : nullptr, ol ? ol->exps : nullptr),
+                      "pack");
 }
 
 // Rank of every block row of X in a breadth-first order through shared block
@@ -729,6 +791,8 @@ bsm_status bsm_destroy(bsm_t X) {
     free_pattern(X);
     dfree(X->row_bs);
     dfree(X->col_bs);
+    dfree(X->row_start);
+    dfree(X->col_start);
     dfree(X->status);
     delete X;
     return BSM_OK;
@@ -822,6 +886,14 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         if (opts.post_filter) return set_error(BSM_ERR_UNSUPPORTED, "no_sync excludes post_filter");
     } else if ((st = ensure_globals())) {
         return st;
+    }
+    if (opts.prec == BSM_P_OZAKI) {
+        if (A->dtype != BSM_FP64) return set_error(BSM_ERR_UNSUPPORTED, "BSM_P_OZAKI needs FP64 data");
+        if (no_sync) {
+            if (!A->row_start || !B->row_start) return set_error(BSM_ERR_ARG, "no_sync needs an earlier eager multiply");
+        } else if ((st = ensure_starts(A)) || (st = ensure_starts(B))) {
+            return st;
+        }
     }
     if ((st = ensure_status(C))) return st;
 
@@ -1016,12 +1088,17 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     ev.mark(4);
 
     // ---- a5/a6: numeric
+    OzLines olA, olB;
     if (tc) {
         if ((st = sc.get(&pkA.words, (size_t)packA_words + 16)) || (st = sc.get(&pkB.words, (size_t)packB_words + 16)))
             return st;
-        e = launch_pack(A, 0, 0, opts.prec, pkA.off, pkA.words, no_sync ? C->status : nullptr, g_stream);
+        if (opts.prec == BSM_P_OZAKI && ((st = oz_lines(sc, A, 0, 0, olA)) || (st = oz_lines(sc, B, 1, 0, olB))))
+            return st;
+        e = launch_pack(A, 0, 0, opts.prec, pkA.off, pkA.words, no_sync ? C->status : nullptr, g_stream, olA.line0,
+                        olA.exps);
         if (e == cudaSuccess)
-            e = launch_pack(B, 1, 0, opts.prec, pkB.off, pkB.words, no_sync ? C->status : nullptr, g_stream);
+            e = launch_pack(B, 1, 0, opts.prec, pkB.off, pkB.words, no_sync ? C->status : nullptr, g_stream,
+                            olB.line0, olB.exps);
         if ((st = cuda_check(e, "pack"))) return st;
     }
     NumericArgs na{};
@@ -1043,6 +1120,8 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.flush_every = opts.flush_every;
     na.x_pack = pkA.words; na.x_pack_off = pkA.off;
     na.y_pack = pkB.words; na.y_pack_off = pkB.off;
+    na.x_exp = olA.exps; na.x_line0 = olA.line0;
+    na.y_exp = olB.exps; na.y_line0 = olB.line0;
     na.status = no_sync ? C->status : nullptr;
     if ((st = sc.get(&na.work_counter, 2))) return st;
     int32_t *order = nullptr;
@@ -1062,7 +1141,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             return st;
     }
     na.n_lane_items = n_marked;
-    if (tc && uses_cores) {  // unpacked pieces for the CUDA-core variant (tensor-core paths)
+    if (needs_plain(opts.prec) && uses_cores) {  // unpacked pieces for the CUDA-core split variant
         const int np = split_pieces(opts.prec);
         float *xp = nullptr, *yp = nullptr;
         if ((st = sc.get(&xp, (size_t)A->data_len * np))) return st;
@@ -1187,13 +1266,19 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
     if (C->prod_A != A || C->prod_B != B || C->prod_A_nnzb != A->nnzb || C->prod_B_nnzb != B->nnzb || !C->cptr)
         return set_error(BSM_ERR_ARG, "C does not hold the product list of a multiply of these A and B");
     if ((st = ensure_globals())) return st;
+    if (opts.prec == BSM_P_OZAKI) {
+        if (C->dtype != BSM_FP64) return set_error(BSM_ERR_UNSUPPORTED, "BSM_P_OZAKI needs FP64 data");
+        if ((st = ensure_starts(A)) || (st = ensure_starts(B)) || (st = ensure_starts(C))) return st;
+    }
     Scratch sc;
     const bool tc = is_tc(opts.prec);
-    // dC as a matrix with C's pattern
+    // dC as a matrix with C's pattern (a view: owns nothing)
     bsm_mat dC;
     dC.nbr = C->nbr; dC.nbc = C->nbc; dC.dtype = C->dtype; dC.nnzb = C->nnzb; dC.data_len = C->data_len;
+    dC.h_row_bs = C->h_row_bs; dC.h_col_bs = C->h_col_bs;
     dC.row_bs = C->row_bs; dC.col_bs = C->col_bs; dC.row_ptr = C->row_ptr; dC.col_idx = C->col_idx;
     dC.blk_off = C->blk_off; dC.blk_rc = C->blk_rc; dC.data = const_cast<void *>(dC_data);
+    dC.row_start = C->row_start; dC.col_start = C->col_start;
     const int64_t nprod = C->nprod;
     for (int side = 0; side < 2; ++side) {
         void *out = side == 0 ? dA_data : dB_data;
@@ -1224,14 +1309,15 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         const bsm_mat *Y = side == 0 ? B : &dC;
         const int xt = side == 0 ? 0 : 1, yt = side == 0 ? 1 : 0;
         Packed pkX, pkY;
+        OzLines olX, olY;
         if (tc && nprod > 0) {
             if ((st = pack_prepare(sc, X, 0, xt, opts.prec, pkX))) return st;
             if ((st = pack_prepare(sc, Y, 1, yt, opts.prec, pkY))) return st;
             const int64_t *src[2] = {pkX.off + X->nnzb, pkY.off + Y->nnzb};
             if ((st = read_words(src, 2))) return st;
             const int64_t wx = g_host[0], wy = g_host[1];
-            if ((st = pack_fill(sc, X, 0, xt, opts.prec, pkX, wx))) return st;
-            if ((st = pack_fill(sc, Y, 1, yt, opts.prec, pkY, wy))) return st;
+            if ((st = pack_fill(sc, X, 0, xt, opts.prec, pkX, wx, &olX))) return st;
+            if ((st = pack_fill(sc, Y, 1, yt, opts.prec, pkY, wy, &olY))) return st;
         }
         NumericArgs na{};
         na.n_items = OUT->nnzb;
@@ -1250,6 +1336,8 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.flush_every = opts.flush_every;
         na.x_pack = pkX.words; na.x_pack_off = pkX.off;
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;
+        na.x_exp = olX.exps; na.x_line0 = olX.line0;
+        na.y_exp = olY.exps; na.y_line0 = olY.line0;
         if ((st = sc.get(&na.work_counter, 2))) return st;
         int32_t *item_order = nullptr;
         int64_t *n_marked = nullptr;
@@ -1258,7 +1346,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
                               opts.prec, &uses_cores, &n_marked)))
             return st;
         na.n_lane_items = n_marked;
-        if (tc && uses_cores && nprod > 0) {
+        if (needs_plain(opts.prec) && uses_cores && nprod > 0) {
             const int np = split_pieces(opts.prec);
             float *xp = nullptr, *yp = nullptr;
             cudaError_t e;
@@ -1448,7 +1536,7 @@ bsm_status bsm_add_backward(bsm_t Z, const void *dZ_data, bsm_t X, bsm_t Y, void
 }
 
 bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant) {
-    if (prec < BSM_P_FP64 || prec > BSM_P_BF16x6 || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim ||
+    if (prec < BSM_P_FP64 || prec > BSM_P_OZAKI || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim ||
         variant < -1 || variant > 1)
         return set_error(BSM_ERR_ARG, "bsm_set_variant: argument out of range");
     variant_of(prec, m, n);  // initialises the table
@@ -1457,7 +1545,7 @@ bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant) 
 }
 
 bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant) {
-    if (!variant || prec < BSM_P_FP64 || prec > BSM_P_BF16x6 || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim)
+    if (!variant || prec < BSM_P_FP64 || prec > BSM_P_OZAKI || m < 1 || m > kMaxBlockDim || n < 1 || n > kMaxBlockDim)
         return set_error(BSM_ERR_ARG, "bsm_get_variant: argument out of range");
     *variant = variant_of(prec, m, n);
     return BSM_OK;

@@ -93,6 +93,9 @@ struct bsm_mat {
     // rank of every block row in a breadth-first order through shared block
     // columns (built on demand, dropped with the pattern); schedules numeric work
     int32_t *row_rank = nullptr;        // [nbr]
+    // first global row / column of every block row / column ([nbr+1], [nbc+1];
+    // built on demand, kept until the handle is destroyed)
+    int32_t *row_start = nullptr, *col_start = nullptr;
     // column-major copy of the pattern (built on demand, dropped with the pattern)
     int64_t *t_ptr = nullptr;           // [nbc+1]
     int32_t *t_row = nullptr, *t_blk = nullptr;  // [nnzb]
@@ -239,8 +242,16 @@ struct NumericArgs {
                                   // item_order are tiny blocks computed one per lane
     const int32_t *status;      // nullable: the kernel does nothing when *status != 0
     unsigned long long *work_counter;  // 8 bytes of device memory, zeroed by the launcher
+    // Ozaki path: biased FP64 exponent field of the largest |x| of every global
+    // line (logical rows of X, logical columns of Y) and the first line of every block
+    const int32_t *x_exp, *x_line0, *y_exp, *y_line0;
 };
 cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s);
+
+// Ozaki path: line0[b] = first global line of block b, lines being the stored
+// rows (by_rows) or the stored columns of M's blocks; exps[line] = max biased
+// exponent field of |x| over the line (exps zeroed by the caller).
+cudaError_t launch_oz_lines(const bsm_mat *M, int by_rows, int32_t *line0, int32_t *exps, cudaStream_t s);
 
 // Tensor-core paths: packed fragment planes of a matrix in role X (A
 // fragments, logical R x T) or Y (B fragments, logical T x S).
@@ -249,8 +260,10 @@ struct PackInfo {
 };
 cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec, int64_t *pack_words,
                               cudaStream_t s);
+// line0 / exps: the Ozaki path's line exponents of M in this role (else null)
 cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
-                        void *pack, const int32_t *status, cudaStream_t s);
+                        void *pack, const int32_t *status, cudaStream_t s, const int32_t *line0 = nullptr,
+                        const int32_t *exps = nullptr);
 // Unpacked split pieces of M's data (split_pieces(prec) floats per element).
 int split_pieces(int prec);
 cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStream_t s);

@@ -810,6 +810,239 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
 }
 
 // =====================================================================
+// Ozaki-style error-free slicing (BSM_P_OZAKI)
+// =====================================================================
+// Error-free transformation of a product into products of short-mantissa
+// operands (Ozaki, Ogita, Oishi and Rump, 2012).  With 2^e the largest power
+// of two not above max |x| over a line (a logical row of X, a logical column
+// of Y), every x of the line is cut into integer digits
+//   x * 2^(7-e) = d_0 + d_1 2^-9 + ... + d_5 2^-45 + rest,   |rest| <= 2^-46,
+// d_0 = rint(x * 2^(7-e)) and each next digit the rounded remainder times 2^9,
+// so |d_p| <= 256 and the slice d_p * 2^(-9p) is exact in BF16.  A slice
+// product of level l = p + q lies on the grid 2^(-9l) (in units of the line
+// pair's scale 2^(ex+ey-14)); products of one level summed in the tensor
+// core's FP32 accumulator stay exact while the sum stays below 2^24 grid
+// units: a level holding c slice pairs takes 2^24 / (c * 2^16) terms of k,
+// 64 for level 3 (4 pairs).  Levels 0..3 have exact FP32 sums that move into
+// an FP64 sum before more than kOzWindow terms of k; levels 4 and 5 (11
+// pairs, below 2^-33 of level 0) share one rounded FP32 sum; levels >= 6 are
+// dropped (below 2^-50 of level 0).  Per term of k the error is below
+// 2^-44 of 2^(ex+ey): the rounded sum (at most 11 roundings of 2^-23 of
+// 64 * 2^16 * 5 * 2^-36 units per term of k) plus the cut digits and levels.
+constexpr int kOzSlices = 6;
+constexpr int kOzLevels = 5;    // FP32 sums: levels 0, 1, 2, 3 exact, 4..5 rounded
+constexpr int kOzWindow = 64;
+constexpr int kOzStages = 3;
+constexpr int kOzXW = 4 * kOzSlices;                 // X words per lane per tile
+constexpr int kOzYW = 2 * kOzSlices;                 // Y words per lane per tile
+constexpr int kOzSW = kOzXW + 2 * kOzYW;             // ring words per lane per stage (1 x 2 tiles)
+__host__ __device__ constexpr int oz_ring_words_per_warp() { return kOzStages * 32 * kOzSW; }
+
+// One pass over a 1 x NTC super tile (16 x 8*NTC output elements) at (mt0, nt0).
+template <int NTC>
+__device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
+                                        uint32_t *ring) {
+    constexpr int ST = kOzStages, SW = kOzSW;
+    const int32_t orc = a.out_blk_rc[q];
+    const int R = rc_rows(orc), S = rc_cols(orc);
+    const int MT = (R + 15) >> 4, NT = (S + 7) >> 3;
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const uint32_t *XP = static_cast<const uint32_t *>(a.x_pack);
+    const uint32_t *YP = static_cast<const uint32_t *>(a.y_pack);
+    uint32_t *myring = ring + lane * SW;
+    const uint32_t ring_s = smem_addr(myring);
+
+    float acc[kOzLevels][NTC][4];
+    double s64[NTC][4];
+#pragma unroll
+    for (int j = 0; j < NTC; ++j)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            s64[j][v] = 0.0;
+#pragma unroll
+            for (int l = 0; l < kOzLevels; ++l) acc[l][j][v] = 0.f;
+        }
+    int kacc = 0;  // terms of k in the open exact window
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+        const int nb = (int)min((int64_t)32, p1 - pb);
+        int64_t mxo = 0, myo = 0;
+        int mkt = 0, mtn = 0;
+        if (lane < nb) {
+            const int32_t ix = a.px[pb + lane], iy = a.py[pb + lane];
+            const int32_t xrc = a.x_blk_rc[ix];
+            mtn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+            mxo = a.x_pack_off[ix];
+            myo = a.y_pack_off[iy];
+            mkt = (mtn + 15) >> 4;
+        }
+        int nsteps = mkt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nsteps += __shfl_xor_sync(0xffffffffu, nsteps, o);
+        int pu = 0, pk = 0;
+        int64_t pxo = __shfl_sync(0xffffffffu, mxo, 0), pyo = __shfl_sync(0xffffffffu, myo, 0);
+        int pkt = __shfl_sync(0xffffffffu, mkt, 0);
+        auto produce = [&](int st) {
+            const uint32_t dst = ring_s + (uint32_t)(st * 32 * SW) * 4u;
+            const uint32_t *src = XP + pxo + ((int64_t)(pk * MT + mt0) * 32 + lane) * kOzXW;
+#pragma unroll
+            for (int c = 0; c < kOzXW / 4; ++c) cp_async16(dst + 16u * c, src + 4 * c);
+#pragma unroll
+            for (int j = 0; j < NTC; ++j) {
+                if (nt0 + j < NT) {
+                    const uint32_t *ys = YP + pyo + ((int64_t)(pk * NT + nt0 + j) * 32 + lane) * kOzYW;
+                    const uint32_t d = dst + (kOzXW + j * kOzYW) * 4u;
+#pragma unroll
+                    for (int c = 0; c < kOzYW / 4; ++c) cp_async16(d + 16u * c, ys + 4 * c);
+                }
+            }
+            if (++pk == pkt) {
+                pk = 0;
+                ++pu;
+                const int src_lane = pu < nb ? pu : 0;
+                pxo = __shfl_sync(0xffffffffu, mxo, src_lane);
+                pyo = __shfl_sync(0xffffffffu, myo, src_lane);
+                pkt = __shfl_sync(0xffffffffu, mkt, src_lane);
+            }
+        };
+#pragma unroll
+        for (int st = 0; st < ST - 1; ++st) {
+            if (st < nsteps) produce(st);
+            cp_async_commit();
+        }
+        int cu = 0, ck = 0;
+        int ckt = __shfl_sync(0xffffffffu, mkt, 0), ctn = __shfl_sync(0xffffffffu, mtn, 0);
+        for (int s = 0; s < nsteps; ++s) {
+            if (s + ST - 1 < nsteps) produce((s + ST - 1) % ST);
+            cp_async_commit();
+            cp_async_wait<ST - 1>();
+            const uint32_t *w = myring + (s % ST) * 32 * SW;
+            uint32_t fa[kOzSlices][4];
+#pragma unroll
+            for (int p = 0; p < kOzSlices; ++p) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(w + 4 * p);
+                fa[p][0] = v.x; fa[p][1] = v.y; fa[p][2] = v.z; fa[p][3] = v.w;
+            }
+            uint32_t fb[NTC][kOzSlices][2];
+#pragma unroll
+            for (int j = 0; j < NTC; ++j)
+#pragma unroll
+                for (int c = 0; c < kOzYW / 4; ++c) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(w + kOzXW + j * kOzYW + 4 * c);
+                    fb[j][2 * c][0] = v.x; fb[j][2 * c][1] = v.y;
+                    fb[j][2 * c + 1][0] = v.z; fb[j][2 * c + 1][1] = v.w;
+                }
+            // close the exact window before it would pass kOzWindow terms of k
+            const int kact = min(16, ctn - 16 * ck);
+            if (kacc + kact > kOzWindow) {
+                kacc = 0;
+#pragma unroll
+                for (int j = 0; j < NTC; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        double t = (double)acc[kOzLevels - 1][j][v];
+#pragma unroll
+                        for (int l = kOzLevels - 2; l >= 0; --l) t += (double)acc[l][j][v];
+                        s64[j][v] += t;
+#pragma unroll
+                        for (int l = 0; l < kOzLevels; ++l) acc[l][j][v] = 0.f;
+                    }
+            }
+            kacc += kact;
+            // slice products, highest level (smallest) first
+#pragma unroll
+            for (int l = kOzSlices - 1; l >= 0; --l)
+#pragma unroll
+                for (int p = 0; p <= l; ++p)
+#pragma unroll
+                    for (int j = 0; j < NTC; ++j)
+                        if (nt0 + j < NT) mma_bf16(acc[l < kOzLevels - 1 ? l : kOzLevels - 1][j], fa[p], fb[j][l - p]);
+            if (++ck == ckt) {
+                ck = 0;
+                ++cu;
+                const int src_lane = cu < nb ? cu : 0;
+                ckt = __shfl_sync(0xffffffffu, mkt, src_lane);
+                ctn = __shfl_sync(0xffffffffu, mtn, src_lane);
+            }
+        }
+        cp_async_wait<0>();
+    }
+    // epilogue: scale by 2^(ex + ey - 14) of the element's row and column
+    const int g = lane >> 2, t4 = lane & 3;
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+    const bool any = p1 > p0;
+    const int32_t xl0 = any ? a.x_line0[a.px[p0]] : 0;
+    const int32_t yl0 = any ? a.y_line0[a.py[p0]] : 0;
+    int ex[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r = mt0 * 16 + g + 8 * h;
+        ex[h] = (any && r < R) ? a.x_exp[xl0 + r] - 1023 : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < NTC; ++j) {
+        int ey[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = (nt0 + j) * 8 + 2 * t4 + h;
+            ey[h] = (any && c < S) ? a.y_exp[yl0 + c] - 1023 : 0;
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = mt0 * 16 + g + ((v >> 1) << 3);
+            const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
+            if (r < R && c < S && nt0 + j < NT) {
+                double t = (double)acc[kOzLevels - 1][j][v];
+#pragma unroll
+                for (int l = kOzLevels - 2; l >= 0; --l) t += (double)acc[l][j][v];
+                const double sum = s64[j][v] + t;
+                double val = a.alpha * ldexp(sum, ex[v >> 1] + ey[v & 1] - 14);
+                const int64_t e = (int64_t)r * S + c;
+                if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
+                static_cast<double *>(a.out_data)[out_off + e] = val;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void oz_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
+    const int32_t orc = a.out_blk_rc[q];
+    const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
+    for (int mt0 = 0; mt0 < MT; ++mt0)
+        for (int nt0 = 0; nt0 < NT; nt0 += 2) {
+            if (NT - nt0 >= 2) oz_pass<2>(a, q, lane, mt0, nt0, ring);
+            else oz_pass<1>(a, q, lane, mt0, nt0, ring);
+        }
+}
+
+// Items [0, n0): a warp each on the tensor cores; items [n0, n_items): tiny
+// blocks one per lane with plain FP64 FMA (exact enough, no slicing needed).
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
+    extern __shared__ __align__(16) uint32_t oz_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *ring = oz_smem + warp * oz_ring_words_per_warp();
+    unsigned long long *ctr = a.work_counter;
+    if (a.status && *a.status != 0) return;
+    const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
+    const int64_t n0 = a.n_items - n_lane;
+    const int64_t tickets = n0 + (n_lane + 31) / 32;
+    while (true) {
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tickets) break;
+        if (t < n0) {
+            int64_t q = t;
+            if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            oz_item(a, q, lane, ring);
+        } else {
+            const int64_t idx = n0 + (t - n0) * 32 + lane;
+            if (idx < a.n_items) cc_lane_dispatch<double>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
+        }
+    }
+}
+
+// =====================================================================
 // Operand splitting and fragment packing
 // =====================================================================
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
@@ -851,10 +1084,10 @@ __device__ __forceinline__ double elem(const T *b, int R, int Tn, int trans, int
 __device__ __forceinline__ int64_t pack_words(int R, int C, int role_y, int prec) {
     const int K = (prec == BSM_P_TF32x3) ? 8 : 16;
     if (!role_y) {
-        const int XW = (prec == BSM_P_BF16x6) ? 12 : 8;
+        const int XW = prec == BSM_P_OZAKI ? kOzXW : (prec == BSM_P_BF16x6) ? 12 : 8;
         return (int64_t)((R + 15) / 16) * ((C + K - 1) / K) * 32 * XW;
     }
-    const int YW = (prec == BSM_P_BF16x6) ? 6 : 4;
+    const int YW = prec == BSM_P_OZAKI ? kOzYW : (prec == BSM_P_BF16x6) ? 6 : 4;
     return (int64_t)((R + K - 1) / K) * ((C + 7) / 8) * 32 * YW;
 }
 
@@ -964,6 +1197,104 @@ __global__ void k_split_plain(int64_t n, const T *data, float *out) {
     }
 }
 
+// Digits of x on its line's grid (see the Ozaki section above): slice p is
+// d_p * 2^(-9p) as BF16 bits, exact.  e = unbiased exponent of the line.
+__device__ __forceinline__ void oz_slices(double x, int e, uint32_t (&out)[kOzSlices]) {
+    double y = ldexp(x, 7 - e);
+    double sc = 1.0;
+#pragma unroll
+    for (int p = 0; p < kOzSlices; ++p) {
+        const double d = rint(y);
+        out[p] = __bfloat16_as_ushort(__double2bfloat16(d * sc));
+        y = (y - d) * 512.0;
+        sc *= 1.0 / 512.0;
+    }
+}
+
+// Ozaki fragment planes of FP64 data: same tiling as k_pack's BF16 layout with
+// kOzSlices planes; X element (r, k) uses the exponent of line line0[b] + r,
+// Y element (k, n) that of line line0[b] + n.
+__global__ void k_pack_oz(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_rc, const double *data,
+                          int role_y, int trans, const int64_t *pack_off, uint32_t *pack, const int32_t *line0,
+                          const int32_t *exps, const int32_t *status) {
+    if (status && *status != 0) return;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = wid; b < nnzb; b += nwarp) {
+        const double *src = data + blk_off[b];
+        int rows, cols;
+        logical_dims(blk_rc[b], trans, rows, cols);
+        const int32_t l0 = line0[b];
+        uint32_t *dst = pack + pack_off[b];
+        uint32_t lo[kOzSlices], hi[kOzSlices];
+        if (!role_y) {
+            const int MT = (rows + 15) / 16, KT = (cols + 15) / 16;
+            for (int kt = 0; kt < KT; ++kt)
+                for (int mt = 0; mt < MT; ++mt) {
+                    uint32_t *w = dst + ((int64_t)(kt * MT + mt) * 32 + lane) * kOzXW;
+                    const int r0 = mt * 16 + g, k0 = kt * 16;
+                    const int rr[4] = {r0, r0 + 8, r0, r0 + 8};
+                    const int kk[4] = {k0 + 2 * t4, k0 + 2 * t4, k0 + 2 * t4 + 8, k0 + 2 * t4 + 8};
+                    for (int v = 0; v < 4; ++v) {
+                        const int e = rr[v] < rows ? exps[l0 + rr[v]] - 1023 : 0;
+                        oz_slices(elem<double>(src, rows, cols, trans, rr[v], kk[v]), e, lo);
+                        oz_slices(elem<double>(src, rows, cols, trans, rr[v], kk[v] + 1), e, hi);
+                        for (int p = 0; p < kOzSlices; ++p) w[4 * p + v] = lo[p] | (hi[p] << 16);
+                    }
+                }
+        } else {
+            const int KT = (rows + 15) / 16, NT = (cols + 7) / 8;
+            for (int kt = 0; kt < KT; ++kt)
+                for (int nt = 0; nt < NT; ++nt) {
+                    uint32_t *w = dst + ((int64_t)(kt * NT + nt) * 32 + lane) * kOzYW;
+                    const int n0 = nt * 8 + g, k0 = kt * 16;
+                    const int e = n0 < cols ? exps[l0 + n0] - 1023 : 0;
+                    const int kk[2] = {k0 + 2 * t4, k0 + 2 * t4 + 8};
+                    for (int v = 0; v < 2; ++v) {
+                        oz_slices(elem<double>(src, rows, cols, trans, kk[v], n0), e, lo);
+                        oz_slices(elem<double>(src, rows, cols, trans, kk[v] + 1, n0), e, hi);
+                        for (int p = 0; p < kOzSlices; ++p) w[2 * p + v] = lo[p] | (hi[p] << 16);
+                    }
+                }
+        }
+    }
+}
+
+// line0[b] for every block: first global line of the block (one warp per block row)
+__global__ void k_oz_line0(int32_t nbr, const int64_t *row_ptr, const int32_t *col_idx, const int32_t *row_start,
+                           const int32_t *col_start, int by_rows, int32_t *line0) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = wid; i < nbr; i += nwarp)
+        for (int64_t b = row_ptr[i] + lane; b < row_ptr[i + 1]; b += 32)
+            line0[b] = by_rows ? row_start[i] : col_start[col_idx[b]];
+}
+
+// exps[line] = max over the line of the biased exponent field of |x| (one warp
+// per block, a lane per line of the block)
+__global__ void k_oz_line_exp(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_rc, const double *data,
+                              const int32_t *line0, int by_rows, int32_t *exps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = wid; b < nnzb; b += nwarp) {
+        const double *src = data + blk_off[b];
+        const int R = rc_rows(blk_rc[b]), C = rc_cols(blk_rc[b]);
+        const int nl = by_rows ? R : C, len = by_rows ? C : R;
+        for (int l = lane; l < nl; l += 32) {
+            int m = 0;
+            for (int t = 0; t < len; ++t) {
+                const double x = by_rows ? src[(int64_t)l * C + t] : src[(int64_t)t * C + l];
+                m = max(m, (int)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+            }
+            atomicMax(&exps[line0[b] + l], m);
+        }
+    }
+}
+
 // Set bit 31 of order[t] when the block order[t] is computed by the CUDA-core
 // variant: variant_of_class[size_index[rows] * ns + size_index[cols]] != 0.
 __global__ void k_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index,
@@ -1024,7 +1355,12 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const bool tc = a.prec == BSM_P_TF32x3 || a.prec == BSM_P_BF16x3 || a.prec == BSM_P_BF16x6;
-    if (!tc) {
+    if (a.prec == BSM_P_OZAKI) {
+        const size_t smem = sizeof(uint32_t) * (size_t)oz_ring_words_per_warp() * kWarpsPerCta;
+        e = cudaFuncSetAttribute(k_numeric_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            k_numeric_oz<<<persistent_grid(k_numeric_oz, a.n_items, smem), kThreadsNum, smem, s>>>(a);
+    } else if (!tc) {
         if (a.dtype == BSM_FP64) {
             k_numeric_cc<double><<<persistent_grid(k_numeric_cc<double>, a.n_items), kThreadsNum, 0, s>>>(a);
         } else {
@@ -1063,6 +1399,21 @@ cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStrea
 
 int split_pieces(int prec) { return prec == BSM_P_BF16x6 ? 3 : 2; }
 
+cudaError_t launch_oz_lines(const bsm_mat *M, int by_rows, int32_t *line0, int32_t *exps, cudaStream_t s) {
+    if (M->nnzb == 0) return cudaSuccess;
+    if (M->dtype != BSM_FP64 || !M->row_start || !M->col_start) return cudaErrorInvalidValue;
+    int64_t g = ((int64_t)M->nbr * 32 + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_oz_line0<<<(unsigned)g, 256, 0, s>>>(M->nbr, M->row_ptr, M->col_idx, M->row_start, M->col_start, by_rows,
+                                           line0);
+    g = (M->nnzb * 32 + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    k_oz_line_exp<<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc, static_cast<const double *>(M->data),
+                                              line0, by_rows, exps);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mark_variant(int64_t n, int32_t *order, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
                                 const int8_t *variant_of_class, unsigned long long *marked, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
@@ -1084,12 +1435,20 @@ cudaError_t launch_pack_sizes(const bsm_mat *M, int role_y, int trans, int prec,
 }
 
 cudaError_t launch_pack(const bsm_mat *M, int role_y, int trans, int prec, const int64_t *pack_off,
-                        void *pack, const int32_t *status, cudaStream_t s) {
+                        void *pack, const int32_t *status, cudaStream_t s, const int32_t *line0,
+                        const int32_t *exps) {
     if (M->nnzb == 0) return cudaSuccess;
     int64_t g = (M->nnzb * 32 + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
     uint32_t *p = static_cast<uint32_t *>(pack);
     const bool f64 = M->dtype == BSM_FP64;
+    if (prec == BSM_P_OZAKI) {
+        if (!f64 || !line0 || !exps) return cudaErrorInvalidValue;
+        k_pack_oz<<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc, static_cast<const double *>(M->data),
+                                              role_y, trans, pack_off, p, line0, exps, status);
+        count_launch(1);
+        return cudaGetLastError();
+    }
 #define BSM_PACK_CASE(PREC)                                                                           \
     if (f64)                                                                                          \
         k_pack<double, PREC><<<(unsigned)g, 256, 0, s>>>(M->nnzb, M->blk_off, M->blk_rc,              \
