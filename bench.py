@@ -51,6 +51,7 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-split", action="store_true", help="skip the split-precision legs")
+    p.add_argument("--legs", default="", help="comma list of split-precision legs to run (default: all)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
@@ -433,13 +434,15 @@ def main():
     tuned = {"fp64": tuned_fp64}
     if not args.no_split:
         from paper_1708_03604_gb300 import autotune
-        for prec in ("ozaki", "tf32x3", "bf16x6", "bf16x3"):
+        legs = [("ozaki", "ozaki", 0), ("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
+                ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2), ("tf32x3_pair4", "tf32x3", -4),
+                ("bf16x6_pair4", "bf16x6", -4)]
+        if args.legs:
+            legs = [lg for lg in legs if lg[0] in args.legs.split(",")]
+        for prec in dict.fromkeys(lg[1] for lg in legs):
             tuned[prec] = autotune.tune(A, B, eps, prec=prec, reps=2)
         ref_norm = torch.linalg.vector_norm(C64).item()
-        for key, prec, fl in (("ozaki", "ozaki", 0), ("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0),
-                              ("bf16x3", "bf16x3", 0),
-                              ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2),
-                              ("tf32x3_pair4", "tf32x3", -4), ("bf16x6_pair4", "bf16x6", -4)):
+        for key, prec, fl in legs:
             step(prec, fl)
             torch.cuda.synchronize()
             bsm.bsm_set_profiling(True)

@@ -348,6 +348,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
 }
+// L2-only variant (16-byte copies of data used once per warp)
+__device__ __forceinline__ void cp_async16_cg(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
+}
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
 }
@@ -823,20 +827,33 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
 // pair's scale 2^(ex+ey-14)); products of one level summed in the tensor
 // core's FP32 accumulator stay exact while the sum stays below 2^24 grid
 // units: a level holding c slice pairs takes 2^24 / (c * 2^16) terms of k,
-// 64 for level 3 (4 pairs).  Levels 0..3 have exact FP32 sums that move into
-// an FP64 sum before more than kOzWindow terms of k; levels 4 and 5 (11
-// pairs, below 2^-33 of level 0) share one rounded FP32 sum; levels >= 6 are
-// dropped (below 2^-50 of level 0).  Per term of k the error is below
-// 2^-44 of 2^(ex+ey): the rounded sum (at most 11 roundings of 2^-23 of
-// 64 * 2^16 * 5 * 2^-36 units per term of k) plus the cut digits and levels.
+// 64 for level 3 (4 pairs).  Levels 0..3 have exact FP32 sums; before more
+// than kOzWindow terms of k they are converted to integers and added into a
+// 64-bit fixed-point sum with unit 2^-27 (exact; a window adds less than
+// 2^49.01 units, so 8192 windows fit, after which the sum is moved into the
+// output element).  Levels 4 and 5 (11 pairs, below 2^-33 of level 0) share
+// one rounded FP32 sum per window (the tensor core's FP32 additions round
+// toward zero, so it is restarted every window) whose window values add up in
+// an FP32 sum with round-to-nearest on the CUDA cores; levels >= 6 are
+// dropped (below 2^-50 of level 0).  Per term of k the error is below 2^-44
+// of 2^(ex+ey): the rounded sums plus the cut digits and levels.
 constexpr int kOzSlices = 6;
 constexpr int kOzLevels = 5;    // FP32 sums: levels 0, 1, 2, 3 exact, 4..5 rounded
 constexpr int kOzWindow = 64;
+constexpr int kOzSpillWindows = 8192;
 constexpr int kOzStages = 3;
 constexpr int kOzXW = 4 * kOzSlices;                 // X words per lane per tile
 constexpr int kOzYW = 2 * kOzSlices;                 // Y words per lane per tile
 constexpr int kOzSW = kOzXW + 2 * kOzYW;             // ring words per lane per stage (1 x 2 tiles)
 __host__ __device__ constexpr int oz_ring_words_per_warp() { return kOzStages * 32 * kOzSW; }
+// Packed tiles are chunk-major: chunk c (16 bytes) of lane L at word
+// c * 128 + 4 * L, so one 16-byte cp.async per lane reads 512 contiguous
+// bytes.  X tile: chunk p = plane p (registers v0..v3); Y tile: chunk c =
+// planes 2c and 2c+1 (registers v0, v1 each; lanes with bit 3 set hold the two
+// 8-byte halves swapped, so 8-byte reads of 16 lanes hit 16 distinct bank
+// pairs).  A ring stage is chunk-major the same way (chunk c of lane L at
+// word c * 128 + 4 * L): each 16-byte copy and read of the warp covers 512
+// contiguous bytes of shared memory.
 
 // One pass over a 1 x NTC super tile (16 x 8*NTC output elements) at (mt0, nt0).
 template <int NTC>
@@ -849,20 +866,64 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
     const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
     const uint32_t *XP = static_cast<const uint32_t *>(a.x_pack);
     const uint32_t *YP = static_cast<const uint32_t *>(a.y_pack);
-    uint32_t *myring = ring + lane * SW;
+    double *O = static_cast<double *>(a.out_data);
+    const int64_t out_off = a.out_blk_off[q];
+    uint32_t *myring = ring + 4 * lane;  // chunk c of stage st at myring + st * 32 * SW + 128 * c
     const uint32_t ring_s = smem_addr(myring);
+    const int hswz = (lane >> 3) & 1;  // 8-byte half order inside a Y chunk
+    const int g = lane >> 2, t4 = lane & 3;
+    // rows g + 8 of this tile exist (else fragment elements v = 2, 3 are padding)
+    const bool hi_rows = R - mt0 * 16 > 8;
 
     float acc[kOzLevels][NTC][4];
-    double s64[NTC][4];
+    long long fx[NTC][4];  // exact sum of levels 0..3, unit 2^-27
+    float low[NTC][4];     // sum of the windows' level 4..5 sums
 #pragma unroll
     for (int j = 0; j < NTC; ++j)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            s64[j][v] = 0.0;
+            fx[j][v] = 0;
+            low[j][v] = 0.f;
 #pragma unroll
             for (int l = 0; l < kOzLevels; ++l) acc[l][j][v] = 0.f;
         }
-    int kacc = 0;  // terms of k in the open exact window
+    int kacc = 0;      // terms of k in the open exact window
+    int nwin = 0;      // windows added into fx since it was last moved out
+    bool spilled = false;
+    // levels 0..3 -> fx (integers below 2^24 on their grids, so the conversions are exact)
+    auto close_window = [&]() {
+#pragma unroll
+        for (int j = 0; j < NTC; ++j)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (v >= 2 && !hi_rows) continue;  // padding rows hold zeros
+                long long t = (long long)__float2int_rn(acc[0][j][v]) << 27;
+                t += (long long)__float2int_rn(acc[1][j][v] * 512.f) << 18;
+                t += (long long)__float2int_rn(acc[2][j][v] * 262144.f) << 9;
+                t += (long long)__float2int_rn(acc[3][j][v] * 134217728.f);
+                fx[j][v] += t;
+                low[j][v] = __fadd_rn(low[j][v], acc[kOzLevels - 1][j][v]);
+#pragma unroll
+                for (int l = 0; l < kOzLevels; ++l) acc[l][j][v] = 0.f;
+            }
+        if (++nwin == kOzSpillWindows) {  // keep fx far from 2^63: move it into the output
+            nwin = 0;
+#pragma unroll
+            for (int j = 0; j < NTC; ++j)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = mt0 * 16 + g + ((v >> 1) << 3);
+                    const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
+                    if (r < R && c < S && nt0 + j < NT) {
+                        const double part = (double)fx[j][v] * 0x1p-27;
+                        const int64_t e = out_off + (int64_t)r * S + c;
+                        O[e] = spilled ? O[e] + part : part;
+                    }
+                    fx[j][v] = 0;
+                }
+            spilled = true;
+        }
+    };
     for (int64_t pb = p0; pb < p1; pb += 32) {
         const int nb = (int)min((int64_t)32, p1 - pb);
         int64_t mxo = 0, myo = 0;
@@ -883,16 +944,16 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
         int pkt = __shfl_sync(0xffffffffu, mkt, 0);
         auto produce = [&](int st) {
             const uint32_t dst = ring_s + (uint32_t)(st * 32 * SW) * 4u;
-            const uint32_t *src = XP + pxo + ((int64_t)(pk * MT + mt0) * 32 + lane) * kOzXW;
+            const uint32_t *src = XP + pxo + (int64_t)(pk * MT + mt0) * (32 * kOzXW) + 4 * lane;
 #pragma unroll
-            for (int c = 0; c < kOzXW / 4; ++c) cp_async16(dst + 16u * c, src + 4 * c);
+            for (int c = 0; c < kOzXW / 4; ++c) cp_async16_cg(dst + 512u * c, src + 128 * c);
 #pragma unroll
             for (int j = 0; j < NTC; ++j) {
                 if (nt0 + j < NT) {
-                    const uint32_t *ys = YP + pyo + ((int64_t)(pk * NT + nt0 + j) * 32 + lane) * kOzYW;
-                    const uint32_t d = dst + (kOzXW + j * kOzYW) * 4u;
+                    const uint32_t *ys = YP + pyo + (int64_t)(pk * NT + nt0 + j) * (32 * kOzYW) + 4 * lane;
 #pragma unroll
-                    for (int c = 0; c < kOzYW / 4; ++c) cp_async16(d + 16u * c, ys + 4 * c);
+                    for (int c = 0; c < kOzYW / 4; ++c)
+                        cp_async16_cg(dst + 512u * (kOzXW / 4 + j * (kOzYW / 4) + c), ys + 128 * c);
                 }
             }
             if (++pk == pkt) {
@@ -919,43 +980,36 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
             uint32_t fa[kOzSlices][4];
 #pragma unroll
             for (int p = 0; p < kOzSlices; ++p) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(w + 4 * p);
+                const uint4 v = *reinterpret_cast<const uint4 *>(w + 128 * p);
                 fa[p][0] = v.x; fa[p][1] = v.y; fa[p][2] = v.z; fa[p][3] = v.w;
             }
-            uint32_t fb[NTC][kOzSlices][2];
-#pragma unroll
-            for (int j = 0; j < NTC; ++j)
-#pragma unroll
-                for (int c = 0; c < kOzYW / 4; ++c) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(w + kOzXW + j * kOzYW + 4 * c);
-                    fb[j][2 * c][0] = v.x; fb[j][2 * c][1] = v.y;
-                    fb[j][2 * c + 1][0] = v.z; fb[j][2 * c + 1][1] = v.w;
-                }
             // close the exact window before it would pass kOzWindow terms of k
             const int kact = min(16, ctn - 16 * ck);
             if (kacc + kact > kOzWindow) {
+                close_window();
                 kacc = 0;
-#pragma unroll
-                for (int j = 0; j < NTC; ++j)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        double t = (double)acc[kOzLevels - 1][j][v];
-#pragma unroll
-                        for (int l = kOzLevels - 2; l >= 0; --l) t += (double)acc[l][j][v];
-                        s64[j][v] += t;
-#pragma unroll
-                        for (int l = 0; l < kOzLevels; ++l) acc[l][j][v] = 0.f;
-                    }
             }
             kacc += kact;
-            // slice products, highest level (smallest) first
+            // slice products: Y slice q (read from the ring when needed) with
+            // every X slice p of level p + q <= 5
 #pragma unroll
-            for (int l = kOzSlices - 1; l >= 0; --l)
+            for (int qq = kOzSlices - 1; qq >= 0; --qq) {
+                uint32_t fb[NTC][2];
 #pragma unroll
-                for (int p = 0; p <= l; ++p)
+                for (int j = 0; j < NTC; ++j) {
+                    const uint2 v = *reinterpret_cast<const uint2 *>(
+                        w + 128 * (kOzXW / 4 + j * (kOzYW / 4) + (qq >> 1)) + 2 * ((qq & 1) ^ hswz));
+                    fb[j][0] = v.x; fb[j][1] = v.y;
+                }
+#pragma unroll
+                for (int p = kOzSlices - 1 - qq; p >= 0; --p)
 #pragma unroll
                     for (int j = 0; j < NTC; ++j)
-                        if (nt0 + j < NT) mma_bf16(acc[l < kOzLevels - 1 ? l : kOzLevels - 1][j], fa[p], fb[j][l - p]);
+                        if (nt0 + j < NT) {
+                            constexpr int top = kOzLevels - 1;
+                            mma_bf16(acc[p + qq < top ? p + qq : top][j], fa[p], fb[j]);
+                        }
+            }
             if (++ck == ckt) {
                 ck = 0;
                 ++cu;
@@ -966,9 +1020,8 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
         }
         cp_async_wait<0>();
     }
+    close_window();
     // epilogue: scale by 2^(ex + ey - 14) of the element's row and column
-    const int g = lane >> 2, t4 = lane & 3;
-    const int64_t out_off = a.out_blk_off[q];
     const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
     const bool any = p1 > p0;
     const int32_t xl0 = any ? a.x_line0[a.px[p0]] : 0;
@@ -992,14 +1045,12 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
             const int r = mt0 * 16 + g + ((v >> 1) << 3);
             const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
             if (r < R && c < S && nt0 + j < NT) {
-                double t = (double)acc[kOzLevels - 1][j][v];
-#pragma unroll
-                for (int l = kOzLevels - 2; l >= 0; --l) t += (double)acc[l][j][v];
-                const double sum = s64[j][v] + t;
-                double val = a.alpha * ldexp(sum, ex[v >> 1] + ey[v & 1] - 14);
                 const int64_t e = (int64_t)r * S + c;
+                double sum = (double)fx[j][v] * 0x1p-27 + (double)low[j][v];
+                if (spilled) sum += O[out_off + e];
+                double val = a.alpha * ldexp(sum, ex[v >> 1] + ey[v & 1] - 14);
                 if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
-                static_cast<double *>(a.out_data)[out_off + e] = val;
+                O[out_off + e] = val;
             }
         }
     }
@@ -1211,9 +1262,9 @@ __device__ __forceinline__ void oz_slices(double x, int e, uint32_t (&out)[kOzSl
     }
 }
 
-// Ozaki fragment planes of FP64 data: same tiling as k_pack's BF16 layout with
-// kOzSlices planes; X element (r, k) uses the exponent of line line0[b] + r,
-// Y element (k, n) that of line line0[b] + n.
+// Ozaki fragment planes of FP64 data: the tiles of k_pack's BF16 layout with
+// kOzSlices planes, chunk-major inside a tile; X element (r, k) uses the
+// exponent of line line0[b] + r, Y element (k, n) that of line line0[b] + n.
 __global__ void k_pack_oz(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_rc, const double *data,
                           int role_y, int trans, const int64_t *pack_off, uint32_t *pack, const int32_t *line0,
                           const int32_t *exps, const int32_t *status) {
@@ -1233,7 +1284,7 @@ __global__ void k_pack_oz(int64_t nnzb, const int64_t *blk_off, const int32_t *b
             const int MT = (rows + 15) / 16, KT = (cols + 15) / 16;
             for (int kt = 0; kt < KT; ++kt)
                 for (int mt = 0; mt < MT; ++mt) {
-                    uint32_t *w = dst + ((int64_t)(kt * MT + mt) * 32 + lane) * kOzXW;
+                    uint32_t *w = dst + (int64_t)(kt * MT + mt) * (32 * kOzXW) + 4 * lane;
                     const int r0 = mt * 16 + g, k0 = kt * 16;
                     const int rr[4] = {r0, r0 + 8, r0, r0 + 8};
                     const int kk[4] = {k0 + 2 * t4, k0 + 2 * t4, k0 + 2 * t4 + 8, k0 + 2 * t4 + 8};
@@ -1241,21 +1292,22 @@ __global__ void k_pack_oz(int64_t nnzb, const int64_t *blk_off, const int32_t *b
                         const int e = rr[v] < rows ? exps[l0 + rr[v]] - 1023 : 0;
                         oz_slices(elem<double>(src, rows, cols, trans, rr[v], kk[v]), e, lo);
                         oz_slices(elem<double>(src, rows, cols, trans, rr[v], kk[v] + 1), e, hi);
-                        for (int p = 0; p < kOzSlices; ++p) w[4 * p + v] = lo[p] | (hi[p] << 16);
+                        for (int p = 0; p < kOzSlices; ++p) w[128 * p + v] = lo[p] | (hi[p] << 16);
                     }
                 }
         } else {
             const int KT = (rows + 15) / 16, NT = (cols + 7) / 8;
             for (int kt = 0; kt < KT; ++kt)
                 for (int nt = 0; nt < NT; ++nt) {
-                    uint32_t *w = dst + ((int64_t)(kt * NT + nt) * 32 + lane) * kOzYW;
+                    uint32_t *w = dst + (int64_t)(kt * NT + nt) * (32 * kOzYW) + 4 * lane;
                     const int n0 = nt * 8 + g, k0 = kt * 16;
                     const int e = n0 < cols ? exps[l0 + n0] - 1023 : 0;
                     const int kk[2] = {k0 + 2 * t4, k0 + 2 * t4 + 8};
                     for (int v = 0; v < 2; ++v) {
                         oz_slices(elem<double>(src, rows, cols, trans, kk[v], n0), e, lo);
                         oz_slices(elem<double>(src, rows, cols, trans, kk[v] + 1, n0), e, hi);
-                        for (int p = 0; p < kOzSlices; ++p) w[2 * p + v] = lo[p] | (hi[p] << 16);
+                        for (int p = 0; p < kOzSlices; ++p)
+                            w[128 * (p >> 1) + 2 * ((p & 1) ^ ((lane >> 3) & 1)) + v] = lo[p] | (hi[p] << 16);
                     }
                 }
         }

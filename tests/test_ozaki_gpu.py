@@ -122,6 +122,20 @@ def test_ozaki_elementwise_bound(bsm, oracle):
     assert np.all(Dg[~nz] == 0.0)
 
 
+def test_ozaki_long_inner_dimension(bsm, oracle):
+    """One output block summing 537,600 terms of k (2,100 blocks of 256): more
+    than 8192 exact 64-term windows, so the fixed-point sum is moved into the
+    output element once before the end."""
+    kbs = np.full(2100, 256, dtype=np.int32)
+    A = random_bcsr(np.array([16], np.int32), kbs, 1.0, seed=151)
+    B = random_bcsr(kbs, np.array([8], np.int32), 1.0, seed=152)
+    Cg = bsm.multiply(1.0, bsm.Matrix.from_host(A), bsm.Matrix.from_host(B), prec="ozaki")
+    ref = oracle.multiply(1.0, A, B)
+    _check_pattern(Cg, ref.C)
+    err = rel_fro(Cg.data_host(), ref.C.data)
+    assert err <= TOL, err
+
+
 def test_ozaki_backward(bsm, oracle):
     import torch
     bs = I.mixed_sizes(40, (3, 7, 13, 23), (0.3, 0.3, 0.2, 0.2), seed=23)
