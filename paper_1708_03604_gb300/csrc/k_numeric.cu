@@ -303,11 +303,14 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
 //   prec      K step   X words   Y words
 //   TF32x3       8        8         4      (hi[4] lo[4] | hi[2] lo[2])
 //   BF16x3      16        8         4      (hi[4] lo[4] | hi[2] lo[2])
-//   BF16x6      16       12         6      (p0[4] p1[4] p2[4] | p0[2] p1[2] p2[2])
+//   BF16x6      16       12         8      (p0[4] p1[4] p2[4] | p0[2] p1[2] p2[2] pad[2])
+// Inside a tile the words are chunk-major: 16-byte chunk c of lane L at word
+// c * 128 + 4 * L (X chunk = one piece, Y chunk = two pieces), so a 16-byte
+// copy of the warp reads 512 contiguous bytes.
 template <int PREC> struct PrecTraits;
 template <> struct PrecTraits<BSM_P_TF32x3> { static constexpr int K = 8, XW = 8, YW = 4, NP = 2; };
 template <> struct PrecTraits<BSM_P_BF16x3> { static constexpr int K = 16, XW = 8, YW = 4, NP = 2; };
-template <> struct PrecTraits<BSM_P_BF16x6> { static constexpr int K = 16, XW = 12, YW = 6, NP = 3; };
+template <> struct PrecTraits<BSM_P_BF16x6> { static constexpr int K = 16, XW = 12, YW = 8, NP = 3; };
 
 __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm(
@@ -331,13 +334,15 @@ __device__ __forceinline__ void mma_piece(float (&d)[4], const uint32_t (&a)[4],
 }
 
 // Per-lane staging ring: every lane copies its own fragment words of the
-// next (product, k-step) steps from global memory into its private slice of
+// next (product, k-step) steps from global memory into its private slots of
 // shared memory with cp.async and reads back only those words, so the ring
-// needs no warp barrier -- only each lane's own cp.async.wait_group.
+// needs no warp barrier -- only each lane's own cp.async.wait_group.  A stage
+// is chunk-major like the packs (chunk c of lane L at word c * 128 + 4 * L):
+// every 16-byte copy and read of the warp covers 512 contiguous bytes.
 template <int PREC> struct RingTraits;
 template <> struct RingTraits<BSM_P_TF32x3> { static constexpr int STAGES = 4, SW = 2 * 8 + 3 * 4; };
 template <> struct RingTraits<BSM_P_BF16x3> { static constexpr int STAGES = 4, SW = 2 * 8 + 3 * 4; };
-template <> struct RingTraits<BSM_P_BF16x6> { static constexpr int STAGES = 3, SW = 2 * 12 + 3 * 6 + 2; };
+template <> struct RingTraits<BSM_P_BF16x6> { static constexpr int STAGES = 3, SW = 2 * 12 + 3 * 8; };
 
 template <int PREC>
 __host__ __device__ constexpr int ring_words_per_warp() { return RingTraits<PREC>::STAGES * 32 * RingTraits<PREC>::SW; }
@@ -345,15 +350,10 @@ __host__ __device__ constexpr int ring_words_per_warp() { return RingTraits<PREC
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
-}
-// L2-only variant (16-byte copies of data used once per warp)
+// 16-byte asynchronous copy global -> shared, cached in L2 only (the staged
+// fragment words are read once per warp)
 __device__ __forceinline__ void cp_async16_cg(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src));
-}
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
@@ -389,8 +389,9 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
     // FP64 mode: flush_every > 0 products per FP64 add; compensated mode:
     // |flush_every| products per TwoSum (0 means 1)
     const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
-    uint32_t *myring = ring + lane * SW;          // stage st at myring + st * 32 * SW
+    uint32_t *myring = ring + 4 * lane;  // chunk c of stage st at myring + st * 32 * SW + 128 * c
     const uint32_t ring_s = smem_addr(myring);
+    constexpr int XC = PT::XW / 4, YC = PT::YW / 4;  // chunks per tile
 
     float acc[MTC][NTC][4];
     float shi[FF ? MTC : 1][FF ? NTC : 1][4], slo[FF ? MTC : 1][FF ? NTC : 1][4];
@@ -435,22 +436,17 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
 #pragma unroll
             for (int i = 0; i < MTC; ++i) {
                 if (mt0 + i < MT) {
-                    const uint32_t *src = XP + pxo + ((int64_t)(pk * MT + mt0 + i) * 32 + lane) * PT::XW;
+                    const uint32_t *src = XP + pxo + (int64_t)(pk * MT + mt0 + i) * (32 * PT::XW) + 4 * lane;
 #pragma unroll
-                    for (int c = 0; c < PT::XW / 4; ++c) cp_async16(dst + (i * PT::XW + 4 * c) * 4u, src + 4 * c);
+                    for (int c = 0; c < XC; ++c) cp_async16_cg(dst + 512u * (i * XC + c), src + 128 * c);
                 }
             }
 #pragma unroll
             for (int j = 0; j < NTC; ++j) {
                 if (nt0 + j < NT) {
-                    const uint32_t *src = YP + pyo + ((int64_t)(pk * NT + nt0 + j) * 32 + lane) * PT::YW;
-                    const uint32_t d = dst + (MTC * PT::XW + j * PT::YW) * 4u;
-                    if constexpr (PT::YW == 4) {
-                        cp_async16(d, src);
-                    } else {
+                    const uint32_t *src = YP + pyo + (int64_t)(pk * NT + nt0 + j) * (32 * PT::YW) + 4 * lane;
 #pragma unroll
-                        for (int c = 0; c < PT::YW / 2; ++c) cp_async8(d + 8u * c, src + 2 * c);
-                    }
+                    for (int c = 0; c < YC; ++c) cp_async16_cg(dst + 512u * (MTC * XC + j * YC + c), src + 128 * c);
                 }
             }
             if (++pk == pkt) {
@@ -479,22 +475,18 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
             for (int i = 0; i < MTC; ++i)
 #pragma unroll
                 for (int pc = 0; pc < PT::NP; ++pc) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(w + i * PT::XW + 4 * pc);
+                    const uint4 v = *reinterpret_cast<const uint4 *>(w + 128 * (i * XC + pc));
                     fa[i][pc][0] = v.x; fa[i][pc][1] = v.y; fa[i][pc][2] = v.z; fa[i][pc][3] = v.w;
                 }
             uint32_t fb[NTC][PT::NP][2];
 #pragma unroll
             for (int j = 0; j < NTC; ++j) {
-                const uint32_t *wy = w + MTC * PT::XW + j * PT::YW;
-                if constexpr (PT::NP == 2) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(wy);
-                    fb[j][0][0] = v.x; fb[j][0][1] = v.y; fb[j][1][0] = v.z; fb[j][1][1] = v.w;
-                } else {
-#pragma unroll
-                    for (int pc = 0; pc < 3; ++pc) {
-                        const uint2 v = *reinterpret_cast<const uint2 *>(wy + 2 * pc);
-                        fb[j][pc][0] = v.x; fb[j][pc][1] = v.y;
-                    }
+                const uint32_t *wy = w + 128 * (MTC * XC + j * YC);
+                const uint4 v = *reinterpret_cast<const uint4 *>(wy);
+                fb[j][0][0] = v.x; fb[j][0][1] = v.y; fb[j][1][0] = v.z; fb[j][1][1] = v.w;
+                if constexpr (PT::NP == 3) {
+                    const uint2 u = *reinterpret_cast<const uint2 *>(wy + 128);
+                    fb[j][2][0] = u.x; fb[j][2][1] = u.y;
                 }
             }
             // piece products, smallest first; consecutive mma instructions go
@@ -1138,7 +1130,7 @@ __device__ __forceinline__ int64_t pack_words(int R, int C, int role_y, int prec
         const int XW = prec == BSM_P_OZAKI ? kOzXW : (prec == BSM_P_BF16x6) ? 12 : 8;
         return (int64_t)((R + 15) / 16) * ((C + K - 1) / K) * 32 * XW;
     }
-    const int YW = prec == BSM_P_OZAKI ? kOzYW : (prec == BSM_P_BF16x6) ? 6 : 4;
+    const int YW = prec == BSM_P_OZAKI ? kOzYW : (prec == BSM_P_BF16x6) ? 8 : 4;
     return (int64_t)((R + K - 1) / K) * ((C + 7) / 8) * 32 * YW;
 }
 
@@ -1182,7 +1174,8 @@ __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_
             const int MT = (rows + 15) / 16, KT = (cols + PT::K - 1) / PT::K;
             for (int kt = 0; kt < KT; ++kt)
                 for (int mt = 0; mt < MT; ++mt) {
-                    uint32_t *w = dst + ((int64_t)(kt * MT + mt) * 32 + lane) * PT::XW;
+                    // chunk pc (piece pc, registers v0..v3) of this lane at word 128 * pc
+                    uint32_t *w = dst + (int64_t)(kt * MT + mt) * (32 * PT::XW) + 4 * lane;
                     const int r0 = mt * 16 + g, k0 = kt * PT::K;
                     if constexpr (PREC == BSM_P_TF32x3) {
                         const int rr[4] = {r0, r0 + 8, r0, r0 + 8};
@@ -1190,7 +1183,7 @@ __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_
                         for (int v = 0; v < 4; ++v) {
                             split_value<PREC>(at(rr[v], kk[v]), sp);
                             w[v] = sp[0];
-                            w[4 + v] = sp[1];
+                            w[128 + v] = sp[1];
                         }
                     } else {
                         // reg v holds (row, k) and (row, k+1)
@@ -1200,7 +1193,7 @@ __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_
                             uint32_t lo[3], hi[3];
                             split_value<PREC>(at(rr[v], kk[v]), lo);
                             split_value<PREC>(at(rr[v], kk[v] + 1), hi);
-                            for (int pc = 0; pc < PT::NP; ++pc) w[4 * pc + v] = lo[pc] | (hi[pc] << 16);
+                            for (int pc = 0; pc < PT::NP; ++pc) w[128 * pc + v] = lo[pc] | (hi[pc] << 16);
                         }
                     }
                 }
@@ -1208,7 +1201,8 @@ __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_
             const int KT = (rows + PT::K - 1) / PT::K, NT = (cols + 7) / 8;
             for (int kt = 0; kt < KT; ++kt)
                 for (int nt = 0; nt < NT; ++nt) {
-                    uint32_t *w = dst + ((int64_t)(kt * NT + nt) * 32 + lane) * PT::YW;
+                    // piece pc, registers v0 v1 at word 128 * (pc >> 1) + 2 * (pc & 1)
+                    uint32_t *w = dst + (int64_t)(kt * NT + nt) * (32 * PT::YW) + 4 * lane;
                     const int n0 = nt * 8 + g, k0 = kt * PT::K;
                     if constexpr (PREC == BSM_P_TF32x3) {
                         const int kk[2] = {k0 + t4, k0 + t4 + 4};
@@ -1223,7 +1217,11 @@ __global__ void k_pack(int64_t nnzb, const int64_t *blk_off, const int32_t *blk_
                             uint32_t lo[3], hi[3];
                             split_value<PREC>(at(kk[v], n0), lo);
                             split_value<PREC>(at(kk[v] + 1, n0), hi);
-                            for (int pc = 0; pc < PT::NP; ++pc) w[2 * pc + v] = lo[pc] | (hi[pc] << 16);
+                            for (int pc = 0; pc < PT::NP; ++pc) w[128 * (pc >> 1) + 2 * (pc & 1) + v] = lo[pc] | (hi[pc] << 16);
+                        }
+                        if constexpr (PT::NP == 3) {  // padding words of the second chunk
+                            w[128 + 2] = 0;
+                            w[128 + 3] = 0;
                         }
                     }
                 }
