@@ -265,7 +265,8 @@ def run_other(args):
         ref = None
         # error over the first 2^28 elements of C (the whole C of the 6912-block case is 38 GB)
         nref = 1 << 28
-        for key, prec in (("fp64", "fp64"), ("tf32x3", "tf32x3"), ("bf16x6", "bf16x6"), ("bf16x3", "bf16x3")):
+        for key, prec in (("fp64", "fp64"), ("ozaki", "ozaki"), ("tf32x3", "tf32x3"), ("bf16x6", "bf16x6"),
+                          ("bf16x3", "bf16x3")):
             ms = _timed(torch, lambda: bsm.multiply(1.0, A, B, 0.0, Cm, w["eps"], prec=prec, build_stacks=False),
                         args.steps, args.warmup)
             flop = Cm.counts().useful_flop
@@ -289,7 +290,7 @@ def run_other(args):
         dA = torch.empty(len(w["A"].data), dtype=torch.float64, device="cuda")
         dB = torch.empty(len(w["B"].data), dtype=torch.float64, device="cuda")
         legs = {}
-        for prec in ("fp64", "tf32x3"):
+        for prec in ("fp64", "ozaki", "tf32x3"):
             def step():
                 bsm.multiply(1.0, A, B, 0.0, Cm, 0.0, prec=prec)
                 bsm.multiply_backward(1.0, Cm, dC, A, B, dA, dB, prec=prec)
@@ -298,7 +299,8 @@ def run_other(args):
             legs[prec] = {"value": flop / ms * 1e-9, "ms_per_step": ms}
         out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
                    config={"workload": name, "step": "multiply + both adjoints", "products": Cm.counts().products,
-                           "useful_flop_per_step": flop}, split_precision={"tf32x3": legs["tf32x3"]})
+                           "useful_flop_per_step": flop},
+                   split_precision={"ozaki": legs["ozaki"], "tf32x3": legs["tf32x3"]})
     elif name == "smm_sweep":
         # square blocks m = n = k = s over the range of the paper's Fig. 1 (4..78):
         # uniform random patterns sized so that A + B hold about 1 GB of FP64 data
@@ -314,7 +316,7 @@ def run_other(args):
             Cm = bsm.Matrix.empty(bs, bs)
             row = {"s": s_, "nb": nb, "occupancy": occ}
             bsm.bsm_set_profiling(True)
-            for prec in ("fp64", "tf32x3"):
+            for prec in ("fp64", "ozaki", "tf32x3"):
                 num = []
                 ms = _timed(torch, lambda: (bsm.multiply(1.0, A, B, 0.0, Cm, 0.0, prec=prec, build_stacks=False),
                                             num.append(Cm.timings()["numeric"])), args.steps, args.warmup)
@@ -332,7 +334,7 @@ def run_other(args):
         w = I.purification_start(nb=2000)
         X0 = bsm.Matrix.from_host(w["X0"])
         legs = {}
-        for prec in ("fp64", "tf32x3"):
+        for prec in ("fp64", "ozaki", "tf32x3"):
             g = chain.McWeenyGraph(X0, w["steps"], w["eps"], prec=prec)
             flop = sum(h.counts().useful_flop for h in g.X2 + g.X3)
             ms = _timed(torch, g.replay, args.steps, args.warmup)
@@ -344,7 +346,7 @@ def run_other(args):
         out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
                    config={"workload": name, "step": "replay of the graph-captured 10-step chain (20 multiplies, "
                                                     "10 filtered adds)", "eps": w["eps"]},
-                   split_precision={"tf32x3": legs["tf32x3"]}, chain=legs)
+                   split_precision={"ozaki": legs["ozaki"], "tf32x3": legs["tf32x3"]}, chain=legs)
     print(json.dumps(out), flush=True)
 
 

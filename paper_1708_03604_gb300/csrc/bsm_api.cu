@@ -45,6 +45,18 @@ int variant_of(int prec, int m, int n) {
     if (v >= 0) return v;
     return m * n <= 16 ? 1 : 0;
 }
+// true when every output block shape (a row size of `rows` by a column size
+// of `cols`) runs the lane-per-block variant for `prec`
+bool all_lane(int prec, const std::vector<int32_t> &rows, const std::vector<int32_t> &cols) {
+    bool rs[kMaxBlockDim + 1] = {}, cs[kMaxBlockDim + 1] = {};
+    for (int32_t v : rows) rs[v] = true;
+    for (int32_t v : cols) cs[v] = true;
+    for (int m = 1; m <= kMaxBlockDim; ++m)
+        if (rs[m])
+            for (int n = 1; n <= kMaxBlockDim; ++n)
+                if (cs[n] && variant_of(prec, m, n) != 1) return false;
+    return true;
+}
 std::atomic<int64_t> g_launches{0};
 
 struct Scratch {
@@ -887,6 +899,13 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     } else if ((st = ensure_globals())) {
         return st;
     }
+    // kernel precision: the Ozaki path whose output blocks all run one per lane
+    // (plain FP64 FMA) needs no slices at all
+    int kprec = opts.prec;
+    if (opts.prec == BSM_P_OZAKI) {
+        if (no_sync) kprec = pl.kprec;
+        else if (all_lane(opts.prec, A->h_row_bs, B->h_col_bs)) kprec = BSM_P_FP64;
+    }
     if (opts.prec == BSM_P_OZAKI) {
         if (A->dtype != BSM_FP64) return set_error(BSM_ERR_UNSUPPORTED, "BSM_P_OZAKI needs FP64 data");
         if (no_sync) {
@@ -952,10 +971,10 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if ((st = cuda_check(e, "symbolic count"))) return st;
     // pack sizes of the tensor-core operands, known with the symbolic totals
     Packed pkA, pkB;
-    const bool tc = is_tc(opts.prec);
+    const bool tc = is_tc(kprec);
     if (tc) {
-        if ((st = pack_prepare(sc, A, 0, 0, opts.prec, pkA))) return st;
-        if ((st = pack_prepare(sc, B, 1, 0, opts.prec, pkB))) return st;
+        if ((st = pack_prepare(sc, A, 0, 0, kprec, pkA))) return st;
+        if ((st = pack_prepare(sc, B, 1, 0, kprec, pkB))) return st;
     }
     int64_t nprod, nnzbC, lenC, nfilt, mnk, packA_words = 0, packB_words = 0, max_ccnt = 0;
     int nchunk = 8;
@@ -1092,12 +1111,12 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (tc) {
         if ((st = sc.get(&pkA.words, (size_t)packA_words + 16)) || (st = sc.get(&pkB.words, (size_t)packB_words + 16)))
             return st;
-        if (opts.prec == BSM_P_OZAKI && ((st = oz_lines(sc, A, 0, 0, olA)) || (st = oz_lines(sc, B, 1, 0, olB))))
+        if (kprec == BSM_P_OZAKI && ((st = oz_lines(sc, A, 0, 0, olA)) || (st = oz_lines(sc, B, 1, 0, olB))))
             return st;
-        e = launch_pack(A, 0, 0, opts.prec, pkA.off, pkA.words, no_sync ? C->status : nullptr, g_stream, olA.line0,
+        e = launch_pack(A, 0, 0, kprec, pkA.off, pkA.words, no_sync ? C->status : nullptr, g_stream, olA.line0,
                         olA.exps);
         if (e == cudaSuccess)
-            e = launch_pack(B, 1, 0, opts.prec, pkB.off, pkB.words, no_sync ? C->status : nullptr, g_stream,
+            e = launch_pack(B, 1, 0, kprec, pkB.off, pkB.words, no_sync ? C->status : nullptr, g_stream,
                             olB.line0, olB.exps);
         if ((st = cuda_check(e, "pack"))) return st;
     }
@@ -1116,7 +1135,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.old_data = use_old ? C->data : nullptr;
     na.old_off = old_off;
     na.dtype = C->dtype;
-    na.prec = opts.prec;
+    na.prec = kprec;
     na.flush_every = opts.flush_every;
     na.x_pack = pkA.words; na.x_pack_off = pkA.off;
     na.y_pack = pkB.words; na.y_pack_off = pkB.off;
@@ -1141,7 +1160,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             return st;
     }
     na.n_lane_items = n_marked;
-    if (needs_plain(opts.prec) && uses_cores) {  // unpacked pieces for the CUDA-core split variant
+    if (needs_plain(kprec) && uses_cores) {  // unpacked pieces for the CUDA-core split variant
         const int np = split_pieces(opts.prec);
         float *xp = nullptr, *yp = nullptr;
         if ((st = sc.get(&xp, (size_t)A->data_len * np))) return st;
@@ -1191,7 +1210,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (!use_old && !opts.post_filter) {
         auto &P = C->plan;
         P.kind = 1; P.A = A; P.B = B; P.A_nnzb = A->nnzb; P.B_nnzb = B->nnzb; P.eps = filter_eps;
-        P.prec = opts.prec; P.nprod = nprod; P.nnzb = nnzbC; P.len = lenC; P.max_ccnt = max_ccnt;
+        P.prec = opts.prec; P.kprec = kprec; P.nprod = nprod; P.nnzb = nnzbC; P.len = lenC; P.max_ccnt = max_ccnt;
         P.uses_cores = uses_cores;
         P.nfilt = nfilt; P.mnk = mnk; P.nchunk = nchunk; P.packA = packA_words; P.packB = packB_words;
     }
@@ -1271,7 +1290,6 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         if ((st = ensure_starts(A)) || (st = ensure_starts(B)) || (st = ensure_starts(C))) return st;
     }
     Scratch sc;
-    const bool tc = is_tc(opts.prec);
     // dC as a matrix with C's pattern (a view: owns nothing)
     bsm_mat dC;
     dC.nbr = C->nbr; dC.nbc = C->nbc; dC.dtype = C->dtype; dC.nnzb = C->nnzb; dC.data_len = C->data_len;
@@ -1307,17 +1325,20 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         }
         const bsm_mat *X = side == 0 ? &dC : A;
         const bsm_mat *Y = side == 0 ? B : &dC;
+        int kprec = opts.prec;  // as in bsm_multiply
+        if (opts.prec == BSM_P_OZAKI && all_lane(opts.prec, OUT->h_row_bs, OUT->h_col_bs)) kprec = BSM_P_FP64;
+        const bool tc = is_tc(kprec);
         const int xt = side == 0 ? 0 : 1, yt = side == 0 ? 1 : 0;
         Packed pkX, pkY;
         OzLines olX, olY;
         if (tc && nprod > 0) {
-            if ((st = pack_prepare(sc, X, 0, xt, opts.prec, pkX))) return st;
-            if ((st = pack_prepare(sc, Y, 1, yt, opts.prec, pkY))) return st;
+            if ((st = pack_prepare(sc, X, 0, xt, kprec, pkX))) return st;
+            if ((st = pack_prepare(sc, Y, 1, yt, kprec, pkY))) return st;
             const int64_t *src[2] = {pkX.off + X->nnzb, pkY.off + Y->nnzb};
             if ((st = read_words(src, 2))) return st;
             const int64_t wx = g_host[0], wy = g_host[1];
-            if ((st = pack_fill(sc, X, 0, xt, opts.prec, pkX, wx, &olX))) return st;
-            if ((st = pack_fill(sc, Y, 1, yt, opts.prec, pkY, wy, &olY))) return st;
+            if ((st = pack_fill(sc, X, 0, xt, kprec, pkX, wx, &olX))) return st;
+            if ((st = pack_fill(sc, Y, 1, yt, kprec, pkY, wy, &olY))) return st;
         }
         NumericArgs na{};
         na.n_items = OUT->nnzb;
@@ -1332,7 +1353,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.alpha = alpha;
         na.beta = 0.0;
         na.dtype = C->dtype;
-        na.prec = opts.prec;
+        na.prec = kprec;
         na.flush_every = opts.flush_every;
         na.x_pack = pkX.words; na.x_pack_off = pkX.off;
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;
@@ -1346,7 +1367,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
                               opts.prec, &uses_cores, &n_marked)))
             return st;
         na.n_lane_items = n_marked;
-        if (needs_plain(opts.prec) && uses_cores && nprod > 0) {
+        if (needs_plain(kprec) && uses_cores && nprod > 0) {
             const int np = split_pieces(opts.prec);
             float *xp = nullptr, *yp = nullptr;
             cudaError_t e;

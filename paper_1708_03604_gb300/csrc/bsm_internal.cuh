@@ -82,6 +82,7 @@ struct bsm_mat {
         int64_t A_nnzb = -1, B_nnzb = -1;
         double eps = 0.0;
         int32_t prec = 0;
+        int32_t kprec = 0;  // precision the kernels ran (the Ozaki path with only lane items runs FP64)
         int64_t nprod = 0, nnzb = 0, len = 0, max_ccnt = 0, nfilt = 0, mnk = 0;
         int32_t nchunk = 1;
         int64_t packA = 0, packB = 0;

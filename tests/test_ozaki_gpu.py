@@ -170,6 +170,18 @@ def test_ozaki_lane_variants(bsm, oracle):
         bsm.bsm_set_variant("ozaki", 5, 5, -1)
 
 
+def test_ozaki_all_lane_shapes_run_fp64(bsm, oracle):
+    """Blocks of 1 and 4 rows/columns only: every output block runs one per
+    lane in FP64, so the Ozaki request gives the FP64 path's result bit for bit."""
+    w = I.purification_start(nb=200)
+    X = bsm.Matrix.from_host(w["X0"])
+    a = bsm.multiply(1.0, X, X, eps=w["eps"], prec="ozaki").data_host()
+    b = bsm.multiply(1.0, X, X, eps=w["eps"], prec="fp64").data_host()
+    np.testing.assert_array_equal(a, b)
+    ref = oracle.multiply(1.0, w["X0"], w["X0"], eps=w["eps"])
+    assert rel_fro(a, ref.C.data) <= TOL
+
+
 def test_ozaki_no_sync_matches_eager(bsm):
     w = I.mixed_banded(nb=150, occ=0.1, eps=1e-6)
     A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
