@@ -505,10 +505,36 @@ def main():
             if it > 0:
                 times.append(dt)
         et = max_ms(statistics.mean(times))
+        # one more (untimed) pass with a synchronisation after every stage: where the time goes
+        parts = {}
+
+        def mark(name, t_prev):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            parts[name] = round((t - t_prev) * 1e3, 2)
+            return t
+
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        hA = bsm.bsm_create(w["A"].row_bs, w["A"].col_bs, w["A"].row_ptr, w["A"].col_idx, w["A"].blk_off,
+                            bsm.BSM_FP64, pin["A"].data_ptr(), pin["A"].numel(), bsm.BSM_DATA_COPY)
+        hB = bsm.bsm_create(w["B"].row_bs, w["B"].col_bs, w["B"].row_ptr, w["B"].col_idx, w["B"].blk_off,
+                            bsm.BSM_FP64, pin["B"].data_ptr(), pin["B"].numel(), bsm.BSM_DATA_COPY)
+        hC = bsm.bsm_create_empty(w["A"].row_bs, w["B"].col_bs, bsm.BSM_FP64)
+        t = mark("create_and_h2d", t)
+        bsm.bsm_multiply(1.0, hA, hB, 0.0, hC, eps, bsm.make_opts("fp64"))
+        t = mark("multiply", t)
+        bsm.lib().bsm_copy_data(hC, out_host.data_ptr())
+        bsm.lib().bsm_copy_pattern(hC, rp.ctypes.data, ci.ctypes.data, bo.ctypes.data)
+        t = mark("d2h", t)
+        for h in (hA, hB, hC):
+            bsm.bsm_destroy(h)
+        mark("destroy", t)
         e2e = {"value": world * flop / et / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": et * 1e3,
                "includes": "host pattern validation, H2D of A and B from pinned memory, multiply, "
-                           "D2H of C's data (pinned) and pattern"}
+                           "D2H of C's data (pinned) and pattern",
+               "stage_ms_untimed_pass": parts}
 
     # ---------------- CPU oracle on sampled rows (+ parity of those rows)
     cpu = None

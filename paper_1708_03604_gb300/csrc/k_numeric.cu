@@ -1249,6 +1249,11 @@ __global__ void k_split_plain(int64_t n, const T *data, float *out) {
 // Digits of x on its line's grid (see the Ozaki section above): slice p is
 // d_p * 2^(-9p) as BF16 bits, exact.  e = unbiased exponent of the line.
 __device__ __forceinline__ void oz_slices(double x, int e, uint32_t (&out)[kOzSlices]) {
+    if (x == 0.0) {  // padding and exact zeros: no FP64 work
+#pragma unroll
+        for (int p = 0; p < kOzSlices; ++p) out[p] = 0u;
+        return;
+    }
     double y = ldexp(x, 7 - e);
     double sc = 1.0;
 #pragma unroll
