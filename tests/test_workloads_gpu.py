@@ -70,7 +70,7 @@ def test_uniform_23_full(env, oracle):
     w = I.uniform_23()
     A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
     ref = oracle.multiply(1.0, w["A"], w["B"])
-    for prec, tol in (("fp64", 1e-12), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
+    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("bf16x6", 1e-6), ("fp64", 1e-12)):
         Cm = bsm.multiply(1.0, A, B, prec=prec)
         rp, ci, bo = Cm.pattern()
         np.testing.assert_array_equal(rp, ref.C.row_ptr)
@@ -113,9 +113,9 @@ def test_mixed_3000_full_pattern_and_sampled_values(env, oracle):
     rows = np.sort(np.random.default_rng(11).choice(w["A"].nbr, 24, replace=False))
     ref = oracle.multiply(1.0, w["A"], w["B"], eps=w["eps"], rows=rows)
     _rows_check(bsm, torch, Cm, ref, rows, w["A"].row_bs, w["B"].col_bs, 1e-12, prods)
-    for prec in ("tf32x3", "bf16x6"):
+    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
         Ct = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec, build_stacks=False)
-        _rows_check(bsm, torch, Ct, ref, rows, w["A"].row_bs, w["B"].col_bs, 1e-6)
+        _rows_check(bsm, torch, Ct, ref, rows, w["A"].row_bs, w["B"].col_bs, tol)
 
 
 def test_large_23_sampled_rows(env, oracle):
@@ -132,10 +132,10 @@ def test_large_23_sampled_rows(env, oracle):
     assert cnt.useful_flop == 2 * 23 ** 3 * cnt.products
     _rows_check(bsm, torch, Cm, ref, rows, w["A"].row_bs, w["B"].col_bs, 1e-12)
     del Cm
-    for prec in ("tf32x3", "bf16x6"):
+    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
         Ct = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec, build_stacks=False)
         assert Ct.counts().products == cnt.products
-        _rows_check(bsm, torch, Ct, ref, rows, w["A"].row_bs, w["B"].col_bs, 1e-6)
+        _rows_check(bsm, torch, Ct, ref, rows, w["A"].row_bs, w["B"].col_bs, tol)
         del Ct
 
 
@@ -149,10 +149,14 @@ def test_differentiation_13_full(env, oracle, dtype):
     tdt = torch.float64 if dtype == "fp64" else torch.float32
     w = I.differentiation_13(dtype=npdt)
     A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
-    Cm = bsm.multiply(1.0, A, B, build_stacks=False)
     rows = np.sort(np.random.default_rng(5).choice(800, 16, replace=False))
     ref = oracle.multiply(1.0, w["A"], w["B"], rows=rows)
     tol = 1e-12 if dtype == "fp64" else 1e-5
+    if dtype == "fp64":  # the Ozaki path: forward rows, then both adjoints below
+        Co = bsm.multiply(1.0, A, B, prec="ozaki", build_stacks=False)
+        _rows_check(bsm, torch, Co, ref, rows, w["A"].row_bs, w["B"].col_bs, 1e-13)
+        del Co
+    Cm = bsm.multiply(1.0, A, B, build_stacks=False)
     _rows_check(bsm, torch, Cm, ref, rows, w["A"].row_bs, w["B"].col_bs, tol)
     rp, ci, bo = Cm.pattern()
     C_h = I.BCSR(w["A"].row_bs, w["B"].col_bs, rp, ci, bo, np.zeros(Cm.info().data_len))
@@ -160,7 +164,17 @@ def test_differentiation_13_full(env, oracle, dtype):
     dA = torch.empty(len(w["A"].data), dtype=tdt, device="cuda")
     dB = torch.empty(len(w["B"].data), dtype=tdt, device="cuda")
     bsm.multiply_backward(1.0, Cm, torch.tensor(G, dtype=tdt, device="cuda"), A, B, dA, dB)
+    outs = [(dA, dB, tol)]
+    if dtype == "fp64":
+        oA, oB = torch.empty_like(dA), torch.empty_like(dB)
+        bsm.multiply_backward(1.0, Cm, torch.tensor(G, dtype=tdt, device="cuda"), A, B, oA, oB, prec="ozaki")
+        outs.append((oA, oB, 1e-13))
     p = Cm.products()
+    for gA_, gB_, tol_ in outs:
+        _adjoint_blocks_check(oracle, w, p, C_h, G, npdt, gA_, gB_, tol_)
+
+
+def _adjoint_blocks_check(oracle, w, p, C_h, G, npdt, dA, dB, tol):
     rng = np.random.default_rng(6)
     for side, (idx, gout, X) in enumerate(((p.a, dA, w["A"]), (p.b, dB, w["B"]))):
         pick = rng.choice(X.nnzb, 64, replace=False)
@@ -212,7 +226,7 @@ def test_square_block_sizes_sweep(env, oracle, s):
     Bh = I.assemble(bs, bs, *I.uniform_pattern(nb, nb, 0.25, I.SEED_B), seed=I.SEED_B + 100)
     A, B = bsm.Matrix.from_host(Ah), bsm.Matrix.from_host(Bh)
     ref = oracle.multiply(1.0, Ah, Bh)
-    for prec, tol in (("fp64", 1e-12), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
+    for prec, tol in (("fp64", 1e-12), ("ozaki", 1e-13), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
         Cm = bsm.multiply(1.0, A, B, prec=prec, build_stacks=False)
         rp, ci, bo = Cm.pattern()
         np.testing.assert_array_equal(ci, ref.C.col_idx)
