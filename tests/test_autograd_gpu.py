@@ -83,6 +83,28 @@ def test_matmul_grad_central_fd(ag):
     assert err <= 1e-6, (err, bound)
 
 
+def test_ozaki_grad_vs_dense_autograd(ag):
+    """The differentiable multiply on the Ozaki path: loss and gradients against
+    dense torch autograd in FP64 (FP64-class agreement)."""
+    import torch
+    w = I.differentiation_13(nb=40, occ=0.15)
+    A = ag.BlockSparseTensor.from_bcsr(w["A"], requires_grad=True)
+    B = ag.BlockSparseTensor.from_bcsr(w["B"], requires_grad=True)
+    Cm = ag.matmul(A, B, prec="ozaki")
+    T = ag.BlockSparseTensor.from_bcsr(w["T"])
+    ic, it = ag.block_pair_index(Cm, T)
+    loss = (Cm.data ** 2).sum() - 2 * (Cm.data[ic] * T.data[it]).sum() + (T.data ** 2).sum()
+    loss.backward()
+    Ad = torch.tensor(to_dense(w["A"]), requires_grad=True)
+    Bd = torch.tensor(to_dense(w["B"]), requires_grad=True)
+    ld = ((Ad @ Bd - torch.tensor(to_dense(w["T"]))) ** 2).sum()
+    ld.backward()
+    assert abs(loss.item() - ld.item()) <= 1e-12 * abs(ld.item())
+    gA = to_dense(type(w["A"])(w["A"].row_bs, w["A"].col_bs, w["A"].row_ptr, w["A"].col_idx, w["A"].blk_off,
+                               A.data.grad.cpu().numpy()))
+    assert rel_fro(gA, Ad.grad.numpy() * block_mask(w["A"])) <= 1e-12
+
+
 def test_fp32_grad_vs_dense(ag):
     import torch
     w = I.differentiation_13(nb=30, occ=0.15)
@@ -99,7 +121,7 @@ def test_fp32_grad_vs_dense(ag):
     assert rel_fro(gA, Ad.grad.numpy() * block_mask(w["A"])) <= 1e-5
 
 
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp64", "ozaki", "tf32x3", "bf16x6"])
 def test_backward_vs_oracle_13(ag, oracle, prec):
     import torch
     from paper_1708_03604_gb300 import bsm
@@ -112,7 +134,7 @@ def test_backward_vs_oracle_13(ag, oracle, prec):
     dA = torch.empty(len(w["A"].data), dtype=torch.float64, device="cuda")
     dB = torch.empty(len(w["B"].data), dtype=torch.float64, device="cuda")
     bsm.multiply_backward(1.0, Cm, torch.tensor(G, device="cuda"), A, B, dA, dB, prec=prec)
-    tol = 1e-12 if prec == "fp64" else 1e-6
+    tol = {"fp64": 1e-12, "ozaki": 1e-13}.get(prec, 1e-6)
     assert rel_fro(dA.cpu().numpy(), dA_ref) <= tol
     assert rel_fro(dB.cpu().numpy(), dB_ref) <= tol
 
