@@ -469,10 +469,11 @@ def main():
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        pin = {}
-        for nm in ("A", "B"):
-            t = torch.from_numpy(w[nm].data).pin_memory()
-            pin[nm] = t
+        pin, pat = {}, {}
+        for nm in ("A", "B"):  # every input array in pinned host memory
+            pin[nm] = torch.from_numpy(w[nm].data).pin_memory()
+            pat[nm] = [torch.from_numpy(np.ascontiguousarray(getattr(w[nm], f))).pin_memory().numpy()
+                       for f in ("row_bs", "col_bs", "row_ptr", "col_idx", "blk_off")]
         ke = max(3, min(args.steps, 5))
         h2d = sum(w[nm].data.nbytes + w[nm].row_ptr.nbytes + w[nm].col_idx.nbytes + w[nm].blk_off.nbytes +
                   w[nm].row_bs.nbytes + w[nm].col_bs.nbytes for nm in ("A", "B"))
@@ -483,18 +484,18 @@ def main():
             barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            hA = bsm.bsm_create(w["A"].row_bs, w["A"].col_bs, w["A"].row_ptr, w["A"].col_idx, w["A"].blk_off,
-                                bsm.BSM_FP64, pin["A"].data_ptr(), pin["A"].numel(), bsm.BSM_DATA_COPY)
-            hB = bsm.bsm_create(w["B"].row_bs, w["B"].col_bs, w["B"].row_ptr, w["B"].col_idx, w["B"].blk_off,
-                                bsm.BSM_FP64, pin["B"].data_ptr(), pin["B"].numel(), bsm.BSM_DATA_COPY)
+            hA = bsm.bsm_create(*pat["A"], bsm.BSM_FP64, pin["A"].data_ptr(), pin["A"].numel(), bsm.BSM_DATA_COPY)
+            hB = bsm.bsm_create(*pat["B"], bsm.BSM_FP64, pin["B"].data_ptr(), pin["B"].numel(), bsm.BSM_DATA_COPY)
             hC = bsm.bsm_create_empty(w["A"].row_bs, w["B"].col_bs, bsm.BSM_FP64)
             bsm.bsm_multiply(1.0, hA, hB, 0.0, hC, eps, bsm.make_opts("fp64"))
             inf = bsm.bsm_get_info(hC)
             if out_host is None or out_host.numel() < inf.data_len:
+                # pinned host buffers for C's values and pattern
                 out_host = torch.empty(inf.data_len, dtype=torch.float64).pin_memory()
-                rp = np.zeros(inf.nbr + 1, np.int64)
-                ci = np.zeros(inf.nnzb, np.int32)
-                bo = np.zeros(inf.nnzb, np.int64)
+                rp_t = torch.empty(inf.nbr + 1, dtype=torch.int64).pin_memory()
+                ci_t = torch.empty(max(inf.nnzb, 1), dtype=torch.int32).pin_memory()
+                bo_t = torch.empty(max(inf.nnzb, 1), dtype=torch.int64).pin_memory()
+                rp, ci, bo = rp_t.numpy(), ci_t.numpy()[:inf.nnzb], bo_t.numpy()[:inf.nnzb]
             bsm.lib().bsm_copy_data(hC, out_host.data_ptr())
             bsm.lib().bsm_copy_pattern(hC, rp.ctypes.data, ci.ctypes.data, bo.ctypes.data)
             for h in (hA, hB, hC):
@@ -516,10 +517,8 @@ def main():
 
         torch.cuda.synchronize()
         t = time.perf_counter()
-        hA = bsm.bsm_create(w["A"].row_bs, w["A"].col_bs, w["A"].row_ptr, w["A"].col_idx, w["A"].blk_off,
-                            bsm.BSM_FP64, pin["A"].data_ptr(), pin["A"].numel(), bsm.BSM_DATA_COPY)
-        hB = bsm.bsm_create(w["B"].row_bs, w["B"].col_bs, w["B"].row_ptr, w["B"].col_idx, w["B"].blk_off,
-                            bsm.BSM_FP64, pin["B"].data_ptr(), pin["B"].numel(), bsm.BSM_DATA_COPY)
+        hA = bsm.bsm_create(*pat["A"], bsm.BSM_FP64, pin["A"].data_ptr(), pin["A"].numel(), bsm.BSM_DATA_COPY)
+        hB = bsm.bsm_create(*pat["B"], bsm.BSM_FP64, pin["B"].data_ptr(), pin["B"].numel(), bsm.BSM_DATA_COPY)
         hC = bsm.bsm_create_empty(w["A"].row_bs, w["B"].col_bs, bsm.BSM_FP64)
         t = mark("create_and_h2d", t)
         bsm.bsm_multiply(1.0, hA, hB, 0.0, hC, eps, bsm.make_opts("fp64"))
