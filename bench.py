@@ -431,41 +431,6 @@ def main():
                 "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2070 MHz"}
     C64 = Cm.data_tensor()
 
-    # ---------------- split-precision legs (variants per block shape autotuned first)
-    split = {}
-    tuned = {"fp64": tuned_fp64}
-    if not args.no_split:
-        from paper_1708_03604_gb300 import autotune
-        legs = [("ozaki", "ozaki", 0), ("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
-                ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2), ("tf32x3_pair4", "tf32x3", -4),
-                ("bf16x6_pair4", "bf16x6", -4)]
-        if args.legs:
-            legs = [lg for lg in legs if lg[0] in args.legs.split(",")]
-        for prec in dict.fromkeys(lg[1] for lg in legs):
-            tuned[prec] = autotune.tune(A, B, eps, prec=prec, reps=2)
-        ref_norm = torch.linalg.vector_norm(C64).item()
-        for key, prec, fl in legs:
-            step(prec, fl)
-            torch.cuda.synchronize()
-            bsm.bsm_set_profiling(True)
-            ks = max(3, min(args.steps, 5))
-            num = []
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for _ in range(ks):
-                step(prec, fl)
-                num.append(Cm.timings()["numeric"])
-            f1.record(stream)
-            torch.cuda.synchronize()
-            bsm.bsm_set_profiling(False)
-            sms = max_ms(f0.elapsed_time(f1)) / ks
-            err = (torch.linalg.vector_norm(Cm.data_tensor() - C64).item() / ref_norm)
-            split[key] = {"value": world * flop / (sms * 1e-3) / 1e12, "ms_per_step": sms,
-                           "numeric_ms": statistics.mean(num), "speedup_vs_fp64": ms / sms,
-                           "rel_fro_err_vs_fp64_path": err}
-        step()  # leave the FP64 result in Cm
-        torch.cuda.synchronize()
-
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -534,6 +499,41 @@ def main():
                "includes": "host pattern validation, H2D of A and B from pinned memory, multiply, "
                            "D2H of C's data (pinned) and pattern",
                "stage_ms_untimed_pass": parts}
+
+    # ---------------- split-precision legs (variants per block shape autotuned first)
+    split = {}
+    tuned = {"fp64": tuned_fp64}
+    if not args.no_split:
+        from paper_1708_03604_gb300 import autotune
+        legs = [("ozaki", "ozaki", 0), ("tf32x3", "tf32x3", 0), ("bf16x6", "bf16x6", 0), ("bf16x3", "bf16x3", 0),
+                ("tf32x3_fp64sum", "tf32x3", 1), ("tf32x3_pair2", "tf32x3", -2), ("tf32x3_pair4", "tf32x3", -4),
+                ("bf16x6_pair4", "bf16x6", -4)]
+        if args.legs:
+            legs = [lg for lg in legs if lg[0] in args.legs.split(",")]
+        for prec in dict.fromkeys(lg[1] for lg in legs):
+            tuned[prec] = autotune.tune(A, B, eps, prec=prec, reps=2)
+        ref_norm = torch.linalg.vector_norm(C64).item()
+        for key, prec, fl in legs:
+            step(prec, fl)
+            torch.cuda.synchronize()
+            bsm.bsm_set_profiling(True)
+            ks = max(3, min(args.steps, 5))
+            num = []
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(ks):
+                step(prec, fl)
+                num.append(Cm.timings()["numeric"])
+            f1.record(stream)
+            torch.cuda.synchronize()
+            bsm.bsm_set_profiling(False)
+            sms = max_ms(f0.elapsed_time(f1)) / ks
+            err = (torch.linalg.vector_norm(Cm.data_tensor() - C64).item() / ref_norm)
+            split[key] = {"value": world * flop / (sms * 1e-3) / 1e12, "ms_per_step": sms,
+                           "numeric_ms": statistics.mean(num), "speedup_vs_fp64": ms / sms,
+                           "rel_fro_err_vs_fp64_path": err}
+        step()  # leave the FP64 result in Cm
+        torch.cuda.synchronize()
 
     # ---------------- CPU oracle on sampled rows (+ parity of those rows)
     cpu = None
