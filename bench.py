@@ -90,12 +90,17 @@ def oracle_sample(w, target_s, seed=11, rows_hint=None):
     rng = np.random.default_rng(seed)
     order = rng.permutation(w["A"].nbr)
     n = rows_hint or 4
-    # calibrate on a few rows, then run the sized sample once
-    t0 = time.perf_counter()
-    O.multiply(1.0, w["A"], w["B"], eps=w["eps"], rows=np.sort(order[:n]))
-    dt = time.perf_counter() - t0
     if rows_hint is None:
-        n = int(max(4, min(len(order), n * target_s / max(dt, 1e-3))))
+        # calibrate on 4 and 16 rows (each call also pays a fixed cost: the block
+        # norms of all of A and B), then run the sized sample once
+        dts = []
+        for m in (4, 16):
+            t0 = time.perf_counter()
+            O.multiply(1.0, w["A"], w["B"], eps=w["eps"], rows=np.sort(order[:m]))
+            dts.append(time.perf_counter() - t0)
+        per_row = max((dts[1] - dts[0]) / 12, 1e-6)
+        fixed = max(dts[0] - 4 * per_row, 0.0)
+        n = int(max(4, min(len(order), (target_s - fixed) / per_row)))
     rows = np.sort(order[:n])
     t0 = time.perf_counter()
     r = O.multiply(1.0, w["A"], w["B"], eps=w["eps"], rows=rows)
