@@ -1137,6 +1137,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.dtype = C->dtype;
     na.prec = kprec;
     na.flush_every = opts.flush_every;
+    na.max_out_rows = A->max_bs_row; na.max_out_cols = B->max_bs_col;
     na.x_pack = pkA.words; na.x_pack_off = pkA.off;
     na.y_pack = pkB.words; na.y_pack_off = pkB.off;
     na.x_exp = olA.exps; na.x_line0 = olA.line0;
@@ -1354,6 +1355,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.beta = 0.0;
         na.dtype = C->dtype;
         na.prec = kprec;
+        na.max_out_rows = OUT->max_bs_row; na.max_out_cols = OUT->max_bs_col;
         na.flush_every = opts.flush_every;
         na.x_pack = pkX.words; na.x_pack_off = pkX.off;
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;

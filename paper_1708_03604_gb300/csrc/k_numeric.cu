@@ -108,8 +108,15 @@ __device__ __forceinline__ void cc_item(const NumericArgs &a, int64_t q, int lan
     }
 }
 
-template <typename T>
+// SMALL: every output block has at most 16 elements (one element per lane at
+// most), so only the smallest variants are compiled in and the kernel needs
+// far fewer registers (more warps per SM for these latency-bound blocks)
+template <typename T, bool SMALL>
 __device__ __forceinline__ void cc_dispatch(const NumericArgs &a, int64_t q, int lane) {
+    if constexpr (SMALL) {
+        cc_item<T, 1>(a, q, lane);
+        return;
+    }
     const int32_t orc = a.out_blk_rc[q];
     const int RS = rc_rows(orc) * rc_cols(orc);
     const int need = (RS + 31) >> 5;
@@ -246,9 +253,20 @@ __device__ __forceinline__ void cc_lane_fixed(const NumericArgs &a, int64_t q) {
         }
 }
 
-template <typename T>
+template <typename T, bool SMALL = false>
 __device__ __forceinline__ void cc_lane_dispatch(const NumericArgs &a, int64_t q) {
     const int32_t orc = a.out_blk_rc[q];
+    if constexpr (SMALL) {
+        switch ((rc_rows(orc) << 8) | rc_cols(orc)) {
+            case 0x101: cc_lane_fixed<T, 1, 1>(a, q); break;
+            case 0x104: cc_lane_fixed<T, 1, 4>(a, q); break;
+            case 0x401: cc_lane_fixed<T, 4, 1>(a, q); break;
+            case 0x404: cc_lane_fixed<T, 4, 4>(a, q); break;
+            case 0x202: cc_lane_fixed<T, 2, 2>(a, q); break;
+            default: cc_lane_item<T>(a, q); break;
+        }
+        return;
+    }
     switch ((rc_rows(orc) << 8) | rc_cols(orc)) {
         case 0x101: cc_lane_fixed<T, 1, 1>(a, q); break;
         case 0x102: cc_lane_fixed<T, 1, 2>(a, q); break;
@@ -265,7 +283,7 @@ __device__ __forceinline__ void cc_lane_dispatch(const NumericArgs &a, int64_t q
     }
 }
 
-template <typename T>
+template <typename T, bool SMALL>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
     const int lane = threadIdx.x & 31;
     if (a.status && *a.status != 0) return;
@@ -282,12 +300,12 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
-            cc_dispatch<T>(a, q, lane);
+            cc_dispatch<T, SMALL>(a, q, lane);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
             if (idx < a.n_items) {
                 const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                cc_lane_dispatch<T>(a, q);
+                cc_lane_dispatch<T, SMALL>(a, q);
             }
         }
     }
@@ -1561,10 +1579,17 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
         if (e == cudaSuccess)
             k_numeric_oz<<<persistent_grid(k_numeric_oz, a.n_items, smem), kThreadsNum, smem, s>>>(a);
     } else if (!tc) {
+        const bool small = a.max_out_rows > 0 && a.max_out_rows * a.max_out_cols <= 16;
         if (a.dtype == BSM_FP64) {
-            k_numeric_cc<double><<<persistent_grid(k_numeric_cc<double>, a.n_items), kThreadsNum, 0, s>>>(a);
+            if (small)
+                k_numeric_cc<double, true><<<persistent_grid(k_numeric_cc<double, true>, a.n_items), kThreadsNum, 0, s>>>(a);
+            else
+                k_numeric_cc<double, false><<<persistent_grid(k_numeric_cc<double, false>, a.n_items), kThreadsNum, 0, s>>>(a);
         } else {
-            k_numeric_cc<float><<<persistent_grid(k_numeric_cc<float>, a.n_items), kThreadsNum, 0, s>>>(a);
+            if (small)
+                k_numeric_cc<float, true><<<persistent_grid(k_numeric_cc<float, true>, a.n_items), kThreadsNum, 0, s>>>(a);
+            else
+                k_numeric_cc<float, false><<<persistent_grid(k_numeric_cc<float, false>, a.n_items), kThreadsNum, 0, s>>>(a);
         }
     } else if (a.prec == BSM_P_TF32x3) {
         e = launch_tc<BSM_P_TF32x3>(a, s);
