@@ -264,6 +264,29 @@ def test_deterministic(bsm):
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_all_tiny_blocks(bsm, oracle, dt):
+    """Blocks of 1, 2 and 4 rows/columns only (every output block at most 16
+    elements: the small-register build of the CUDA-core kernel), FP64 and FP32
+    data, with a transposed adjoint."""
+    import torch
+    bs = I.mixed_sizes(80, (1, 2, 4), (0.4, 0.2, 0.4), seed=17)
+    A, B = random_bcsr(bs, bs, 0.2, seed=91, dtype=dt), random_bcsr(bs, bs, 0.2, seed=92, dtype=dt)
+    Cg, ref, gA, gB = _run(bsm, oracle, A, B, 0.0)
+    _check_pattern(Cg, ref.C)
+    tol = 1e-12 if dt == np.float64 else 1e-5
+    assert rel_fro(Cg.data_host(), ref.C.data) <= tol
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    G = np.random.default_rng(2).standard_normal(ref.C.data_len)
+    dA_ref, dB_ref = oracle.multiply_backward(1.0, A.astype(np.float64), B.astype(np.float64), ref.C,
+                                              G.astype(dt).astype(np.float64), ref.prods)
+    dA = torch.empty(len(A.data), dtype=tdt, device="cuda")
+    dB = torch.empty(len(B.data), dtype=tdt, device="cuda")
+    bsm.multiply_backward(1.0, Cg, torch.tensor(G, dtype=tdt, device="cuda"), gA, gB, dA, dB)
+    assert rel_fro(dA.double().cpu().numpy(), dA_ref) <= tol
+    assert rel_fro(dB.double().cpu().numpy(), dB_ref) <= tol
+
+
 def test_fp32_data(bsm, oracle):
     w = I.differentiation_13(nb=60, occ=0.15, dtype=np.float32)
     Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], 0.0)
