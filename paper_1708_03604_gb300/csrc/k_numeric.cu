@@ -108,18 +108,32 @@ __device__ __forceinline__ void cc_item(const NumericArgs &a, int64_t q, int lan
     }
 }
 
-// SMALL: every output block has at most 16 elements (one element per lane at
-// most), so only the smallest variants are compiled in and the kernel needs
-// far fewer registers (more warps per SM for these latency-bound blocks)
-template <typename T, bool SMALL>
+// Builds of the CUDA-core kernel (the widest element-per-lane template sets
+// the register count, and with it how many warps an SM holds):
+//   kCcSmall  every output block has at most 16 elements: one element per lane
+//             at most (72 registers)
+//   kCcNarrow up to 9 elements per lane per pass, more passes over the
+//             products for larger blocks (128 registers)
+//   kCcWide   up to 24 elements per lane per pass (253 registers)
+constexpr int kCcSmall = 0, kCcNarrow = 1, kCcWide = 2;
+template <typename T, int BUILD>
 __device__ __forceinline__ void cc_dispatch(const NumericArgs &a, int64_t q, int lane) {
-    if constexpr (SMALL) {
+    if constexpr (BUILD == kCcSmall) {
         cc_item<T, 1>(a, q, lane);
         return;
     }
     const int32_t orc = a.out_blk_rc[q];
     const int RS = rc_rows(orc) * rc_cols(orc);
     const int need = (RS + 31) >> 5;
+    if constexpr (BUILD == kCcNarrow) {
+        if (need <= 1) cc_item<T, 1>(a, q, lane);
+        else if (need <= 2) cc_item<T, 2>(a, q, lane);
+        else if (need <= 3) cc_item<T, 3>(a, q, lane);
+        else if (need <= 4) cc_item<T, 4>(a, q, lane);
+        else if (need <= 6) cc_item<T, 6>(a, q, lane);
+        else cc_item<T, 9>(a, q, lane);
+        return;
+    }
     if (need <= 1) cc_item<T, 1>(a, q, lane);
     else if (need <= 2) cc_item<T, 2>(a, q, lane);
     else if (need <= 3) cc_item<T, 3>(a, q, lane);
@@ -253,10 +267,10 @@ __device__ __forceinline__ void cc_lane_fixed(const NumericArgs &a, int64_t q) {
         }
 }
 
-template <typename T, bool SMALL = false>
+template <typename T, int BUILD = kCcWide>
 __device__ __forceinline__ void cc_lane_dispatch(const NumericArgs &a, int64_t q) {
     const int32_t orc = a.out_blk_rc[q];
-    if constexpr (SMALL) {
+    if constexpr (BUILD == kCcSmall) {
         switch ((rc_rows(orc) << 8) | rc_cols(orc)) {
             case 0x101: cc_lane_fixed<T, 1, 1>(a, q); break;
             case 0x104: cc_lane_fixed<T, 1, 4>(a, q); break;
@@ -283,7 +297,7 @@ __device__ __forceinline__ void cc_lane_dispatch(const NumericArgs &a, int64_t q
     }
 }
 
-template <typename T, bool SMALL>
+template <typename T, int BUILD>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
     const int lane = threadIdx.x & 31;
     if (a.status && *a.status != 0) return;
@@ -300,12 +314,12 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
-            cc_dispatch<T, SMALL>(a, q, lane);
+            cc_dispatch<T, BUILD>(a, q, lane);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
             if (idx < a.n_items) {
                 const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                cc_lane_dispatch<T, SMALL>(a, q);
+                cc_lane_dispatch<T, BUILD>(a, q);
             }
         }
     }
@@ -1552,6 +1566,11 @@ int persistent_grid(K kernel, int64_t n_items, size_t smem = 0) {
     return (int)g;
 }
 
+template <typename T, int BUILD>
+void launch_cc(const NumericArgs &a, cudaStream_t s) {
+    k_numeric_cc<T, BUILD><<<persistent_grid(k_numeric_cc<T, BUILD>, a.n_items), kThreadsNum, 0, s>>>(a);
+}
+
 template <int PREC, bool FF>
 cudaError_t launch_tc_ff(const NumericArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC>() * kWarpsPerCta;
@@ -1579,17 +1598,19 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
         if (e == cudaSuccess)
             k_numeric_oz<<<persistent_grid(k_numeric_oz, a.n_items, smem), kThreadsNum, smem, s>>>(a);
     } else if (!tc) {
-        const bool small = a.max_out_rows > 0 && a.max_out_rows * a.max_out_cols <= 16;
+        // the build by the largest output block: all within one narrow pass
+        // (<= 288 elements) or beyond the wide ladder's single pass (> 768)
+        // run narrow -- measured faster there -- the rest wide
+        const int area = a.max_out_rows * a.max_out_cols;
+        const int build = (area > 0 && area <= 16) ? kCcSmall : (area <= 288 || area > 768) ? kCcNarrow : kCcWide;
         if (a.dtype == BSM_FP64) {
-            if (small)
-                k_numeric_cc<double, true><<<persistent_grid(k_numeric_cc<double, true>, a.n_items), kThreadsNum, 0, s>>>(a);
-            else
-                k_numeric_cc<double, false><<<persistent_grid(k_numeric_cc<double, false>, a.n_items), kThreadsNum, 0, s>>>(a);
+            if (build == kCcSmall) launch_cc<double, kCcSmall>(a, s);
+            else if (build == kCcNarrow) launch_cc<double, kCcNarrow>(a, s);
+            else launch_cc<double, kCcWide>(a, s);
         } else {
-            if (small)
-                k_numeric_cc<float, true><<<persistent_grid(k_numeric_cc<float, true>, a.n_items), kThreadsNum, 0, s>>>(a);
-            else
-                k_numeric_cc<float, false><<<persistent_grid(k_numeric_cc<float, false>, a.n_items), kThreadsNum, 0, s>>>(a);
+            if (build == kCcSmall) launch_cc<float, kCcSmall>(a, s);
+            else if (build == kCcNarrow) launch_cc<float, kCcNarrow>(a, s);
+            else launch_cc<float, kCcWide>(a, s);
         }
     } else if (a.prec == BSM_P_TF32x3) {
         e = launch_tc<BSM_P_TF32x3>(a, s);
