@@ -878,106 +878,6 @@ __host__ __device__ constexpr int oz_ring_words_per_warp() { return kOzStages * 
 // pairs).  A ring stage is chunk-major the same way (chunk c of lane L at
 // word c * 128 + 4 * L): each 16-byte copy and read of the warp covers 512
 // contiguous bytes of shared memory.
-//
-// Half steps.  When a block's last k-step has at most 8 terms, its fragment
-// registers for k + 8 (X: v2, v3; Y: v1) are zero, so two such steps of
-// different block products of one output block fit one k16 MMA step: the
-// first one's k-low registers in the k-low slots, the second one's in the
-// k-high slots.  Those last tiles are stored as half tiles:
-//   X half tile, 3 chunks: chunk c = planes 2c, 2c+1 (v0 v1 each)
-//   Y half tile, 2 chunks: v0 of plane p < 4 at word p ^ ((lane >> 3) & 3) of
-//                          chunk 0; v0 of planes 4, 5 in words 0, 1 of chunk 1
-// and a ring stage holds either one full step or a merged pair of half steps
-// (X: first half in slots 0..2, second in 3..5; Y tile j: first half chunk 0
-// in slot 6+3j, chunk 1's 8 bytes of both halves in slot 6+3j+1, second half
-// chunk 0 in slot 6+3j+2); an unpaired half step gets zeros for the second.
-__host__ __device__ __forceinline__ bool oz_last_half(int k) { return k - 16 * ((k + 15) / 16 - 1) <= 8; }
-// chunks of the packing of a logical R x T block in role X / T x S in role Y
-__host__ __device__ __forceinline__ int64_t oz_pack_chunks(int rows, int cols, int role_y) {
-    if (!role_y) {
-        const int MT = (rows + 15) / 16, KT = (cols + 15) / 16;
-        const int h = oz_last_half(cols) ? 1 : 0;
-        return (int64_t)(KT - h) * MT * 6 + (int64_t)h * MT * 3;
-    }
-    const int KT = (rows + 15) / 16, NT = (cols + 7) / 8;
-    const int h = oz_last_half(rows) ? 1 : 0;
-    return (int64_t)(KT - h) * NT * 3 + (int64_t)h * NT * 2;
-}
-
-// cp.async with zero fill: src_bytes = 0 writes zeros without reading global memory
-__device__ __forceinline__ void cp_async16_cg_zfill(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async8_zfill(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
-
-// The 21 slice products of one ring stage holding a full k-step.
-template <int NTC>
-__device__ __forceinline__ void oz_step_full(const uint32_t *w, float (&acc)[kOzLevels][NTC][4], int hswz) {
-    uint32_t fa[kOzSlices][4];
-#pragma unroll
-    for (int p = 0; p < kOzSlices; ++p) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(w + 128 * p);
-        fa[p][0] = v.x; fa[p][1] = v.y; fa[p][2] = v.z; fa[p][3] = v.w;
-    }
-    // Y slice q (read from the ring when needed) with every X slice p of level p + q <= 5
-#pragma unroll
-    for (int qq = kOzSlices - 1; qq >= 0; --qq) {
-        uint32_t fb[NTC][2];
-#pragma unroll
-        for (int j = 0; j < NTC; ++j) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(w + 128 * (6 + 3 * j + (qq >> 1)) + 2 * ((qq & 1) ^ hswz));
-            fb[j][0] = v.x; fb[j][1] = v.y;
-        }
-#pragma unroll
-        for (int p = kOzSlices - 1 - qq; p >= 0; --p)
-#pragma unroll
-            for (int j = 0; j < NTC; ++j) {
-                constexpr int top = kOzLevels - 1;
-                mma_bf16(acc[p + qq < top ? p + qq : top][j], fa[p], fb[j]);
-            }
-    }
-}
-
-// The 21 slice products of a ring stage holding two half steps: the first
-// one's k-low registers in the MMA's k-low slots, the second one's in the
-// k-high slots.
-template <int NTC>
-__device__ __forceinline__ void oz_step_halves(const uint32_t *w, float (&acc)[kOzLevels][NTC][4], int wswz) {
-    uint32_t fa[kOzSlices][4];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const uint4 u = *reinterpret_cast<const uint4 *>(w + 128 * c);
-        const uint4 v = *reinterpret_cast<const uint4 *>(w + 128 * (3 + c));
-        fa[2 * c][0] = u.x; fa[2 * c][1] = u.y; fa[2 * c][2] = v.x; fa[2 * c][3] = v.y;
-        fa[2 * c + 1][0] = u.z; fa[2 * c + 1][1] = u.w; fa[2 * c + 1][2] = v.z; fa[2 * c + 1][3] = v.w;
-    }
-    uint4 hi45[NTC];  // planes 4, 5 of both halves
-#pragma unroll
-    for (int j = 0; j < NTC; ++j) hi45[j] = *reinterpret_cast<const uint4 *>(w + 128 * (6 + 3 * j + 1));
-#pragma unroll
-    for (int qq = kOzSlices - 1; qq >= 0; --qq) {
-        uint32_t fb[NTC][2];
-#pragma unroll
-        for (int j = 0; j < NTC; ++j) {
-            if (qq >= 4) {
-                fb[j][0] = qq == 5 ? hi45[j].y : hi45[j].x;
-                fb[j][1] = qq == 5 ? hi45[j].w : hi45[j].z;
-            } else {
-                fb[j][0] = w[128 * (6 + 3 * j) + (qq ^ wswz)];
-                fb[j][1] = w[128 * (6 + 3 * j + 2) + (qq ^ wswz)];
-            }
-        }
-#pragma unroll
-        for (int p = kOzSlices - 1 - qq; p >= 0; --p)
-#pragma unroll
-            for (int j = 0; j < NTC; ++j) {
-                constexpr int top = kOzLevels - 1;
-                mma_bf16(acc[p + qq < top ? p + qq : top][j], fa[p], fb[j]);
-            }
-    }
-}
 
 // One pass over a 1 x NTC super tile (16 x 8*NTC output elements) at (mt0, nt0).
 template <int NTC>
@@ -1048,11 +948,10 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
             spilled = true;
         }
     };
-    const int wswz = (lane >> 3) & 3;  // word order inside a Y half tile's first chunk
     for (int64_t pb = p0; pb < p1; pb += 32) {
         const int nb = (int)min((int64_t)32, p1 - pb);
         int64_t mxo = 0, myo = 0;
-        int mkt = 0, mtn = 0, mh = 0;
+        int mkt = 0, mtn = 0;
         if (lane < nb) {
             const int32_t ix = a.px[pb + lane], iy = a.py[pb + lane];
             const int32_t xrc = a.x_blk_rc[ix];
@@ -1060,112 +959,88 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
             mxo = a.x_pack_off[ix];
             myo = a.y_pack_off[iy];
             mkt = (mtn + 15) >> 4;
-            mh = oz_last_half(mtn) ? 1 : 0;
         }
-        // ring slots of this batch: every full k-step, and the half steps two by two
-        int nfull = mkt - mh, nhalf = mh;
+        int nsteps = mkt;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            nfull += __shfl_xor_sync(0xffffffffu, nfull, o);
-            nhalf += __shfl_xor_sync(0xffffffffu, nhalf, o);
-        }
-        const int nslots = nfull + ((nhalf + 1) >> 1);
-        // producer cursor over (product, k-step); a half step waits for the next one
+        for (int o = 16; o > 0; o >>= 1) nsteps += __shfl_xor_sync(0xffffffffu, nsteps, o);
         int pu = 0, pk = 0;
         int64_t pxo = __shfl_sync(0xffffffffu, mxo, 0), pyo = __shfl_sync(0xffffffffu, myo, 0);
-        int pkt = __shfl_sync(0xffffffffu, mkt, 0), ptn = __shfl_sync(0xffffffffu, mtn, 0);
-        bool have_half = false;
-        int64_t hxo = 0, hyo = 0;
-        int hk = 0, hkt = 0;
-        uint32_t desc = 0;  // per stage st, bits 8st..8st+7: k terms (bits 0..4), half-step slot (bit 5)
-        auto next_product = [&]() {
-            pk = 0;
-            ++pu;
-            const int sl = pu < nb ? pu : 0;
-            pxo = __shfl_sync(0xffffffffu, mxo, sl);
-            pyo = __shfl_sync(0xffffffffu, myo, sl);
-            pkt = __shfl_sync(0xffffffffu, mkt, sl);
-            ptn = __shfl_sync(0xffffffffu, mtn, sl);
-        };
-        // the half tiles of (xo1, yo1) at k-step kt1 and of (xo2, yo2) at kt2 (zeros when !two)
-        auto copy_halves = [&](uint32_t dst, int64_t xo1, int64_t yo1, int kt1, int64_t xo2, int64_t yo2, int kt2,
-                               bool two) {
-            const uint32_t *x1 = XP + xo1 + 128 * ((int64_t)kt1 * MT * 6 + (int64_t)mt0 * 3) + 4 * lane;
-            const uint32_t *x2 = XP + xo2 + 128 * ((int64_t)kt2 * MT * 6 + (int64_t)mt0 * 3) + 4 * lane;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                cp_async16_cg(dst + 512u * c, x1 + 128 * c);
-                cp_async16_cg_zfill(dst + 512u * (3 + c), x2 + 128 * c, two ? 16u : 0u);
-            }
-#pragma unroll
-            for (int j = 0; j < NTC; ++j) {
-                const uint32_t *y1 = YP + yo1 + 128 * ((int64_t)kt1 * NT * 3 + (int64_t)(nt0 + j) * 2) + 4 * lane;
-                const uint32_t *y2 = YP + yo2 + 128 * ((int64_t)kt2 * NT * 3 + (int64_t)(nt0 + j) * 2) + 4 * lane;
-                const uint32_t d = dst + 512u * (6 + 3 * j);
-                cp_async16_cg(d, y1);
-                cp_async8_zfill(d + 512u, y1 + 128, 8u);
-                cp_async8_zfill(d + 512u + 8u, y2 + 128, two ? 8u : 0u);
-                cp_async16_cg_zfill(d + 1024u, y2, two ? 16u : 0u);
-            }
-        };
+        int pkt = __shfl_sync(0xffffffffu, mkt, 0);
         auto produce = [&](int st) {
             const uint32_t dst = ring_s + (uint32_t)(st * 32 * SW) * 4u;
-            uint32_t dv = 0;
-            while (true) {
-                if (pu < nb) {
-                    if (!(pk == pkt - 1 && oz_last_half(ptn))) {  // a full k-step
-                        const uint32_t *src = XP + pxo + 128 * ((int64_t)pk * MT * 6 + (int64_t)mt0 * 6) + 4 * lane;
+            const uint32_t *src = XP + pxo + (int64_t)(pk * MT + mt0) * (32 * kOzXW) + 4 * lane;
 #pragma unroll
-                        for (int c = 0; c < 6; ++c) cp_async16_cg(dst + 512u * c, src + 128 * c);
+            for (int c = 0; c < kOzXW / 4; ++c) cp_async16_cg(dst + 512u * c, src + 128 * c);
 #pragma unroll
-                        for (int j = 0; j < NTC; ++j) {
-                            const uint32_t *ys = YP + pyo + 128 * ((int64_t)pk * NT * 3 + (int64_t)(nt0 + j) * 3) + 4 * lane;
+            for (int j = 0; j < NTC; ++j) {
+                if (nt0 + j < NT) {
+                    const uint32_t *ys = YP + pyo + (int64_t)(pk * NT + nt0 + j) * (32 * kOzYW) + 4 * lane;
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) cp_async16_cg(dst + 512u * (6 + 3 * j + c), ys + 128 * c);
-                        }
-                        dv = (uint32_t)min(16, ptn - 16 * pk);
-                        if (++pk == pkt) next_product();
-                        break;
-                    }
-                    if (!have_half) {  // this product's half step waits for the next one
-                        have_half = true;
-                        hxo = pxo; hyo = pyo; hk = ptn - 16 * pk; hkt = pk;
-                        next_product();
-                        continue;
-                    }
+                    for (int c = 0; c < kOzYW / 4; ++c)
+                        cp_async16_cg(dst + 512u * (kOzXW / 4 + j * (kOzYW / 4) + c), ys + 128 * c);
                 }
-                // a half-step slot: the waiting half step and this product's one,
-                // or at the end of the batch the waiting one alone (the slot
-                // count leaves exactly that one there)
-                const bool two = pu < nb;
-                copy_halves(dst, hxo, hyo, hkt, two ? pxo : hxo, two ? pyo : hyo, two ? pk : hkt, two);
-                dv = 32u | (uint32_t)(hk + (two ? ptn - 16 * pk : 0));
-                have_half = false;
-                if (two) next_product();
-                break;
             }
-            desc = (desc & ~(0xffu << (8 * st))) | (dv << (8 * st));
+            if (++pk == pkt) {
+                pk = 0;
+                ++pu;
+                const int src_lane = pu < nb ? pu : 0;
+                pxo = __shfl_sync(0xffffffffu, mxo, src_lane);
+                pyo = __shfl_sync(0xffffffffu, myo, src_lane);
+                pkt = __shfl_sync(0xffffffffu, mkt, src_lane);
+            }
         };
 #pragma unroll
         for (int st = 0; st < ST - 1; ++st) {
-            if (st < nslots) produce(st);
+            if (st < nsteps) produce(st);
             cp_async_commit();
         }
-        for (int s = 0; s < nslots; ++s) {
-            if (s + ST - 1 < nslots) produce((s + ST - 1) % ST);
+        int cu = 0, ck = 0;
+        int ckt = __shfl_sync(0xffffffffu, mkt, 0), ctn = __shfl_sync(0xffffffffu, mtn, 0);
+        for (int s = 0; s < nsteps; ++s) {
+            if (s + ST - 1 < nsteps) produce((s + ST - 1) % ST);
             cp_async_commit();
             cp_async_wait<ST - 1>();
             const uint32_t *w = myring + (s % ST) * 32 * SW;
-            const uint32_t dv = (desc >> (8 * (s % ST))) & 0xffu;
-            const int kact = (int)(dv & 31u);
+            uint32_t fa[kOzSlices][4];
+#pragma unroll
+            for (int p = 0; p < kOzSlices; ++p) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(w + 128 * p);
+                fa[p][0] = v.x; fa[p][1] = v.y; fa[p][2] = v.z; fa[p][3] = v.w;
+            }
             // close the exact window before it would pass kOzWindow terms of k
+            const int kact = min(16, ctn - 16 * ck);
             if (kacc + kact > kOzWindow) {
                 close_window();
                 kacc = 0;
             }
             kacc += kact;
-            if (dv & 32u) oz_step_halves<NTC>(w, acc, wswz);
-            else oz_step_full<NTC>(w, acc, hswz);
+            // slice products: Y slice q (read from the ring when needed) with
+            // every X slice p of level p + q <= 5
+#pragma unroll
+            for (int qq = kOzSlices - 1; qq >= 0; --qq) {
+                uint32_t fb[NTC][2];
+#pragma unroll
+                for (int j = 0; j < NTC; ++j) {
+                    const uint2 v = *reinterpret_cast<const uint2 *>(
+                        w + 128 * (kOzXW / 4 + j * (kOzYW / 4) + (qq >> 1)) + 2 * ((qq & 1) ^ hswz));
+                    fb[j][0] = v.x; fb[j][1] = v.y;
+                }
+#pragma unroll
+                for (int p = kOzSlices - 1 - qq; p >= 0; --p)
+#pragma unroll
+                    for (int j = 0; j < NTC; ++j)
+                        if (nt0 + j < NT) {
+                            constexpr int top = kOzLevels - 1;
+                            mma_bf16(acc[p + qq < top ? p + qq : top][j], fa[p], fb[j]);
+                        }
+            }
+            if (++ck == ckt) {
+                ck = 0;
+                ++cu;
+                const int src_lane = cu < nb ? cu : 0;
+                ckt = __shfl_sync(0xffffffffu, mkt, src_lane);
+                ctn = __shfl_sync(0xffffffffu, mtn, src_lane);
+            }
         }
         cp_async_wait<0>();
     }
@@ -1282,7 +1157,6 @@ __device__ __forceinline__ double elem(const T *b, int R, int Tn, int trans, int
 
 // words of one block's packing
 __device__ __forceinline__ int64_t pack_words(int R, int C, int role_y, int prec) {
-    if (prec == BSM_P_OZAKI) return 128 * oz_pack_chunks(R, C, role_y);
     const int K = (prec == BSM_P_TF32x3) ? 8 : 16;
     if (!role_y) {
         const int XW = prec == BSM_P_OZAKI ? kOzXW : (prec == BSM_P_BF16x6) ? 12 : 8;
@@ -1439,57 +1313,38 @@ __global__ void k_pack_oz(int64_t nnzb, const int64_t *blk_off, const int32_t *b
         int rows, cols;
         logical_dims(blk_rc[b], trans, rows, cols);
         const int32_t l0 = line0[b];
-        uint32_t *dst = pack + pack_off[b] + 4 * lane;
+        uint32_t *dst = pack + pack_off[b];
         uint32_t lo[kOzSlices], hi[kOzSlices];
-        const int hs = (lane >> 3) & 1, ws = (lane >> 3) & 3;
         if (!role_y) {
             const int MT = (rows + 15) / 16, KT = (cols + 15) / 16;
-            const bool lh = oz_last_half(cols);
-            for (int kt = 0; kt < KT; ++kt) {
-                const bool half = lh && kt == KT - 1;
+            for (int kt = 0; kt < KT; ++kt)
                 for (int mt = 0; mt < MT; ++mt) {
-                    uint32_t *w = dst + 128 * ((int64_t)kt * MT * 6 + (int64_t)mt * (half ? 3 : 6));
+                    uint32_t *w = dst + (int64_t)(kt * MT + mt) * (32 * kOzXW) + 4 * lane;
                     const int r0 = mt * 16 + g, k0 = kt * 16;
                     const int rr[4] = {r0, r0 + 8, r0, r0 + 8};
                     const int kk[4] = {k0 + 2 * t4, k0 + 2 * t4, k0 + 2 * t4 + 8, k0 + 2 * t4 + 8};
-                    for (int v = 0; v < (half ? 2 : 4); ++v) {
+                    for (int v = 0; v < 4; ++v) {
                         const int e = rr[v] < rows ? exps[l0 + rr[v]] - 1023 : 0;
                         oz_slices(elem<double>(src, rows, cols, trans, rr[v], kk[v]), e, lo);
                         oz_slices(elem<double>(src, rows, cols, trans, rr[v], kk[v] + 1), e, hi);
-                        for (int p = 0; p < kOzSlices; ++p) {
-                            const uint32_t word = lo[p] | (hi[p] << 16);
-                            if (half) w[128 * (p >> 1) + 2 * (p & 1) + v] = word;
-                            else w[128 * p + v] = word;
-                        }
+                        for (int p = 0; p < kOzSlices; ++p) w[128 * p + v] = lo[p] | (hi[p] << 16);
                     }
                 }
-            }
         } else {
             const int KT = (rows + 15) / 16, NT = (cols + 7) / 8;
-            const bool lh = oz_last_half(rows);
-            for (int kt = 0; kt < KT; ++kt) {
-                const bool half = lh && kt == KT - 1;
+            for (int kt = 0; kt < KT; ++kt)
                 for (int nt = 0; nt < NT; ++nt) {
-                    uint32_t *w = dst + 128 * ((int64_t)kt * NT * 3 + (int64_t)nt * (half ? 2 : 3));
+                    uint32_t *w = dst + (int64_t)(kt * NT + nt) * (32 * kOzYW) + 4 * lane;
                     const int n0 = nt * 8 + g, k0 = kt * 16;
                     const int e = n0 < cols ? exps[l0 + n0] - 1023 : 0;
                     const int kk[2] = {k0 + 2 * t4, k0 + 2 * t4 + 8};
-                    for (int v = 0; v < (half ? 1 : 2); ++v) {
+                    for (int v = 0; v < 2; ++v) {
                         oz_slices(elem<double>(src, rows, cols, trans, kk[v], n0), e, lo);
                         oz_slices(elem<double>(src, rows, cols, trans, kk[v] + 1, n0), e, hi);
-                        for (int p = 0; p < kOzSlices; ++p) {
-                            const uint32_t word = lo[p] | (hi[p] << 16);
-                            if (!half) w[128 * (p >> 1) + 2 * ((p & 1) ^ hs) + v] = word;
-                            else if (p < 4) w[p ^ ws] = word;
-                            else w[128 + (p - 4)] = word;
-                        }
-                    }
-                    if (half) {
-                        w[128 + 2] = 0u;
-                        w[128 + 3] = 0u;
+                        for (int p = 0; p < kOzSlices; ++p)
+                            w[128 * (p >> 1) + 2 * ((p & 1) ^ ((lane >> 3) & 1)) + v] = lo[p] | (hi[p] << 16);
                     }
                 }
-            }
         }
     }
 }
