@@ -20,7 +20,7 @@
  *   - a block product is performed only if the product of the two block
  *     norms exceeds the filter threshold (on-the-fly filtering, §2).
  *
- * Readings where the paper is silent (listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - block norm = Frobenius norm, accumulated as an fma chain x*x + n over
  *     the block's elements in row-major order starting from +0.0, then an
  *     IEEE square root; FP32 data is widened to FP64 first;
