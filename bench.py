@@ -433,7 +433,7 @@ def main():
     traffic = traffic_from_profile()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_numeric_cc<double> (FP64 FMA)", "launch_ms": num_ms,
+                "kernel": "k_numeric_cc<double, wide build> (FP64 FMA)", "launch_ms": num_ms,
                 "peak_basis": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2070 MHz"}
     C64 = Cm.data_tensor()
 
