@@ -42,6 +42,28 @@ def test_graph_replay_equals_eager_and_oracle(mods, oracle, prec):
         assert rel_fro(eager, ref.data) <= 1e-12
 
 
+def test_ozaki_chain_graph_replay(mods, oracle):
+    """The chain on mixed 5 / 13 blocks (tensor-core items on the Ozaki path:
+    line exponents, slices and the numeric kernel all inside the graph):
+    replay equals the eager pass bit for bit, and both follow the oracle."""
+    bsm, chain, torch = mods
+    w = I.purification_start(nb=120, occ=0.05, sizes=(5, 13), probs=(0.6, 0.4))
+    X0 = bsm.Matrix.from_host(w["X0"])
+    g = chain.McWeenyGraph(X0, 4, w["eps"], prec="ozaki")
+    eager = g.result.data_host().copy()
+    for h in g.X[1:] + g.X2 + g.X3:
+        h.set_data(np.zeros(h.info().data_len))
+    g.replay()
+    torch.cuda.synchronize()
+    assert g.status() == 0
+    np.testing.assert_array_equal(g.result.data_host(), eager)
+    ref = oracle.mcweeny(w["X0"], 4, w["eps"])[-1]
+    pat = g.result.pattern()
+    np.testing.assert_array_equal(pat[0], ref.row_ptr)
+    np.testing.assert_array_equal(pat[1], ref.col_idx)
+    assert rel_fro(eager, ref.data) <= 1e-12
+
+
 def test_graph_replay_flags_changed_patterns(mods):
     """New X0 values that change the filtered patterns: the replay must not
     write past any handle's storage; the status words report it."""
