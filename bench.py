@@ -45,6 +45,44 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "numeric_fp64_mixed3000.md")
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU model (MEASURED_PEAKS.json), else 6678."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get("hbm_gbs")
+        return float(v) if v else 6678.0
+    except (OSError, ValueError, TypeError):
+        return 6678.0
+
+
+def phase_rates(phases, w, cnt, c_blocks, c_len):
+    """Algorithmic bytes and GB/s of the index phases (block norms, symbolic
+    fill, stacks) of one FP64 step, against the measured HBM bandwidth."""
+    A, B = w["A"], w["B"]
+    peak = hbm_peak_gbs()
+    cand = cnt.products + cnt.filtered
+    per = {
+        # every element of A and B read once, one FP64 norm written per block
+        "norms": (8.0 * (len(A.data) + len(B.data)) + 8.0 * (A.nnzb + B.nnzb),
+                  "8 B per element read + 8 B per block written"),
+        # per candidate product one B column index and one B norm (L2-resident re-reads)
+        "symbolic": (12.0 * cand, "12 B per candidate product (B index + norm)"),
+        # product list (3 x int32) and C pattern (col int32, blk_off int64, rc int32, segment int64)
+        "fill": (12.0 * cnt.products + 24.0 * c_blocks, "12 B per product + 24 B per C block written"),
+        # product ids read, (a_off, b_off, c_off) int64 triples written
+        "stacks": (36.0 * cnt.products, "12 B per product read + 24 B per triple written"),
+    }
+    out = {}
+    for k, (b, how) in per.items():
+        ms = phases.get(k)
+        if ms:
+            gbs = b / (ms * 1e-3) / 1e9
+            out[k] = {"ms": ms, "algorithmic_gb": b / 1e9, "gb_per_s": gbs, "frac_of_hbm": gbs / peak,
+                      "bytes": how}
+    out["hbm_peak_gbs"] = peak
+    return out
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -573,7 +611,8 @@ def main():
                                   "c_blocks": Cm.nnzb, "parallelism": "replicas" if world > 1 else "single GPU"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "split_precision": split, "split_autotune": tuned, "parity_sample": parity,
-                "phase_ms_last_fp64_step": phases}
+                "phase_ms_last_fp64_step": phases,
+                "index_phases": phase_rates(phases, w, cnt, Cm.nnzb, Cm.info().data_len)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
