@@ -82,7 +82,7 @@ typedef struct {
     int32_t flush_every;   /* split paths: how the FP32 partial sums of the block
                               products are combined.  F > 0: FP64 running sum
                               refreshed every F block products; F < 0:
-                              compensated FP32 pair (TwoSum) refreshed every -F
+                              compensated FP32 pair (Kahan) refreshed every -F
                               products, converted to FP64 at the end; 0: as -1.
                               Range [-1024, 1024].  BSM_P_OZAKI ignores it (its
                               flushes follow from the exact-sum bound).            */

@@ -391,20 +391,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
 
-// Compensated (error-free) addition of b into the pair (hi, lo): hi + lo
-// carries about 48 significant bits (Knuth's TwoSum on FP32 values).
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
-    const float s = __fadd_rn(hi, b);
-    const float bp = __fsub_rn(s, hi);
-    const float ap = __fsub_rn(s, bp);
-    const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(b, bp));
-    hi = s;
-    lo = __fadd_rn(lo, e);
+// Compensated (Kahan) addition of b into the pair (hi, lo), value hi + lo:
+// the low part lost by each addition is fed into the next one (4 FP32 adds;
+// error below about 2u of the sum of |b|, u = 2^-24).
+__device__ __forceinline__ void kahan_acc(float &hi, float &lo, float b) {
+    const float y = __fadd_rn(b, lo);
+    const float t = __fadd_rn(hi, y);
+    lo = __fsub_rn(y, __fsub_rn(t, hi));
+    hi = t;
 }
 
 // One pass over a super tile of MTC x NTC (at most 2 x 3) fragment tiles
 // starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
-// FF: cross-product sum as a float-float pair (TwoSum after every |F| block
+// FF: cross-product sum as a compensated float pair (Kahan after every |F| block
 // products); otherwise an FP64 sum refreshed every F products.
 template <int PREC, int MTC, int NTC, bool FF>
 __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
@@ -419,7 +418,7 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
     const uint32_t *XP = static_cast<const uint32_t *>(a.x_pack);
     const uint32_t *YP = static_cast<const uint32_t *>(a.y_pack);
     // FP64 mode: flush_every > 0 products per FP64 add; compensated mode:
-    // |flush_every| products per TwoSum (0 means 1)
+    // |flush_every| products per compensated addition (0 means 1)
     const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
     uint32_t *myring = ring + 4 * lane;  // chunk c of stage st at myring + st * 32 * SW + 128 * c
     const uint32_t ring_s = smem_addr(myring);
@@ -548,7 +547,7 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                         for (int j = 0; j < NTC; ++j)
 #pragma unroll
                             for (int v = 0; v < 4; ++v) {
-                                if constexpr (FF) two_sum_acc(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
+                                if constexpr (FF) kahan_acc(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
                                 else s64[i][j][v] += (double)acc[i][j][v];
                                 acc[i][j][v] = 0.f;
                             }
@@ -681,7 +680,7 @@ __device__ __forceinline__ void cs_lane_item(const NumericArgs &a, int64_t q) {
             since = 0;
 #pragma unroll
             for (int e = 0; e < L; ++e) {
-                if constexpr (FF) two_sum_acc(shi[e], slo[e], acc[e]);
+                if constexpr (FF) kahan_acc(shi[e], slo[e], acc[e]);
                 else s64[e] += (double)acc[e];
                 acc[e] = 0.f;
             }
@@ -771,7 +770,7 @@ __device__ __forceinline__ void cs_lane_fixed(const NumericArgs &a, int64_t q) {
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int c = 0; c < S; ++c) {
-                    if constexpr (FF) two_sum_acc(shi[r][c], slo[r][c], acc[r][c]);
+                    if constexpr (FF) kahan_acc(shi[r][c], slo[r][c], acc[r][c]);
                     else s64[r][c] += (double)acc[r][c];
                     acc[r][c] = 0.f;
                 }
