@@ -264,6 +264,39 @@ def test_deterministic(bsm):
         np.testing.assert_array_equal(x, y)
 
 
+def _split_bound_coeff(prec, kmax):
+    """Worst-case error of one output element of a split path, as a multiple
+    of sum_k |a_ik||b_kj|: the cut of every operand into np pieces of p
+    significant bits (round to nearest, so x - sum(pieces) <= 2^-(np p) |x|)
+    plus the piece products left out; the FP32 sums inside the tensor core
+    (at most npp * kmax terms per block product, each addition off by at most
+    2^-23 of the running magnitude: round toward zero); the compensated sum
+    across block products (about 2u, u = 2^-24)."""
+    if prec == "tf32x3":   # 2 pieces of 11 bits, 3 products (lo*lo left out)
+        trunc, npp = 3 * 2.0 ** -22, 3
+    elif prec == "bf16x3":  # 2 pieces of 8 bits, 3 products
+        trunc, npp = 3 * 2.0 ** -16, 3
+    else:                   # bf16x6: 3 pieces of 8 bits, 6 products
+        trunc, npp = 5 * 2.0 ** -24, 6
+    return 1.1 * (trunc + npp * kmax * 2.0 ** -23 + 2.0 ** -22)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x6", "bf16x3"])
+def test_split_elementwise_analytic_bound(bsm, oracle, prec):
+    """Every element of a split-precision product within the analytic bound
+    of its method, on blocks of 5..40 (several fragment tiles and k-steps)."""
+    from tests.helpers import to_dense
+    bs = I.mixed_sizes(30, (5, 13, 23, 40), (0.3, 0.3, 0.2, 0.2), seed=27)
+    A, B = random_bcsr(bs, bs, 0.3, seed=101), random_bcsr(bs, bs, 0.3, seed=102)
+    Cg, ref, _, _ = _run(bsm, oracle, A, B, 0.0, prec=prec)
+    _check_pattern(Cg, ref.C)
+    Ch = I.BCSR(ref.C.row_bs, ref.C.col_bs, ref.C.row_ptr, ref.C.col_idx, ref.C.blk_off, Cg.data_host())
+    err = np.abs(to_dense(Ch) - to_dense(ref.C))
+    absprod = np.abs(to_dense(A)) @ np.abs(to_dense(B))
+    bound = _split_bound_coeff(prec, int(bs.max())) * absprod
+    assert np.all(err <= bound), float(np.max(err / np.where(bound > 0, bound, 1.0)))
+
+
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_all_tiny_blocks(bsm, oracle, dt):
     """Blocks of 1, 2 and 4 rows/columns only (every output block at most 16
