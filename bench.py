@@ -93,7 +93,7 @@ def parse_args():
     p.add_argument("--legs", default="", help="comma list of split-precision legs to run (default: all)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the oracle sample")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the oracle sample")
     p.add_argument("--nb", type=int, default=WORKLOAD["nb"],
                    help="block rows/cols (smaller cases for profiling; the metric is quoted at 3000)")
     p.add_argument("--workload", default="mixed3000",
