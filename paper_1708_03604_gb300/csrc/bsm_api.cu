@@ -1064,21 +1064,39 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         if (nsh > (1 << 24)) return set_error(BSM_ERR_UNSUPPORTED, "too many distinct block sizes for stacks");
         std::vector<int32_t> sidx(kMaxBlockDim + 1, 0);
         for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
-        int32_t *d_sidx, *iota, *order, *vals_alt;
-        uint32_t *keys, *keys_sorted, *keys_alt;
-        int64_t *rtmp, *counts;
-        if ((st = sc.get(&d_sidx, kMaxBlockDim + 1)) || (st = sc.get(&iota, nprod)) || (st = sc.get(&order, nprod)) ||
-            (st = sc.get(&vals_alt, nprod)) || (st = sc.get(&keys, nprod)) || (st = sc.get(&keys_sorted, nprod)) ||
-            (st = sc.get(&keys_alt, nprod)) || (st = sc.get(&rtmp, radix_tmp_elems(nprod))) ||
-            (st = sc.get(&counts, nsh)))
-            return st;
-        int bits = 1;
-        while ((1ll << bits) < nsh) ++bits;
+        int32_t *d_sidx;
+        int64_t *counts;
+        if ((st = sc.get(&d_sidx, kMaxBlockDim + 1)) || (st = sc.get(&counts, nsh))) return st;
+        if ((st = dalloc_t(&triples, (size_t)nprod * 3))) return st;
+        sc.ptrs.push_back(triples);
         e = cudaMemcpyAsync(d_sidx, sidx.data(), sizeof(int32_t) * sidx.size(), cudaMemcpyHostToDevice, g_stream);
-        if (e == cudaSuccess) e = launch_product_shape_ids(nprod, pa, pb, A->blk_rc, B->blk_rc, d_sidx, ns, keys, iota, g_stream);
-        if (e == cudaSuccess)
-            e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, nprod, bits, rtmp, g_stream);
-        if (e == cudaSuccess) e = launch_histogram_u32(nprod, keys, nsh, counts, g_stream);
+        if (nsh <= stack_max_bins()) {
+            // few shapes: per-tile histogram, then every triple written to its place
+            int64_t *stmp;
+            if ((st = sc.get(&stmp, stack_tmp_elems(nprod, (int32_t)nsh)))) return st;
+            if (e == cudaSuccess)
+                e = launch_stacks_direct(nprod, pa, pb, pc, A->blk_rc, B->blk_rc, d_sidx, ns, (int32_t)nsh,
+                                         A->blk_off, B->blk_off, c_off, triples, counts, stmp, g_stream);
+        } else {
+            // many shapes: stable radix sort of the shape ids, then the triples
+            int32_t *iota, *order, *vals_alt;
+            uint32_t *keys, *keys_sorted, *keys_alt;
+            int64_t *rtmp;
+            if ((st = sc.get(&iota, nprod)) || (st = sc.get(&order, nprod)) || (st = sc.get(&vals_alt, nprod)) ||
+                (st = sc.get(&keys, nprod)) || (st = sc.get(&keys_sorted, nprod)) || (st = sc.get(&keys_alt, nprod)) ||
+                (st = sc.get(&rtmp, radix_tmp_elems(nprod))))
+                return st;
+            int bits = 1;
+            while ((1ll << bits) < nsh) ++bits;
+            if (e == cudaSuccess)
+                e = launch_product_shape_ids(nprod, pa, pb, A->blk_rc, B->blk_rc, d_sidx, ns, keys, iota, g_stream);
+            if (e == cudaSuccess)
+                e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, nprod, bits, rtmp,
+                                            g_stream);
+            if (e == cudaSuccess) e = launch_histogram_u32(nprod, keys, nsh, counts, g_stream);
+            if (e == cudaSuccess)
+                e = launch_stack_triples(nprod, order, pa, pb, pc, A->blk_off, B->blk_off, c_off, triples, g_stream);
+        }
         std::vector<int64_t> h_counts((size_t)nsh);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h_counts.data(), counts, sizeof(int64_t) * nsh, cudaMemcpyDeviceToHost, g_stream);
@@ -1096,13 +1114,9 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         nshapes = (int32_t)(h_ptr.size() - 1);
         if ((st = dalloc_t(&stack_ptr, h_ptr.size()))) return st;
         sc.ptrs.push_back(stack_ptr);
-        if ((st = dalloc_t(&triples, (size_t)nprod * 3))) return st;
-        sc.ptrs.push_back(triples);
         e = cudaMemcpyAsync(stack_ptr, h_ptr.data(), sizeof(int64_t) * h_ptr.size(), cudaMemcpyHostToDevice, g_stream);
-        if (e == cudaSuccess)
-            e = launch_stack_triples(nprod, order, pa, pb, pc, A->blk_off, B->blk_off, c_off, triples, g_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);  // h_ptr is pageable
-        if ((st = cuda_check(e, "stack triples"))) return st;
+        if ((st = cuda_check(e, "stack pointers"))) return st;
     }
     ev.mark(4);
 

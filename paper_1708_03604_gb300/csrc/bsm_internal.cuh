@@ -197,6 +197,15 @@ cudaError_t launch_product_shape_ids(int64_t nprod, const int32_t *pa, const int
                                      const int32_t *a_blk_rc, const int32_t *b_blk_rc,
                                      const int32_t *size_index /*[kMaxBlockDim+1]*/, int32_t ns,
                                      uint32_t *keys, int32_t *iota, cudaStream_t s);
+// Stacks in two passes (per-tile shape histogram, then every triple written
+// to its place) for at most stack_max_bins() shapes; counts[nbins] = products
+// per shape.  `tmp` needs stack_tmp_elems(nprod, nbins) int64.
+int stack_max_bins();
+size_t stack_tmp_elems(int64_t nprod, int32_t nbins);
+cudaError_t launch_stacks_direct(int64_t nprod, const int32_t *pa, const int32_t *pb, const int32_t *pc,
+                                 const int32_t *a_rc, const int32_t *b_rc, const int32_t *size_index, int32_t ns,
+                                 int32_t nbins, const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
+                                 int64_t *triples, int64_t *counts, int64_t *tmp, cudaStream_t s);
 cudaError_t launch_stack_triples(int64_t nprod, const int32_t *order, const int32_t *pa,
                                  const int32_t *pb, const int32_t *pc, const int64_t *a_off,
                                  const int64_t *b_off, const int64_t *c_off, int64_t *triples,

@@ -564,6 +564,80 @@ __global__ void k_product_shape_ids(int64_t nprod, const int32_t *pa, const int3
     }
 }
 
+// Stacks in two passes when there are at most kStackBins shapes: per tile of
+// kRadixTile products a shared-memory histogram of the shape ids (pass 1),
+// then each product's triple is written straight to its place -- the shape's
+// start, plus the earlier tiles' products of that shape, plus its rank inside
+// the tile (warp by warp, lane by lane) -- so every stack keeps the canonical
+// (i, j, k) order, as the stable sort did (pass 2).
+constexpr int kStackBins = 256;
+__device__ __forceinline__ uint32_t product_shape(int64_t p, const int32_t *pa, const int32_t *pb,
+                                                  const int32_t *a_rc, const int32_t *b_rc,
+                                                  const int32_t *size_index, int32_t ns) {
+    const int32_t ra = a_rc[pa[p]], rb = b_rc[pb[p]];
+    return (uint32_t)((size_index[rc_rows(ra)] * ns + size_index[rc_cols(rb)]) * ns + size_index[rc_cols(ra)]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_stack_count(int64_t nprod, const int32_t *pa, const int32_t *pb,
+                                                          const int32_t *a_rc, const int32_t *b_rc,
+                                                          const int32_t *size_index, int32_t ns, int32_t nbins,
+                                                          int64_t ntiles, int64_t *tile_hist,
+                                                          unsigned long long *counts) {
+    __shared__ int32_t h[kStackBins];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int q = 0; q < kRadixRounds; ++q) {
+        const int64_t p = base + (int64_t)q * kThreads + threadIdx.x;
+        if (p < nprod) atomicAdd(&h[product_shape(p, pa, pb, a_rc, b_rc, size_index, ns)], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        tile_hist[(int64_t)b * ntiles + blockIdx.x] = h[b];
+        if (h[b]) atomicAdd(&counts[b], (unsigned long long)h[b]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_stack_scatter(int64_t nprod, const int32_t *pa, const int32_t *pb,
+                                                            const int32_t *pc, const int32_t *a_rc,
+                                                            const int32_t *b_rc, const int32_t *size_index,
+                                                            int32_t ns, int32_t nbins, int64_t ntiles,
+                                                            const int64_t *offs, const int64_t *a_off,
+                                                            const int64_t *b_off, const int64_t *c_off,
+                                                            int64_t *triples) {
+    __shared__ int64_t run[kStackBins];
+    __shared__ int32_t wcnt[kThreads / 32][kStackBins];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int b = tid; b < nbins; b += blockDim.x) run[b] = offs[(int64_t)b * ntiles + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int q = 0; q < kRadixRounds; ++q) {
+        for (int w = 0; w < kThreads / 32; ++w)
+            for (int b = tid; b < nbins; b += blockDim.x) wcnt[w][b] = 0;
+        __syncthreads();
+        const int64_t p = base + (int64_t)q * kThreads + tid;
+        const bool valid = p < nprod;
+        const int d = valid ? (int)product_shape(p, pa, pb, a_rc, b_rc, size_index, ns) : kStackBins;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            int64_t pos = run[d] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            triples[3 * pos + 0] = a_off[pa[p]];
+            triples[3 * pos + 1] = b_off[pb[p]];
+            triples[3 * pos + 2] = c_off[pc[p]];
+        }
+        __syncthreads();
+        for (int b = tid; b < nbins; b += blockDim.x) {
+            int32_t add = 0;
+            for (int w = 0; w < kThreads / 32; ++w) add += wcnt[w][b];
+            run[b] += add;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_stack_triples(int64_t nprod, const int32_t *order, const int32_t *pa,
                                 const int32_t *pb, const int32_t *pc, const int64_t *a_off,
                                 const int64_t *b_off, const int64_t *c_off, int64_t *triples) {
@@ -787,6 +861,34 @@ cudaError_t launch_product_shape_ids(int64_t nprod, const int32_t *pa, const int
     k_product_shape_ids<<<grid_for(nprod), kThreads, 0, s>>>(nprod, pa, pb, a_blk_rc, b_blk_rc,
                                                              size_index, ns, keys, iota);
     count_launch(1);
+    return cudaGetLastError();
+}
+
+int stack_max_bins() { return kStackBins; }
+
+size_t stack_tmp_elems(int64_t nprod, int32_t nbins) {
+    const int64_t nt = (nprod + kRadixTile - 1) / kRadixTile;
+    const int64_t h = (int64_t)nbins * (nt > 0 ? nt : 1);
+    return (size_t)(2 * h + 1 + scan_tmp_elems(h));
+}
+
+cudaError_t launch_stacks_direct(int64_t nprod, const int32_t *pa, const int32_t *pb, const int32_t *pc,
+                                 const int32_t *a_rc, const int32_t *b_rc, const int32_t *size_index, int32_t ns,
+                                 int32_t nbins, const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
+                                 int64_t *triples, int64_t *counts, int64_t *tmp, cudaStream_t s) {
+    if (nprod == 0 || nbins > kStackBins) return nprod == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    const int64_t nt = (nprod + kRadixTile - 1) / kRadixTile;
+    const int64_t h = (int64_t)nbins * nt;
+    int64_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h + 1;  // offs holds h+1 entries
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * nbins, s);
+    if (e != cudaSuccess) return e;
+    k_stack_count<<<(unsigned)nt, kThreads, 0, s>>>(nprod, pa, pb, a_rc, b_rc, size_index, ns, nbins, nt, hist,
+                                                    reinterpret_cast<unsigned long long *>(counts));
+    e = launch_scan_i64(hist, offs, h, stmp, s);
+    if (e != cudaSuccess) return e;
+    k_stack_scatter<<<(unsigned)nt, kThreads, 0, s>>>(nprod, pa, pb, pc, a_rc, b_rc, size_index, ns, nbins, nt,
+                                                      offs, a_off, b_off, c_off, triples);
+    count_launch(2);
     return cudaGetLastError();
 }
 
