@@ -202,6 +202,30 @@ def test_ragged_sizes_and_large_blocks(bsm, oracle):
         Cg, ref, _, _ = _run(bsm, oracle, A, B, 0.0, prec=prec)
         _check_pattern(Cg, ref.C)
         assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
+    # about 40 distinct sizes: far more shapes than the two-pass stack builder
+    # takes, so the stacks come from the radix-sort path
+    shapes, ptr, trip = Cg.stacks()
+    s_ref, p_ref, t_ref = oracle.stacks(A, B, ref.C, ref.prods)
+    assert len(s_ref) > 256
+    np.testing.assert_array_equal(shapes, s_ref)
+    np.testing.assert_array_equal(ptr, p_ref)
+    np.testing.assert_array_equal(trip, t_ref)
+
+
+@pytest.mark.parametrize("nsizes", [6, 7])
+def test_stacks_at_the_bin_limit(bsm, oracle, nsizes):
+    """6 distinct sizes give 216 shape bins (two-pass builder), 7 give 343
+    (radix-sort path): both bit-exact against the oracle's stable bucketing."""
+    sizes = (1, 2, 3, 5, 7, 9, 11)[:nsizes]
+    bs = I.mixed_sizes(60, sizes, (1.0 / nsizes,) * nsizes, seed=33)
+    A, B = random_bcsr(bs, bs, 0.2, seed=111), random_bcsr(bs, bs, 0.2, seed=112)
+    Cg, ref, _, _ = _run(bsm, oracle, A, B, 0.0)
+    _check_pattern(Cg, ref.C)
+    shapes, ptr, trip = Cg.stacks()
+    s_ref, p_ref, t_ref = oracle.stacks(A, B, ref.C, ref.prods)
+    np.testing.assert_array_equal(shapes, s_ref)
+    np.testing.assert_array_equal(ptr, p_ref)
+    np.testing.assert_array_equal(trip, t_ref)
 
 
 def test_alpha_beta_merge(bsm, oracle):
