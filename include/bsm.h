@@ -61,7 +61,7 @@ typedef enum {
     BSM_P_TF32x3 = 2,     /* hi/lo TF32 split, 3 tensor-core products, FP32 accumulate, FP64 sum */
     BSM_P_BF16x3 = 3,     /* hi/lo BF16 split, 3 products                    */
     BSM_P_BF16x6 = 4,     /* hi/mid/lo BF16 split, 6 products                */
-    BSM_P_OZAKI = 5       /* error-free slicing after Ozaki et al. (2012): every
+    BSM_P_OZAKI = 5,      /* error-free slicing after Ozaki et al. (2012): every
                              row of the left operand and every column of the
                              right one is put on its own power-of-two fixed-point
                              grid and cut into 6 BF16 slices of at most 9 bits;
@@ -73,6 +73,19 @@ typedef enum {
                              row's and the column's largest |x|; FP64 data only
                              (BSM_ERR_UNSUPPORTED for FP32).  Non-finite inputs
                              give non-finite outputs in their rows / columns.  */
+    BSM_P_TF32x3_PANEL = 6 /* TF32x3 (the split and piece products of
+                             BSM_P_TF32x3) on the fifth-generation tensor cores
+                             (tcgen05, accumulators in tensor memory), over dense
+                             tiles of 5 x 5 output blocks: every k-step of a tile
+                             is one 128 x 128 x 24 product; two k-steps are
+                             summed in FP32 (at most 3 x 48 terms), and those
+                             sums added into a compensated FP32 pair per element.
+                             Runs when the data is FP64, every block of A, B and
+                             C has one size s <= 24 and the norm filter removed
+                             no product; otherwise the multiply runs the
+                             BSM_P_TF32x3 kernel (bsm_get_engine tells which).
+                             The adjoint runs BSM_P_TF32x3.  Not with no_sync
+                             (BSM_ERR_UNSUPPORTED).                             */
 } bsm_prec;
 
 typedef struct {
@@ -262,6 +275,16 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
 /* Counts of the last multiply into C: kept products, filtered candidate
  * products and useful FLOPs (sum of 2*m*n*k over kept products). */
 bsm_status bsm_get_counts(bsm_t C, int64_t *products, int64_t *filtered, double *useful_flop);
+
+/* Numeric engine of the last multiply into C. */
+typedef enum {
+    BSM_E_NONE = -1,        /* no multiply (or no output block)                 */
+    BSM_E_FP64_CORES = 0,   /* FP64 (or FP32) FMA on the CUDA cores             */
+    BSM_E_SPLIT_MMA = 1,    /* split precision on mma.sync tensor-core tiles    */
+    BSM_E_OZAKI_MMA = 2,    /* Ozaki slices on mma.sync tensor-core tiles       */
+    BSM_E_PANEL_TCGEN05 = 3 /* BSM_P_TF32x3_PANEL: tcgen05 row-panel tiles      */
+} bsm_engine;
+bsm_status bsm_get_engine(bsm_t C, int32_t *engine);
 
 /* Per-phase timings of the last multiply into C (BSM_T_COUNT doubles, ms),
  * valid when profiling was on.  Synchronises the stream. */

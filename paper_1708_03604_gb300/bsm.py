@@ -24,9 +24,12 @@ BSM_OK, BSM_ERR_ARG, BSM_ERR_BLOCKING, BSM_ERR_CAPACITY, BSM_ERR_ALLOC, BSM_ERR_
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_BLOCKING", "ERR_CAPACITY", "ERR_ALLOC", "ERR_CUDA", "ERR_TIMEOUT",
                 "ERR_UNSUPPORTED"]
 BSM_FP64, BSM_FP32 = 0, 1
-BSM_P_FP64, BSM_P_FP64_DMMA, BSM_P_TF32x3, BSM_P_BF16x3, BSM_P_BF16x6, BSM_P_OZAKI = range(6)
+BSM_P_FP64, BSM_P_FP64_DMMA, BSM_P_TF32x3, BSM_P_BF16x3, BSM_P_BF16x6, BSM_P_OZAKI, BSM_P_TF32x3_PANEL = range(7)
 PREC = {"fp64": BSM_P_FP64, "fp64_dmma": BSM_P_FP64_DMMA, "tf32x3": BSM_P_TF32x3, "bf16x3": BSM_P_BF16x3,
-        "bf16x6": BSM_P_BF16x6, "ozaki": BSM_P_OZAKI}
+        "bf16x6": BSM_P_BF16x6, "ozaki": BSM_P_OZAKI, "tf32x3_panel": BSM_P_TF32x3_PANEL}
+# bsm_engine
+BSM_E_NONE, BSM_E_FP64_CORES, BSM_E_SPLIT_MMA, BSM_E_OZAKI_MMA, BSM_E_PANEL_TCGEN05 = -1, 0, 1, 2, 3
+ENGINE_NAMES = {-1: "none", 0: "fp64_cores", 1: "split_mma", 2: "ozaki_mma", 3: "panel_tcgen05"}
 BSM_DATA_COPY, BSM_DATA_BORROW = 0, 1
 TIMING_PHASES = ["norms", "symbolic", "fill", "stacks", "numeric", "post", "total"]
 
@@ -35,7 +38,7 @@ EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_lau
            "bsm_copy_data", "bsm_set_data", "bsm_data_ptr", "bsm_block_norms", "bsm_multiply",
            "bsm_multiply_backward", "bsm_get_counts", "bsm_get_timings", "bsm_get_products",
            "bsm_get_stacks", "bsm_add", "bsm_count_products_static", "bsm_borrow_data", "bsm_add_backward",
-           "bsm_get_status", "bsm_set_variant", "bsm_get_variant"]
+           "bsm_get_status", "bsm_set_variant", "bsm_get_variant", "bsm_get_engine"]
 
 
 class BsmError(RuntimeError):
@@ -87,6 +90,7 @@ def lib() -> C.CDLL:
         "bsm_get_stacks": ([_vp, _P(_i32), _P(_i64), _vp, _vp, _vp], _i32),
         "bsm_add": ([_f64, _vp, _f64, _vp, _vp, _f64, _P(Opts)], _i32),
         "bsm_get_status": ([_vp, _P(_i32)], _i32),
+        "bsm_get_engine": ([_vp, _P(_i32)], _i32),
         "bsm_set_variant": ([_i32, _i32, _i32, _i32], _i32),
         "bsm_get_variant": ([_i32, _i32, _i32, _P(_i32)], _i32),
         "bsm_count_products_static": ([_vp, _vp, _f64, _vp, _vp, _vp], _i32),
@@ -212,6 +216,13 @@ def bsm_get_status(X: int) -> int:
     if st not in (BSM_OK, BSM_ERR_CAPACITY):
         _check(st)
     return s.value
+
+
+def bsm_get_engine(Cm: int) -> str:
+    """Numeric engine of the last multiply into Cm (ENGINE_NAMES)."""
+    v = _i32()
+    _check(lib().bsm_get_engine(Cm, C.byref(v)))
+    return ENGINE_NAMES.get(v.value, str(v.value))
 
 
 def bsm_get_counts(Cm: int):
@@ -349,6 +360,9 @@ class Matrix:
 
     def timings(self) -> dict:
         return bsm_get_timings(self.h)
+
+    def engine(self) -> str:
+        return bsm_get_engine(self.h)
 
     def products(self):
         n = _i64()

@@ -148,6 +148,10 @@ void free_pattern(bsm_mat *X) {
     dfree(X->item_order); X->item_order = nullptr;
     dfree(X->n_marked); X->n_marked = nullptr;
     dfree(X->row_rank); X->row_rank = nullptr;
+    dfree(X->panel_ord_r); X->panel_ord_r = nullptr;
+    dfree(X->panel_ord_c); X->panel_ord_c = nullptr;
+    dfree(X->panel_pos_c); X->panel_pos_c = nullptr;
+    X->panel_B = nullptr;
     dfree(X->t_ptr); X->t_ptr = nullptr;
     dfree(X->t_row); X->t_row = nullptr;
     dfree(X->t_blk); X->t_blk = nullptr;
@@ -159,7 +163,7 @@ bsm_status check_opts(const bsm_opts *o, bsm_opts *out) {
     bsm_opts_default(out);
     if (!o) return BSM_OK;
     *out = *o;
-    if (o->prec < BSM_P_FP64 || o->prec > BSM_P_OZAKI) return set_error(BSM_ERR_ARG, "opts.prec out of range");
+    if (o->prec < BSM_P_FP64 || o->prec > BSM_P_TF32x3_PANEL) return set_error(BSM_ERR_ARG, "opts.prec out of range");
     if (o->flush_every < -1024 || o->flush_every > 1024) return set_error(BSM_ERR_ARG, "opts.flush_every outside [-1024, 1024]");
     if (o->no_sync != 0 && o->no_sync != 1) return set_error(BSM_ERR_ARG, "opts.no_sync must be 0 or 1");
     for (int q = 0; q < 3; ++q)
@@ -262,27 +266,36 @@ bsm_status pack_fill(Scratch &sc, const bsm_mat *M, int role_y, int trans, int p
 // kernels' schedule uses it, so that warps running at the same time read the
 // same operand blocks from L2.  Built on the host from X's pattern and kept
 // on the handle.
-bsm_status ensure_row_rank(bsm_mat *X) {
-    if (X->row_rank || X->nbr == 0) return BSM_OK;
+// X's pattern on the host: rows (rp, ci) and columns (cp, cr)
+struct HostPattern {
+    std::vector<int64_t> rp, cp;
+    std::vector<int32_t> ci, cr;
+};
+bsm_status host_pattern(const bsm_mat *X, HostPattern &h) {
     const int32_t nbr = X->nbr, nbc = X->nbc;
-    std::vector<int64_t> rp((size_t)nbr + 1);
-    std::vector<int32_t> ci((size_t)X->nnzb);
-    cudaError_t e = cudaMemcpyAsync(rp.data(), X->row_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyDeviceToHost, g_stream);
+    h.rp.assign((size_t)nbr + 1, 0);
+    h.ci.assign((size_t)X->nnzb, 0);
+    cudaError_t e = cudaMemcpyAsync(h.rp.data(), X->row_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyDeviceToHost,
+                                    g_stream);
     if (e == cudaSuccess && X->nnzb)
-        e = cudaMemcpyAsync(ci.data(), X->col_idx, sizeof(int32_t) * X->nnzb, cudaMemcpyDeviceToHost, g_stream);
+        e = cudaMemcpyAsync(h.ci.data(), X->col_idx, sizeof(int32_t) * X->nnzb, cudaMemcpyDeviceToHost, g_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
     bsm_status st;
     if ((st = cuda_check(e, "read pattern"))) return st;
-    // column -> rows
-    std::vector<int64_t> cp((size_t)nbc + 1, 0);
-    for (int32_t c : ci) cp[(size_t)c + 1]++;
-    for (int32_t c = 0; c < nbc; ++c) cp[c + 1] += cp[c];
-    std::vector<int32_t> cr((size_t)X->nnzb);
-    {
-        std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
-        for (int32_t r = 0; r < nbr; ++r)
-            for (int64_t b = rp[r]; b < rp[r + 1]; ++b) cr[pos[ci[b]]++] = r;
-    }
+    h.cp.assign((size_t)nbc + 1, 0);
+    for (int32_t c : h.ci) h.cp[(size_t)c + 1]++;
+    for (int32_t c = 0; c < nbc; ++c) h.cp[c + 1] += h.cp[c];
+    h.cr.assign((size_t)X->nnzb, 0);
+    std::vector<int64_t> pos(h.cp.begin(), h.cp.end() - 1);
+    for (int32_t r = 0; r < nbr; ++r)
+        for (int64_t b = h.rp[r]; b < h.rp[r + 1]; ++b) h.cr[pos[h.ci[b]]++] = r;
+    return BSM_OK;
+}
+
+// breadth-first rank of the rows of a pattern through shared columns
+std::vector<int32_t> bfs_row_rank(const HostPattern &h, int32_t nbr, int32_t nbc) {
+    const std::vector<int64_t> &rp = h.rp, &cp = h.cp;
+    const std::vector<int32_t> &ci = h.ci, &cr = h.cr;
     std::vector<int32_t> seed((size_t)nbr);
     for (int32_t r = 0; r < nbr; ++r) seed[r] = r;
     std::stable_sort(seed.begin(), seed.end(), [&](int32_t x, int32_t y) { return rp[x + 1] - rp[x] < rp[y + 1] - rp[y]; });
@@ -310,6 +323,17 @@ bsm_status ensure_row_rank(bsm_mat *X) {
             }
         }
     }
+    return rank;
+}
+
+bsm_status ensure_row_rank(bsm_mat *X) {
+    if (X->row_rank || X->nbr == 0) return BSM_OK;
+    const int32_t nbr = X->nbr;
+    HostPattern h;
+    bsm_status st;
+    if ((st = host_pattern(X, h))) return st;
+    std::vector<int32_t> rank = bfs_row_rank(h, nbr, X->nbc);
+    cudaError_t e;
     int32_t *d = nullptr;
     if ((st = dalloc_t(&d, nbr))) return st;
     e = cudaMemcpyAsync(d, rank.data(), sizeof(int32_t) * nbr, cudaMemcpyHostToDevice, g_stream);
@@ -443,6 +467,183 @@ bsm_status read_words(const int64_t *const *src, int n) {
         if (e != cudaSuccess) return cuda_check(e, "reading sizes");
     }
     return cuda_check(cudaStreamSynchronize(g_stream), "stream synchronize");
+}
+
+// ---------------------------------------------------------------------------
+// Row-panel engine (BSM_P_TF32x3_PANEL)
+
+// the blocking of A, B (and so of C) is one size s <= the panel slot
+bool panel_blocking(const bsm_mat *A, const bsm_mat *B, int32_t *s_out) {
+    if (A->nbr == 0 || A->nbc == 0 || B->nbc == 0) return false;
+    if (A->nnzb > INT32_MAX || B->nnzb > INT32_MAX) return false;
+    const int32_t s = A->h_row_bs[0];
+    if (s > panel_slot()) return false;
+    for (const auto *v : {&A->h_row_bs, &A->h_col_bs, &B->h_col_bs})
+        for (int32_t x : *v)
+            if (x != s) return false;
+    *s_out = s;
+    return true;
+}
+
+// Positions of A's block rows and B's block columns along the band of the
+// product: rows start at their breadth-first rank; a block index k of the
+// inner dimension sits at the mean position of A's rows that hold it; a row
+// is then placed at the mean position of its k, and a column of B at the
+// mean position of its k.  Rows (columns) sorted by position form the
+// groups of 5 of the tiles, so that a group's members share most of their k.
+bsm_status panel_orders(bsm_mat *A, bsm_mat *B) {
+    if (A->panel_ord_r && A->panel_B == B && A->panel_B_nnzb == B->nnzb && A->panel_B_nbc == B->nbc)
+        return BSM_OK;
+    dfree(A->panel_ord_r); A->panel_ord_r = nullptr;
+    dfree(A->panel_ord_c); A->panel_ord_c = nullptr;
+    dfree(A->panel_pos_c); A->panel_pos_c = nullptr;
+    const int32_t nbr = A->nbr, nbk = A->nbc, nbc = B->nbc;
+    HostPattern ha, hb;
+    bsm_status st;
+    if ((st = host_pattern(A, ha)) || (st = host_pattern(B, hb))) return st;
+    const std::vector<int32_t> rank = bfs_row_rank(ha, nbr, nbk);
+    std::vector<double> y((size_t)nbk, -1.0), x((size_t)nbr), z((size_t)nbc);
+    for (int32_t k = 0; k < nbk; ++k) {
+        const int64_t n = ha.cp[k + 1] - ha.cp[k];
+        if (!n) continue;
+        double acc = 0.0;
+        for (int64_t q = ha.cp[k]; q < ha.cp[k + 1]; ++q) acc += rank[ha.cr[q]];
+        y[k] = acc / (double)n;
+    }
+    for (int32_t i = 0; i < nbr; ++i) {
+        double acc = 0.0;
+        int64_t n = 0;
+        for (int64_t b = ha.rp[i]; b < ha.rp[i + 1]; ++b) {
+            acc += y[ha.ci[b]];
+            ++n;
+        }
+        x[i] = n ? acc / (double)n : (double)rank[i];
+    }
+    for (int32_t j = 0; j < nbc; ++j) {
+        double acc = 0.0;
+        int64_t n = 0;
+        for (int64_t q = hb.cp[j]; q < hb.cp[j + 1]; ++q) {
+            const double v = y[hb.cr[q]];
+            if (v < 0.0) continue;
+            acc += v;
+            ++n;
+        }
+        z[j] = n ? acc / (double)n : (double)nbr + j;
+    }
+    std::vector<int32_t> ord_r((size_t)nbr), ord_c((size_t)nbc), pos_c((size_t)nbc);
+    for (int32_t i = 0; i < nbr; ++i) ord_r[i] = i;
+    for (int32_t j = 0; j < nbc; ++j) ord_c[j] = j;
+    std::stable_sort(ord_r.begin(), ord_r.end(), [&](int32_t p, int32_t q) { return x[p] < x[q]; });
+    std::stable_sort(ord_c.begin(), ord_c.end(), [&](int32_t p, int32_t q) { return z[p] < z[q]; });
+    for (int32_t p = 0; p < nbc; ++p) pos_c[ord_c[p]] = p;
+    int32_t *dr = nullptr, *dc = nullptr, *dp = nullptr;
+    if ((st = dalloc_t(&dr, nbr)) || (st = dalloc_t(&dc, nbc)) || (st = dalloc_t(&dp, nbc))) {
+        dfree(dr);
+        dfree(dc);
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(dr, ord_r.data(), sizeof(int32_t) * nbr, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dc, ord_c.data(), sizeof(int32_t) * nbc, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, pos_c.data(), sizeof(int32_t) * nbc, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);  // the host vectors are pageable
+    if ((st = cuda_check(e, "upload panel orders"))) {
+        dfree(dr);
+        dfree(dc);
+        dfree(dp);
+        return st;
+    }
+    A->panel_ord_r = dr;
+    A->panel_ord_c = dc;
+    A->panel_pos_c = dp;
+    A->panel_B = B;
+    A->panel_B_nnzb = B->nnzb;
+    A->panel_B_nbc = nbc;
+    return BSM_OK;
+}
+
+// super tiles of the panel schedule (row groups x column groups)
+int g_panel_sg = 12, g_panel_sh = 12;
+
+struct PanelOut {
+    int64_t nnzbC;
+    const int64_t *c_row_ptr;
+    const int32_t *c_col;
+    const int64_t *c_off;
+    double *c_data;
+    const int64_t *old_off;  // null unless beta != 0
+    const void *old_data;
+    double alpha, beta;
+    int32_t *status;
+};
+
+bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const PanelOut &o, Events &ev) {
+    bsm_status st;
+    if ((st = panel_orders(A, B)) || (st = ensure_transpose(B))) return st;
+    const int32_t nbr = A->nbr, nbc = B->nbc;
+    const int32_t ngr = (nbr + panel_tile_rows() - 1) / panel_tile_rows();
+    const int32_t ngc = (nbc + panel_tile_cols() - 1) / panel_tile_cols();
+    int64_t *tile_cnt, *tile_ptr, *stmp;
+    if ((st = sc.get(&tile_cnt, ngr)) || (st = sc.get(&tile_ptr, (size_t)ngr + 1)) ||
+        (st = sc.get(&stmp, scan_tmp_elems(ngr))))
+        return st;
+    cudaError_t e = launch_panel_tiles_count(nbr, A->panel_ord_r, A->panel_pos_c, o.c_row_ptr, o.c_col, ngc, tile_cnt,
+                                             g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(tile_cnt, tile_ptr, ngr, stmp, g_stream);
+    if ((st = cuda_check(e, "panel tiles"))) return st;
+    const int64_t *src[1] = {tile_ptr + ngr};
+    if ((st = read_words(src, 1))) return st;
+    const int64_t ntiles = g_host[0];
+    if (ntiles == 0) return BSM_OK;
+    if (ntiles > INT32_MAX / 25) return set_error(BSM_ERR_UNSUPPORTED, "too many panel tiles");
+    const int nt = panel_tile_rows() * panel_tile_cols();
+    int32_t *tile_g, *tile_h, *cblk, *iota, *vals_alt, *order;
+    uint32_t *keys, *keys_alt, *keys_sorted;
+    int64_t *rtmp;
+    if ((st = sc.get(&tile_g, ntiles)) || (st = sc.get(&tile_h, ntiles)) || (st = sc.get(&cblk, (size_t)ntiles * nt)) ||
+        (st = sc.get(&iota, ntiles)) || (st = sc.get(&vals_alt, ntiles)) || (st = sc.get(&order, ntiles)) ||
+        (st = sc.get(&keys, ntiles)) || (st = sc.get(&keys_alt, ntiles)) || (st = sc.get(&keys_sorted, ntiles)) ||
+        (st = sc.get(&rtmp, radix_tmp_elems(ntiles))))
+        return st;
+    e = cudaMemsetAsync(cblk, 0xFF, sizeof(int32_t) * (size_t)ntiles * nt, g_stream);
+    if (e == cudaSuccess)
+        e = launch_panel_tiles_fill(nbr, A->panel_ord_r, A->panel_pos_c, o.c_row_ptr, o.c_col, ngc, tile_ptr, tile_g,
+                                    tile_h, cblk, g_stream);
+    const int sg = g_panel_sg, sh = g_panel_sh;
+    const int64_t nkeys = (int64_t)((ngr + sg - 1) / sg) * ((ngc + sh - 1) / sh);
+    int bits = 1;
+    while ((1ll << bits) < nkeys) ++bits;
+    if (e == cudaSuccess) e = launch_panel_tile_keys(ntiles, tile_g, tile_h, sg, sh, ngc, keys, iota, g_stream);
+    if (e == cudaSuccess)
+        e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, ntiles, bits, rtmp, g_stream);
+    if ((st = cuda_check(e, "panel tiles"))) return st;
+    // operand planes
+    uint8_t *apk, *bpk, *zeros;
+    unsigned long long *counter;
+    if ((st = sc.get(&apk, (size_t)panel_pack_bytes(A->nnzb))) || (st = sc.get(&bpk, (size_t)panel_pack_bytes(B->nnzb))) ||
+        (st = sc.get(&zeros, (size_t)panel_pack_bytes(1))) || (st = sc.get(&counter, 1)))
+        return st;
+    e = launch_panel_pack(A, 0, apk, g_stream);
+    if (e == cudaSuccess) e = launch_panel_pack(B, 1, bpk, g_stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, (size_t)panel_pack_bytes(1), g_stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), g_stream);
+    if ((st = cuda_check(e, "panel operands"))) return st;
+    PanelArgs pa{};
+    pa.nbr = nbr; pa.nbc = nbc; pa.s = s;
+    pa.n_tiles = ntiles;
+    pa.tile_order = order; pa.tile_g = tile_g; pa.tile_h = tile_h; pa.cblk = cblk;
+    pa.ord_r = A->panel_ord_r; pa.ord_c = A->panel_ord_c;
+    pa.a_row_ptr = A->row_ptr; pa.a_col_idx = A->col_idx;
+    pa.b_t_ptr = B->t_ptr; pa.b_t_row = B->t_row; pa.b_t_blk = B->t_blk;
+    pa.a_pack = apk; pa.b_pack = bpk; pa.zeros = zeros;
+    pa.c_data = o.c_data; pa.c_blk_off = o.c_off;
+    pa.alpha = o.alpha; pa.beta = o.beta;
+    pa.old_data = o.old_data; pa.old_off = o.old_off;
+    pa.status = o.status;
+    pa.work_counter = counter;
+    ev.mark(5);
+    if ((st = cuda_check(launch_panel_numeric(pa, g_stream), "panel numeric"))) return st;
+    ev.mark(6);
+    return BSM_OK;
 }
 
 }  // namespace
@@ -888,6 +1089,11 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (!std::isfinite(alpha) || !std::isfinite(beta) || std::isnan(filter_eps))
         return set_error(BSM_ERR_ARG, "alpha, beta and eps must be finite");
     const bool no_sync = opts.no_sync != 0;
+    // BSM_P_TF32x3_PANEL: the tcgen05 row-panel engine where it applies, else
+    // the mma.sync TF32x3 kernel (rprec: the precision of the mma.sync path)
+    const bool want_panel = opts.prec == BSM_P_TF32x3_PANEL;
+    if (want_panel && no_sync) return set_error(BSM_ERR_UNSUPPORTED, "BSM_P_TF32x3_PANEL does not run with no_sync");
+    const int rprec = want_panel ? BSM_P_TF32x3 : opts.prec;
     const auto &pl = C->plan;
     if (no_sync) {
         if (pl.kind != 1 || pl.A != A || pl.B != B || pl.A_nnzb != A->nnzb || pl.B_nnzb != B->nnzb ||
@@ -901,7 +1107,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     }
     // kernel precision: the Ozaki path whose output blocks all run one per lane
     // (plain FP64 FMA) needs no slices at all
-    int kprec = opts.prec;
+    int kprec = rprec;
     if (opts.prec == BSM_P_OZAKI) {
         if (no_sync) kprec = pl.kprec;
         else if (all_lane(opts.prec, A->h_row_bs, B->h_col_bs)) kprec = BSM_P_FP64;
@@ -1016,6 +1222,9 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         if (symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 220 * 1024)
             return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
     }
+    int32_t panel_s = 0;
+    const bool use_panel = want_panel && A->dtype == BSM_FP64 && nfilt == 0 && panel_blocking(A, B, &panel_s) &&
+                           panel_tile_smem((B->nbc + panel_tile_cols() - 1) / panel_tile_cols()) <= 200 * 1024;
     ev.mark(2);
 
     // ---- a3: fill C's pattern and the product list
@@ -1122,6 +1331,19 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
 
     // ---- a5/a6: numeric
     OzLines olA, olB;
+    int32_t *order = nullptr;
+    int64_t *n_marked = nullptr;
+    bool uses_cores = false;
+    if (use_panel) {
+        PanelOut po{nnzbC, crow_ptr, c_col, c_off, static_cast<double *>(c_data), old_off,
+                    use_old ? C->data : nullptr, alpha, use_old ? beta : 0.0, C->status};
+        if ((st = run_panel(sc, A, B, panel_s, po, ev))) return st;
+        int32_t hs = 0;
+        e = cudaMemcpyAsync(&hs, C->status, sizeof(int32_t), cudaMemcpyDeviceToHost, g_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+        if ((st = cuda_check(e, "panel status"))) return st;
+        if (hs != 0) return set_error(BSM_ERR_TIMEOUT, "a wait of the row-panel kernel gave up");
+    } else {
     if (tc) {
         if ((st = sc.get(&pkA.words, (size_t)packA_words + 16)) || (st = sc.get(&pkB.words, (size_t)packB_words + 16)))
             return st;
@@ -1158,9 +1380,6 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     na.y_exp = olB.exps; na.y_line0 = olB.line0;
     na.status = no_sync ? C->status : nullptr;
     if ((st = sc.get(&na.work_counter, 2))) return st;
-    int32_t *order = nullptr;
-    int64_t *n_marked = nullptr;
-    bool uses_cores = false;
     if (no_sync) {
         order = C->item_order;
         n_marked = C->n_marked;
@@ -1171,18 +1390,18 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         rows_view.nbr = nbr;
         rows_view.row_ptr = crow_ptr;
         if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
-                              opts.prec, &uses_cores, &n_marked)))
+                              rprec, &uses_cores, &n_marked)))
             return st;
     }
     na.n_lane_items = n_marked;
     if (needs_plain(kprec) && uses_cores) {  // unpacked pieces for the CUDA-core split variant
-        const int np = split_pieces(opts.prec);
+        const int np = split_pieces(rprec);
         float *xp = nullptr, *yp = nullptr;
         if ((st = sc.get(&xp, (size_t)A->data_len * np))) return st;
-        e = launch_split_plain(A, opts.prec, xp, g_stream);
+        e = launch_split_plain(A, rprec, xp, g_stream);
         if (e == cudaSuccess && B != A) {
             if ((st = sc.get(&yp, (size_t)B->data_len * np))) return st;
-            e = launch_split_plain(B, opts.prec, yp, g_stream);
+            e = launch_split_plain(B, rprec, yp, g_stream);
         }
         if ((st = cuda_check(e, "split pieces"))) return st;
         na.x_plain = xp;
@@ -1192,6 +1411,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     ev.mark(5);
     if ((st = cuda_check(launch_numeric(na, g_stream), "numeric"))) return st;
     ev.mark(6);
+    }
     if (no_sync) return BSM_OK;  // C's storage, counts and plan are unchanged
 
     // ---- swap C's pattern (old arrays are freed stream-ordered after the numeric kernel)
@@ -1218,6 +1438,11 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     C->triples = triples;
     C->prod_A = A; C->prod_B = B;
     C->prod_A_nnzb = A->nnzb; C->prod_B_nnzb = B->nnzb;
+    C->engine = nnzbC == 0 ? BSM_E_NONE
+                : use_panel ? BSM_E_PANEL_TCGEN05
+                : kprec == BSM_P_OZAKI ? BSM_E_OZAKI_MMA
+                : is_tc(kprec) ? BSM_E_SPLIT_MMA
+                               : BSM_E_FP64_CORES;
     for (void *p : {(void *)crow_ptr, (void *)c_col, (void *)c_off, (void *)c_rc, c_data, (void *)cptr, (void *)pa,
                     (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order, (void *)n_marked})
         sc.release(p);
@@ -1297,6 +1522,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
     bsm_opts opts;
     bsm_status st = check_opts(opts_in, &opts);
     if (st) return st;
+    if (opts.prec == BSM_P_TF32x3_PANEL) opts.prec = BSM_P_TF32x3;  // the adjoint runs the mma.sync kernel
     if (C->prod_A != A || C->prod_B != B || C->prod_A_nnzb != A->nnzb || C->prod_B_nnzb != B->nnzb || !C->cptr)
         return set_error(BSM_ERR_ARG, "C does not hold the product list of a multiply of these A and B");
     if ((st = ensure_globals())) return st;
@@ -1405,6 +1631,12 @@ bsm_status bsm_get_counts(bsm_t C, int64_t *products, int64_t *filtered, double 
     if (products) *products = C->nprod;
     if (filtered) *filtered = C->nfiltered;
     if (useful_flop) *useful_flop = C->useful_flop;
+    return BSM_OK;
+}
+
+bsm_status bsm_get_engine(bsm_t C, int32_t *engine) {
+    if (!C || !engine) return set_error(BSM_ERR_ARG, "NULL argument");
+    *engine = C->engine;
     return BSM_OK;
 }
 

@@ -97,6 +97,16 @@ struct bsm_mat {
     // first global row / column of every block row / column ([nbr+1], [nbc+1];
     // built on demand, kept until the handle is destroyed)
     int32_t *row_start = nullptr, *col_start = nullptr;
+    // numeric engine of the last multiply into this matrix (bsm_engine)
+    int32_t engine = -1;
+    // row-panel tiling of this matrix as the left operand of a multiply with
+    // panel_B (built on demand, dropped with the pattern): block rows in
+    // ord_r order, the right operand's block columns in ord_c order (pos_c
+    // is its inverse); only the tiles' locality depends on them
+    bsm_t panel_B = nullptr;
+    int64_t panel_B_nnzb = -1;
+    int32_t panel_B_nbc = -1;
+    int32_t *panel_ord_r = nullptr, *panel_ord_c = nullptr, *panel_pos_c = nullptr;
     // column-major copy of the pattern (built on demand, dropped with the pattern)
     int64_t *t_ptr = nullptr;           // [nbc+1]
     int32_t *t_row = nullptr, *t_blk = nullptr;  // [nnzb]
@@ -341,5 +351,48 @@ cudaError_t launch_compact_i64(int64_t nnzb, const int64_t *kscan, const int64_t
 cudaError_t launch_add_backward(int64_t nnzb, const int64_t *z_blk_off, const int32_t *z_blk_rc,
                                 const int64_t *x_src, const int64_t *y_src, double a, double b, const void *dZ,
                                 void *dX, void *dY, int32_t dtype, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Row-panel TF32x3 numeric kernel on tcgen05 tensor cores (k_panel.cu), for
+// FP64 matrices whose blocks all have one size s <= 24 and multiplies whose
+// norm filter removed no product.  Tiles of 5 x 5 output blocks: row group g
+// holds block rows ord_r[5g .. 5g+4], column group h block columns
+// ord_c[5h .. 5h+4]; cblk[t][5r + c] is the index of C block (row slot r,
+// column slot c) of tile t, or -1.
+struct PanelArgs {
+    int32_t nbr, nbc, s;
+    int64_t n_tiles;
+    const int32_t *tile_order;            // [n_tiles] processing order
+    const int32_t *tile_g, *tile_h;       // [n_tiles]
+    const int32_t *cblk;                  // [n_tiles * 25]
+    const int32_t *ord_r, *ord_c;         // block row / column of every position
+    const int64_t *a_row_ptr; const int32_t *a_col_idx;              // A's pattern
+    const int64_t *b_t_ptr; const int32_t *b_t_row, *b_t_blk;        // B's pattern by columns
+    const uint8_t *a_pack, *b_pack;       // 2 planes x 2304 bytes per block
+    const uint8_t *zeros;                 // 2304 zero bytes
+    double *c_data; const int64_t *c_blk_off;
+    double alpha, beta;
+    const void *old_data; const int64_t *old_off;  // beta != 0: old values (or null)
+    int32_t *status;                      // set to BSM_ERR_TIMEOUT when a wait gives up
+    unsigned long long *work_counter;     // zeroed by the caller
+};
+int64_t panel_pack_bytes(int64_t nblk);
+int panel_slot();
+int panel_tile_rows();
+int panel_tile_cols();
+size_t panel_tile_smem(int32_t ngc);
+size_t panel_smem_bytes();
+// planes of every block of M (trans = 1: of its transposed blocks)
+cudaError_t launch_panel_pack(const bsm_mat *M, int trans, void *out, cudaStream_t s);
+cudaError_t launch_panel_tiles_count(int32_t nbr, const int32_t *ord_r, const int32_t *pos_c,
+                                     const int64_t *c_row_ptr, const int32_t *c_col, int32_t ngc, int64_t *tile_cnt,
+                                     cudaStream_t s);
+cudaError_t launch_panel_tiles_fill(int32_t nbr, const int32_t *ord_r, const int32_t *pos_c,
+                                    const int64_t *c_row_ptr, const int32_t *c_col, int32_t ngc,
+                                    const int64_t *tile_ptr, int32_t *tile_g, int32_t *tile_h, int32_t *cblk,
+                                    cudaStream_t s);
+cudaError_t launch_panel_tile_keys(int64_t ntiles, const int32_t *tile_g, const int32_t *tile_h, int sg, int sh,
+                                   int32_t ngc, uint32_t *keys, int32_t *iota, cudaStream_t s);
+cudaError_t launch_panel_numeric(const PanelArgs &a, cudaStream_t s);
 
 }  // namespace bsm
