@@ -309,8 +309,8 @@ def run_other(args):
         ref = None
         # error over the first 2^28 elements of C (the whole C of the 6912-block case is 38 GB)
         nref = 1 << 28
-        for key, prec in (("fp64", "fp64"), ("ozaki", "ozaki"), ("tf32x3", "tf32x3"), ("bf16x6", "bf16x6"),
-                          ("bf16x3", "bf16x3")):
+        for key, prec in (("fp64", "fp64"), ("ozaki", "ozaki"), ("tf32x3", "tf32x3"),
+                          ("tf32x3_panel", "tf32x3_panel"), ("bf16x6", "bf16x6"), ("bf16x3", "bf16x3")):
             ms = _timed(torch, lambda: bsm.multiply(1.0, A, B, 0.0, Cm, w["eps"], prec=prec, build_stacks=False),
                         args.steps, args.warmup)
             flop = Cm.counts().useful_flop
@@ -320,7 +320,7 @@ def run_other(args):
                 ref = c
             err = (torch.linalg.vector_norm(c - ref) / torch.linalg.vector_norm(ref)).item()
             legs[key] = {"value": flop / ms * 1e-9, "ms_per_step": ms, "rel_fro_err_vs_fp64_path": err,
-                         "err_sample_elements": int(c.numel())}
+                         "err_sample_elements": int(c.numel()), "engine": Cm.engine()}
             del c
             torch.cuda.empty_cache()
         out.update(value=legs["fp64"]["value"], ms_per_step=legs["fp64"]["ms_per_step"],
@@ -360,13 +360,14 @@ def run_other(args):
             Cm = bsm.Matrix.empty(bs, bs)
             row = {"s": s_, "nb": nb, "occupancy": occ}
             bsm.bsm_set_profiling(True)
-            for prec in ("fp64", "ozaki", "tf32x3"):
+            for prec in ("fp64", "ozaki", "tf32x3") + (("tf32x3_panel",) if s_ <= 24 else ()):
                 num = []
                 ms = _timed(torch, lambda: (bsm.multiply(1.0, A, B, 0.0, Cm, 0.0, prec=prec, build_stacks=False),
                                             num.append(Cm.timings()["numeric"])), args.steps, args.warmup)
                 flop = Cm.counts().useful_flop
                 nm = statistics.median(num[args.warmup:] or num)
-                row[prec] = {"step_tflops": flop / ms * 1e-9, "numeric_tflops": flop / nm * 1e-9, "numeric_ms": nm}
+                row[prec] = {"step_tflops": flop / ms * 1e-9, "numeric_tflops": flop / nm * 1e-9, "numeric_ms": nm,
+                             "engine": Cm.engine()}
             bsm.bsm_set_profiling(False)
             row["products"] = Cm.counts().products
             rows.append(row)

@@ -77,9 +77,10 @@ typedef enum {
                              BSM_P_TF32x3) on the fifth-generation tensor cores
                              (tcgen05, accumulators in tensor memory), over dense
                              tiles of 5 x 5 output blocks: every k-step of a tile
-                             is one 128 x 128 x 24 product; two k-steps are
-                             summed in FP32 (at most 3 x 48 terms), and those
-                             sums added into a compensated FP32 pair per element.
+                             is one 128 x 128 x 24 product; three k-steps are
+                             summed in FP32 (at most 3 x 72 terms), and those
+                             sums added into a compensated pair per element
+                             (FP32 sum, BF16 compensation term).
                              Runs when the data is FP64, every block of A, B and
                              C has one size s <= 24 and the norm filter removed
                              no product; otherwise the multiply runs the

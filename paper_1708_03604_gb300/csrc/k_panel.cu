@@ -10,39 +10,42 @@
 // panel (rows padded to 128) by the 5 B blocks side by side (24 x 120, padded
 // to 128 columns): a 128 x 128 x 24 product, three MMAs of K = 8 for each of
 // the three TF32 piece products lo.hi, hi.lo and hi.hi (the split and the
-// order of the mma.sync TF32x3 path).  Two consecutive k-steps of a tile
+// order of the mma.sync TF32x3 path).  Three consecutive k-steps of a tile
 // accumulate in FP32 inside the tensor core (rounding toward zero, as
-// measured: at most 3 x 48 terms per sum); each such sum is added on the CUDA
-// cores into a compensated FP32 pair (Kahan summation, the update of the
-// mma.sync path) that lives in tensor memory beside two accumulator buffers,
-// and converted to FP64 once per tile.  Products the tile computes for absent
+// measured: at most 3 x 72 terms per sum); each such sum is added on the CUDA
+// cores into a compensated pair held in the drain threads' registers (Kahan
+// summation as on the mma.sync path, the FP32 sum as there, the compensation
+// term kept in BF16: at most 2^-33 of the sum lost per add), and converted to
+// FP64 once per tile.  Products the tile computes for absent
 // blocks are exact zeros.  A product removed by the norm filter would still
 // be computed inside the dense tile, so the launcher uses this kernel only
 // when the filter removed none.
 //
-// Roles in one persistent CTA per SM (14 warps):
+// Roles in one persistent CTA per SM (12 warps):
 //   warp 0      merge: takes tiles from an atomic ticket and merges the five
 //               A rows' and five B columns' sorted block-index lists (each
-//               read 4 entries ahead) into k-step records in a shared ring;
-//   warps 1..4  copy: warp c stages operand plane c (A hi, A lo, B hi, B lo)
-//               of every k-step, 5 block planes of 2304 bytes pre-packed in
-//               the tensor core's shared-memory layout, with 16-byte cp.async
-//               (absent blocks zero-filled); once a stage's copies of a
-//               thread have landed it fences them into the async proxy and
-//               arrives on the stage's "full" barrier (4-stage ring);
-//   warp 5      allocates tensor memory; one lane issues the MMAs of a k-step
+//               read 4 entries ahead, with the blocks they name) into k-step
+//               records in a shared ring;
+//   warps 1, 2  copy: stage the 10 blocks of every k-step (warp 1 A's, warp 2
+//               B's), one bulk copy of 4608 bytes per block pre-packed in the
+//               tensor core's shared-memory layout (absent blocks from a zero
+//               block), completion counted in bytes on the stage's "full"
+//               barrier (4-stage ring);
+//   warp 3      allocates tensor memory; one lane issues the MMAs of a k-step
 //               into accumulator buffer b and commits them to the stage's
-//               "empty" barrier and, every second k-step, to the buffer's
+//               "empty" barrier and, every third k-step, to the buffer's
 //               "full" barrier;
-//   warps 6..13 drain: each owns one 32-lane quarter of tensor memory (32 rows
-//               of the tile) and one half of its columns, adds the buffer into
-//               the compensated pair, frees the buffer, and on a tile's last
-//               k-step writes C.
+//   warps 4..11 drain: each owns one 32-lane quarter of tensor memory (32 rows
+//               of the tile) and one half of its columns, reads the buffer
+//               into registers, frees it, adds it into the compensated pair,
+//               and on a tile's last k-step writes C.
 // Every wait is bounded (2 s); a wait that runs out sets the output's status
 // word to BSM_ERR_TIMEOUT, every role then leaves its loop, waits for its own
 // copies and MMAs in flight, and the tensor memory is freed.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -67,7 +70,7 @@ constexpr int kStageBytes = 2 * kOperand;    // A, then B
 constexpr int kStages = 4;
 constexpr int kRing = 16;                 // k-step records between the merge and the copy warps
 constexpr int kPre = 4;                   // list entries the merge loads ahead
-constexpr int kPair = 2;                  // k-steps summed in one accumulator buffer before a drain
+constexpr int kPair = 3;                  // k-steps summed in one accumulator buffer before a drain
 constexpr int kCopyWarps = 2, kMmaWarp = 3, kDrainWarps = 8;
 constexpr int kThreads = 32 * (2 + kCopyWarps + kDrainWarps);
 constexpr unsigned long long kWaitNs = 2000000000ull;  // a wait gives up after 2 s
@@ -122,21 +125,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const int32_t *abort) {
-    unsigned long long t0 = 0;
-    for (long it = 0;; ++it) {
-        if ((it & 1023) == 1023) {
-            if (*(volatile const int32_t *)abort) return false;
-            const unsigned long long t = global_ns();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > kWaitNs) return false;
-        }
+    // each try_wait suspends the thread (no issue slots taken) until the
+    // phase completes or the hinted 20 us pass
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(mbar), "r"(parity)
+            : "r"(mbar), "r"(parity), "r"(20000)
             : "memory");
         if (ok) return true;
+        if (*(volatile const int32_t *)abort) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
     }
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -152,25 +153,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
-        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
-        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
-}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// compensated add of b into (hi, lo): the update of the mma.sync TF32x3 path
-__device__ __forceinline__ void kahan(float &hi, float &lo, float b) {
-    const float y = __fadd_rn(b, lo);
-    const float t = __fadd_rn(hi, y);
-    lo = __fsub_rn(y, __fsub_rn(t, hi));
-    hi = t;
+// compensated add of b into (hi, lo) (the update of the mma.sync TF32x3
+// path) with the compensation lo held as BF16: lo is below half an ulp of hi,
+// so rounding it to 8 bits costs at most 2^-9 of it, 2^-33 of hi, per add
+__device__ __forceinline__ void kahan_b2(float &hi0, float &hi1, __nv_bfloat162 &lo, float b0, float b1) {
+    const float2 l = __bfloat1622float2(lo);
+    const float y0 = __fadd_rn(b0, l.x), y1 = __fadd_rn(b1, l.y);
+    const float t0 = __fadd_rn(hi0, y0), t1 = __fadd_rn(hi1, y1);
+    lo = __floats2bfloat162_rn(__fsub_rn(y0, __fsub_rn(t0, hi0)), __fsub_rn(y1, __fsub_rn(t1, hi1)));
+    hi0 = t0;
+    hi1 = t1;
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -310,8 +304,8 @@ __global__ void k_panel_tile_keys(int64_t ntiles, const int32_t *tile_g, const i
 // ---------------------------------------------------------------------------
 struct Record {
     int32_t tile, flags;
-    int32_t a[kRB];  // A block index (position in A's CSR) of every row slot, or -1
-    int32_t b[kCB];  // position in B's column-major list of every column slot, or -1
+    int32_t a[kRB];  // A block of every row slot (or -1)
+    int32_t b[kCB];  // B block of every column slot (or -1)
 };
 
 struct SmemCtl {
@@ -332,6 +326,80 @@ __device__ __forceinline__ void fail(SmemCtl &ctl, int32_t *status) {
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Drain warp of tensor-memory lanes 32 quarter .. +31 (tile rows) and columns
+// 64 HALF .. +63 of both accumulator buffers: its threads keep the compensated
+// pair of their 64 elements in registers (sum FP32, compensation BF16), add
+// every buffer into it, and on a tile's last k-step write the tile's C blocks.
+template <int HALF>
+__device__ __forceinline__ void drain(const PanelArgs &a, SmemCtl &ctl, uint32_t tmem, int quarter, int lane,
+                                      bool dead) {
+    const int row = quarter * 32 + lane;
+    const int si = row / kSlot, ri = row - si * kSlot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + HALF * 64;
+    float sh[64];
+    __nv_bfloat162 sl[32];  // compensation of elements 2i, 2i + 1
+    uint32_t buf = 0, bph = 0;
+    bool ok = !dead;
+    while (ok) {
+        if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.accf[buf]), bph, &ctl.abort))) {
+            if (lane == 0) fail(ctl, a.status);
+            break;
+        }
+        tc_fence_after();
+        const int32_t t = ctl.ameta_t[buf], flags = ctl.ameta_f[buf];
+        if (flags & kDone) break;
+        const bool first = flags & kFirst, last = flags & kLast;
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            uint32_t v[32];
+            tmem_ld32(lane_base + buf * 128 + ch * 32, v);
+            tmem_wait_ld();
+            if (ch == 1) {  // the buffer is free as soon as it is in registers
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(saddr(&ctl.acce[buf]));
+            }
+#pragma unroll
+            for (int e = 0; e < 32; e += 2) {
+                if (first) {  // the compensated add of v into (0, 0)
+                    sh[ch * 32 + e] = __uint_as_float(v[e]);
+                    sh[ch * 32 + e + 1] = __uint_as_float(v[e + 1]);
+                    sl[(ch * 32 + e) / 2] = __floats2bfloat162_rn(0.f, 0.f);
+                } else {
+                    kahan_b2(sh[ch * 32 + e], sh[ch * 32 + e + 1], sl[(ch * 32 + e) / 2], __uint_as_float(v[e]),
+                             __uint_as_float(v[e + 1]));
+                }
+            }
+        }
+        buf ^= 1u;
+        if (buf == 0) bph ^= 1u;
+        if (last && si < kRB && ri < a.s) {
+            const double *old = static_cast<const double *>(a.old_data);
+            const int32_t *cb = a.cblk + (int64_t)t * (kRB * kCB) + si * kCB;
+            // the column slots this half of the tile touches
+            constexpr int c0 = (HALF * 64) / kSlot, c1 = (HALF * 64 + 63) / kSlot;
+#pragma unroll
+            for (int c = c0; c <= c1 && c < kCB; ++c) {
+                const int32_t q = cb[c];
+                if (q < 0) continue;
+                const int64_t o = a.c_blk_off[q] + (int64_t)ri * a.s;
+                const int64_t oo = (old && a.old_off) ? a.old_off[q] : -1;
+#pragma unroll
+                for (int e = 0; e < 64; ++e) {
+                    const int col = HALF * 64 + e;
+                    if (col / kSlot != c) continue;
+                    const int cj = col - c * kSlot;
+                    if (cj >= a.s) continue;
+                    const float2 lo = __bfloat1622float2(sl[e / 2]);
+                    double val = a.alpha * ((double)sh[e] + (double)((e & 1) ? lo.y : lo.x));
+                    if (oo >= 0) val = fma(a.beta, old[oo + (int64_t)ri * a.s + cj], val);
+                    a.c_data[o + cj] = val;
+                }
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
     extern __shared__ __align__(1024) uint8_t dsm[];
@@ -427,22 +495,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
                     pe = a.b_t_ptr[j + 1];
                 }
             }
+            // q: block index k of the next entries; bq: their block (B: from
+            // the column-major list; A: the CSR position itself)
             uint32_t q[kPre];
+            int32_t bq[kPre];
 #pragma unroll
-            for (int d = 0; d < kPre; ++d) q[d] = p + d < pe ? (uint32_t)list[p + d] : 0xFFFFFFFFu;
-            auto next_step = [&](int32_t &pos) -> bool {
+            for (int d = 0; d < kPre; ++d) {
+                q[d] = p + d < pe ? (uint32_t)list[p + d] : 0xFFFFFFFFu;
+                bq[d] = p + d < pe ? (is_b ? a.b_t_blk[p + d] : (int32_t)(p + d)) : -1;
+            }
+            auto next_step = [&](int32_t &blk) -> bool {
                 for (;;) {
                     const uint32_t k = __reduce_min_sync(0xffffffffu, q[0]);
                     if (k == 0xFFFFFFFFu) return false;
                     const bool mine = q[0] == k;
                     const uint32_t am = __ballot_sync(0xffffffffu, mine && lane < kRB);
                     const uint32_t bm = __ballot_sync(0xffffffffu, mine && is_b);
-                    pos = mine ? (int32_t)p : -1;
+                    blk = mine ? bq[0] : -1;
                     if (mine) {
                         ++p;
 #pragma unroll
-                        for (int d = 0; d + 1 < kPre; ++d) q[d] = q[d + 1];
-                        q[kPre - 1] = p + kPre - 1 < pe ? (uint32_t)list[p + kPre - 1] : 0xFFFFFFFFu;
+                        for (int d = 0; d + 1 < kPre; ++d) {
+                            q[d] = q[d + 1];
+                            bq[d] = bq[d + 1];
+                        }
+                        const int64_t n = p + kPre - 1;
+                        q[kPre - 1] = n < pe ? (uint32_t)list[n] : 0xFFFFFFFFu;
+                        bq[kPre - 1] = n < pe ? (is_b ? a.b_t_blk[n] : (int32_t)n) : -1;
                     }
                     if (am && bm) return true;
                 }
@@ -465,10 +544,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
         if (ok) put(0, kDone, -1);
     } else if (warp <= kCopyWarps) {
         // ------------------------------------------------------------ copy
-        // warp 1 stages the 5 A blocks of every k-step, warp 2 the 5 B blocks:
-        // one bulk copy of 4608 bytes per block (absent blocks from a zero
-        // block), completion counted in bytes on the stage's "full" barrier
-        const bool is_a = warp == 1;
+        // warp 1 stages A's 5 blocks of every k-step, warp 2 B's: one bulk
+        // copy of 4608 bytes per block (absent blocks from a zero block),
+        // completion counted in bytes on the stage's "full" barrier
+        const int cw = warp - 1;
+        const bool is_a = cw == 0;
+        const int s0 = 0, ns = kRB;
         const uint8_t *pk = is_a ? a.a_pack : a.b_pack;
         uint32_t st = 0, ph = 0, rs = 0, rph = 0;
         int64_t issued = 0;
@@ -481,32 +562,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
             }
             const Record &r = ctl.rec[rs];
             const int32_t tile = r.tile, flags = r.flags;
-            int32_t blk = lane < kRB ? (is_a ? r.a[lane] : r.b[lane]) : -1;
+            const int32_t blk = lane < ns ? (is_a ? r.a[s0 + lane] : r.b[s0 + lane]) : -1;
             __syncwarp();
             if (lane == 0) mbar_arrive(saddr(&ctl.rec_empty[rs]));
             if (++rs == kRing) {
                 rs = 0;
                 rph ^= 1u;
             }
-            if (!is_a && blk >= 0) blk = a.b_t_blk[blk];
             if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort))) {
                 if (lane == 0) fail(ctl, a.status);
                 ok = false;
                 break;
             }
             if (lane == 0) {
-                if (is_a) {
+                if (cw == 0) {
                     ctl.smeta_t[st] = tile;
                     ctl.smeta_f[st] = flags;
                 }
                 if (flags & kDone) mbar_arrive(saddr(&ctl.full[st]));
-                else mbar_arrive_tx(saddr(&ctl.full[st]), kRB * kBlk);
+                else mbar_arrive_tx(saddr(&ctl.full[st]), ns * kBlk);
             }
             if (flags & kDone) break;
             __syncwarp();
-            if (lane < kRB) {
+            if (lane < ns) {
                 const void *src = blk >= 0 ? (const void *)(pk + (int64_t)blk * kBlk) : (const void *)a.zeros;
-                bulk_copy(saddr(stages + st * kStageBytes + (is_a ? 0 : kOperand) + lane * kBlk), src, kBlk,
+                bulk_copy(saddr(stages + st * kStageBytes + (is_a ? 0 : kOperand) + (s0 + lane) * kBlk), src, kBlk,
                           saddr(&ctl.full[st]));
             }
             ++issued;
@@ -588,90 +668,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
         __syncwarp();
     } else {
         // ------------------------------------------------------------ drain
-        // warp d owns tensor-memory lanes 32 (warp % 4) .. +31 (tile rows) and
-        // columns 64 half .. +63 of every buffer and of the compensated pair
-        const int quarter = warp & 3, half = (warp - kMmaWarp - 1) / 4;
-        const int row = quarter * 32 + lane;
-        const int si = row / kSlot, ri = row - si * kSlot;
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + half * 64;
-        uint32_t buf = 0, bph = 0;
-        bool ok = !dead;
-        while (ok) {
-            if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.accf[buf]), bph, &ctl.abort))) {
-                if (lane == 0) fail(ctl, a.status);
-                break;
-            }
-            tc_fence_after();
-            const int32_t t = ctl.ameta_t[buf], flags = ctl.ameta_f[buf];
-            if (flags & kDone) break;
-            const bool first = flags & kFirst, last = flags & kLast;
-            int64_t coff[kCB], ooff[kCB];
-            const double *old = static_cast<const double *>(a.old_data);
-            if (last) {
-#pragma unroll
-                for (int c = 0; c < kCB; ++c) {
-                    const int32_t q = si < kRB ? a.cblk[(int64_t)t * (kRB * kCB) + si * kCB + c] : -1;
-                    coff[c] = (q >= 0 && ri < a.s) ? a.c_blk_off[q] : -1;
-                    ooff[c] = (q >= 0 && old && a.old_off) ? a.old_off[q] : -1;
-                }
-            }
-#pragma unroll 1
-            for (int ch = 0; ch < 2; ++ch) {
-                uint32_t v[32], sh[32], sl[32];
-                __syncwarp();
-                tmem_ld32(lane_base + buf * 128 + ch * 32, v);
-                if (first) {
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        sh[e] = v[e];  // the compensated add of v into (0, 0)
-                        sl[e] = 0u;
-                    }
-                } else {
-                    tmem_ld32(lane_base + 256 + ch * 32, sh);
-                    tmem_ld32(lane_base + 384 + ch * 32, sl);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        float hi = __uint_as_float(sh[e]), lo = __uint_as_float(sl[e]);
-                        kahan(hi, lo, __uint_as_float(v[e]));
-                        sh[e] = __float_as_uint(hi);
-                        sl[e] = __float_as_uint(lo);
-                    }
-                }
-                if (last) {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int col = half * 64 + ch * 32 + e;
-                        const int sj = col / kSlot, cj = col - sj * kSlot;
-                        if (sj < kCB && cj < a.s) {
-                            int64_t o = -1, oo = -1;
-#pragma unroll
-                            for (int c = 0; c < kCB; ++c)
-                                if (c == sj) {
-                                    o = coff[c];
-                                    oo = ooff[c];
-                                }
-                            if (o >= 0) {
-                                const int64_t el = (int64_t)ri * a.s + cj;
-                                double val = a.alpha * ((double)__uint_as_float(sh[e]) + (double)__uint_as_float(sl[e]));
-                                if (oo >= 0) val = fma(a.beta, old[oo + el], val);
-                                a.c_data[o + el] = val;
-                            }
-                        }
-                    }
-                } else {
-                    tmem_st32(lane_base + 256 + ch * 32, sh);
-                    tmem_st32(lane_base + 384 + ch * 32, sl);
-                }
-            }
-            if (!last) tmem_wait_st();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&ctl.acce[buf]));
-            buf ^= 1u;
-            if (buf == 0) bph ^= 1u;
-        }
+        const int quarter = warp & 3;
+        if ((warp - kMmaWarp - 1) / 4 == 0) drain<0>(a, ctl, tmem, quarter, lane, dead);
+        else drain<1>(a, ctl, tmem, quarter, lane, dead);
     }
     tc_fence_before();
     __syncthreads();

@@ -45,13 +45,15 @@ def _run(bsm, oracle, A, B, eps=0.0, beta=0.0, C0=None, alpha=1.0, prec="tf32x3_
     return Cg, ref, gA, gB
 
 
-def _bound_coeff(s):
+def _bound_coeff(s, nsteps):
     """TF32x3 worst case per element as a multiple of sum_k |a_ik||b_kj|: the
     cut into two 11-bit pieces and the left-out lo*lo product (3 * 2^-22), the
-    FP32 sum inside the tensor core of two k-steps (3 piece products of 2 s
+    FP32 sum inside the tensor core of three k-steps (3 piece products of 3 s
     terms, each addition off by at most 2^-23 of the running magnitude:
-    rounding toward zero), the compensated sum across those sums (2^-22)."""
-    return 1.1 * (3 * 2.0 ** -22 + 3 * 2 * s * 2.0 ** -23 + 2.0 ** -22)
+    rounding toward zero), the compensated sum across those sums (2^-22) with
+    its compensation term rounded to BF16 after every add (2^-33 each, at most
+    one add per k-step)."""
+    return 1.1 * (3 * 2.0 ** -22 + 3 * 3 * s * 2.0 ** -23 + 2.0 ** -22 + nsteps * 2.0 ** -33)
 
 
 @pytest.mark.parametrize("case", ["uniform23", "banded23", "s13", "s24", "s4"])
@@ -94,7 +96,7 @@ def test_panel_elementwise_bound(bsm, oracle):
     _check_pattern(Cg, ref.C)
     Ch = I.BCSR(ref.C.row_bs, ref.C.col_bs, ref.C.row_ptr, ref.C.col_idx, ref.C.blk_off, Cg.data_host())
     err = np.abs(to_dense(Ch) - to_dense(ref.C))
-    bound = _bound_coeff(23) * (np.abs(to_dense(A)) @ np.abs(to_dense(B)))
+    bound = _bound_coeff(23, len(bs)) * (np.abs(to_dense(A)) @ np.abs(to_dense(B)))
     assert np.all(err <= bound), float(np.max(err / np.where(bound > 0, bound, 1.0)))
 
 

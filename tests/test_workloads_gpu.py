@@ -70,8 +70,11 @@ def test_uniform_23_full(env, oracle):
     w = I.uniform_23()
     A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
     ref = oracle.multiply(1.0, w["A"], w["B"])
-    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("bf16x6", 1e-6), ("fp64", 1e-12)):
+    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("tf32x3_panel", 1e-6), ("bf16x6", 1e-6),
+                      ("fp64", 1e-12)):
         Cm = bsm.multiply(1.0, A, B, prec=prec)
+        if prec == "tf32x3_panel":
+            assert Cm.engine() == "panel_tcgen05"
         rp, ci, bo = Cm.pattern()
         np.testing.assert_array_equal(rp, ref.C.row_ptr)
         np.testing.assert_array_equal(ci, ref.C.col_idx)
@@ -132,9 +135,11 @@ def test_large_23_sampled_rows(env, oracle):
     assert cnt.useful_flop == 2 * 23 ** 3 * cnt.products
     _rows_check(bsm, torch, Cm, ref, rows, w["A"].row_bs, w["B"].col_bs, 1e-12)
     del Cm
-    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("bf16x6", 1e-6)):
+    for prec, tol in (("ozaki", 1e-13), ("tf32x3", 1e-6), ("tf32x3_panel", 1e-6), ("bf16x6", 1e-6)):
         Ct = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec, build_stacks=False)
         assert Ct.counts().products == cnt.products
+        if prec == "tf32x3_panel":
+            assert Ct.engine() == "panel_tcgen05"
         _rows_check(bsm, torch, Ct, ref, rows, w["A"].row_bs, w["B"].col_bs, tol)
         del Ct
 
