@@ -616,6 +616,29 @@ bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const Panel
     if (e == cudaSuccess)
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, ntiles, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "panel tiles"))) return st;
+    PanelArgs pa{};
+    pa.nbr = nbr; pa.nbc = nbc; pa.s = s;
+    pa.n_tiles = ntiles;
+    pa.tile_order = order; pa.tile_g = tile_g; pa.tile_h = tile_h; pa.cblk = cblk;
+    pa.ord_r = A->panel_ord_r; pa.ord_c = A->panel_ord_c;
+    pa.a_row_ptr = A->row_ptr; pa.a_col_idx = A->col_idx;
+    pa.b_t_ptr = B->t_ptr; pa.b_t_row = B->t_row; pa.b_t_blk = B->t_blk;
+    // the k-steps of every tile (a merge of its 10 block-index lists)
+    int64_t *step_cnt, *step_ptr, *stmp2;
+    if ((st = sc.get(&step_cnt, ntiles)) || (st = sc.get(&step_ptr, (size_t)ntiles + 1)) ||
+        (st = sc.get(&stmp2, scan_tmp_elems(ntiles))))
+        return st;
+    e = launch_panel_steps(pa, 0, step_cnt, g_stream);
+    if (e == cudaSuccess) e = launch_scan_i64(step_cnt, step_ptr, ntiles, stmp2, g_stream);
+    if ((st = cuda_check(e, "panel steps"))) return st;
+    const int64_t *ssrc[1] = {step_ptr + ntiles};
+    if ((st = read_words(ssrc, 1))) return st;
+    const int64_t nsteps = g_host[0];
+    int32_t *steps;
+    if ((st = sc.get(&steps, (size_t)nsteps * 2 * panel_tile_rows()))) return st;
+    pa.step_ptr = step_ptr;
+    pa.steps = steps;
+    if ((st = cuda_check(launch_panel_steps(pa, 1, nullptr, g_stream), "panel steps"))) return st;
     // operand planes
     uint8_t *apk, *bpk, *zeros;
     unsigned long long *counter;
@@ -627,13 +650,6 @@ bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const Panel
     if (e == cudaSuccess) e = cudaMemsetAsync(zeros, 0, (size_t)panel_pack_bytes(1), g_stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), g_stream);
     if ((st = cuda_check(e, "panel operands"))) return st;
-    PanelArgs pa{};
-    pa.nbr = nbr; pa.nbc = nbc; pa.s = s;
-    pa.n_tiles = ntiles;
-    pa.tile_order = order; pa.tile_g = tile_g; pa.tile_h = tile_h; pa.cblk = cblk;
-    pa.ord_r = A->panel_ord_r; pa.ord_c = A->panel_ord_c;
-    pa.a_row_ptr = A->row_ptr; pa.a_col_idx = A->col_idx;
-    pa.b_t_ptr = B->t_ptr; pa.b_t_row = B->t_row; pa.b_t_blk = B->t_blk;
     pa.a_pack = apk; pa.b_pack = bpk; pa.zeros = zeros;
     pa.c_data = o.c_data; pa.c_blk_off = o.c_off;
     pa.alpha = o.alpha; pa.beta = o.beta;

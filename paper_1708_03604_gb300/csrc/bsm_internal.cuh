@@ -368,8 +368,12 @@ struct PanelArgs {
     const int32_t *ord_r, *ord_c;         // block row / column of every position
     const int64_t *a_row_ptr; const int32_t *a_col_idx;              // A's pattern
     const int64_t *b_t_ptr; const int32_t *b_t_row, *b_t_blk;        // B's pattern by columns
-    const uint8_t *a_pack, *b_pack;       // 2 planes x 2304 bytes per block
-    const uint8_t *zeros;                 // 2304 zero bytes
+    const uint8_t *a_pack, *b_pack;       // 4608 bytes per block (TF32 hi and lo planes)
+    const uint8_t *zeros;                 // 4608 zero bytes
+    // k-steps of every tile t: steps[step_ptr[t] .. step_ptr[t+1]), each 10
+    // block indices (A's 5 row slots, then B's 5 column slots; -1: absent)
+    const int64_t *step_ptr;
+    int32_t *steps;
     double *c_data; const int64_t *c_blk_off;
     double alpha, beta;
     const void *old_data; const int64_t *old_off;  // beta != 0: old values (or null)
@@ -393,6 +397,8 @@ cudaError_t launch_panel_tiles_fill(int32_t nbr, const int32_t *ord_r, const int
                                     cudaStream_t s);
 cudaError_t launch_panel_tile_keys(int64_t ntiles, const int32_t *tile_g, const int32_t *tile_h, int sg, int sh,
                                    int32_t ngc, uint32_t *keys, int32_t *iota, cudaStream_t s);
+// k-steps of every tile: counts (fill = 0: step_cnt[t]) or records (fill = 1)
+cudaError_t launch_panel_steps(const PanelArgs &a, int fill, int64_t *step_cnt, cudaStream_t s);
 cudaError_t launch_panel_numeric(const PanelArgs &a, cudaStream_t s);
 
 }  // namespace bsm

@@ -68,7 +68,7 @@ constexpr int kBlk = 3 * kGroupStride;    // bytes of one packed block (hi and l
 constexpr int kOperand = 16 * kGroupStride;  // one operand of a stage, 128 rows: 24576
 constexpr int kStageBytes = 2 * kOperand;    // A, then B
 constexpr int kStages = 4;
-constexpr int kRing = 16;                 // k-step records between the merge and the copy warps
+constexpr int kRing = 8;                  // tiles handed from the ticket warp to the copy warps
 constexpr int kPre = 4;                   // list entries the merge loads ahead
 constexpr int kPair = 3;                  // k-steps summed in one accumulator buffer before a drain
 constexpr int kCopyWarps = 2, kMmaWarp = 3, kDrainWarps = 8;
@@ -302,10 +302,9 @@ __global__ void k_panel_tile_keys(int64_t ntiles, const int32_t *tile_g, const i
 }
 
 // ---------------------------------------------------------------------------
-struct Record {
-    int32_t tile, flags;
-    int32_t a[kRB];  // A block of every row slot (or -1)
-    int32_t b[kCB];  // B block of every column slot (or -1)
+struct TileRec {
+    int32_t tile;    // -1: no more tiles
+    int64_t s0, s1;  // its k-steps
 };
 
 struct SmemCtl {
@@ -313,7 +312,7 @@ struct SmemCtl {
     uint64_t accf[2], acce[2];
     uint64_t rec_full[kRing], rec_empty[kRing];
     uint64_t fin;
-    Record rec[kRing];
+    TileRec rec[kRing];
     int32_t smeta_t[kStages], smeta_f[kStages];
     int32_t ameta_t[2], ameta_f[2];
     uint32_t tmem;
@@ -326,6 +325,99 @@ __device__ __forceinline__ void fail(SmemCtl &ctl, int32_t *status) {
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// The k-steps of tile t in ascending inner block index k: every k for which
+// some A_ik of the tile's 5 block rows and some B_kj of its 5 block columns
+// are present (a merge of the 10 sorted lists, lanes 0..4 walking A's rows,
+// lanes 8..12 B's columns, the next kPre entries of every list loaded ahead).
+// emit(blk) is called once per k-step by every lane, blk being the block of
+// the lane's row / column slot there (or -1); a tile without any such k (only
+// blocks kept from the old C) gets one step with all blocks absent.
+template <class F>
+__device__ __forceinline__ void panel_merge(const PanelArgs &a, int32_t t, int lane, F &&emit) {
+    const int32_t g = a.tile_g[t], h = a.tile_h[t];
+    // cursors: lanes 0..4 walk A's rows, lanes 8..12 B's columns; the
+    // next kPre entries of every list are loaded ahead
+    int64_t p = 0, pe = 0;
+    const bool is_b = lane >= 8 && lane < 8 + kCB;
+    const int32_t *list = is_b ? a.b_t_row : a.a_col_idx;
+    if (lane < kRB) {
+        const int pr = g * kRB + lane;
+        if (pr < a.nbr) {
+            const int i = a.ord_r[pr];
+            p = a.a_row_ptr[i];
+            pe = a.a_row_ptr[i + 1];
+        }
+    } else if (is_b) {
+        const int pc = h * kCB + lane - 8;
+        if (pc < a.nbc) {
+            const int j = a.ord_c[pc];
+            p = a.b_t_ptr[j];
+            pe = a.b_t_ptr[j + 1];
+        }
+    }
+    // q: block index k of the next entries; bq: their block (B: from
+    // the column-major list; A: the CSR position itself)
+    uint32_t q[kPre];
+    int32_t bq[kPre];
+#pragma unroll
+    for (int d = 0; d < kPre; ++d) {
+        q[d] = p + d < pe ? (uint32_t)list[p + d] : 0xFFFFFFFFu;
+        bq[d] = p + d < pe ? (is_b ? a.b_t_blk[p + d] : (int32_t)(p + d)) : -1;
+    }
+    auto next_step = [&](int32_t &blk) -> bool {
+        for (;;) {
+            const uint32_t k = __reduce_min_sync(0xffffffffu, q[0]);
+            if (k == 0xFFFFFFFFu) return false;
+            const bool mine = q[0] == k;
+            const uint32_t am = __ballot_sync(0xffffffffu, mine && lane < kRB);
+            const uint32_t bm = __ballot_sync(0xffffffffu, mine && is_b);
+            blk = mine ? bq[0] : -1;
+            if (mine) {
+                ++p;
+#pragma unroll
+                for (int d = 0; d + 1 < kPre; ++d) {
+                    q[d] = q[d + 1];
+                    bq[d] = bq[d + 1];
+                }
+                const int64_t n = p + kPre - 1;
+                q[kPre - 1] = n < pe ? (uint32_t)list[n] : 0xFFFFFFFFu;
+                bq[kPre - 1] = n < pe ? (is_b ? a.b_t_blk[n] : (int32_t)n) : -1;
+            }
+            if (am && bm) return true;
+        }
+    };
+    int32_t cur = -1, nxt = -1;
+    bool have = next_step(cur);
+    if (!have) {
+        emit(-1);
+        return;
+    }
+    while (have) {
+        const bool more = next_step(nxt);
+        emit(cur);
+        cur = nxt;
+        have = more;
+    }
+}
+
+// one warp per tile: fill = 0 counts the tile's k-steps into step_cnt[t],
+// fill = 1 writes their records at step_ptr[t]
+__global__ void __launch_bounds__(256) k_panel_steps(PanelArgs a, int fill, int64_t *step_cnt) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= a.n_tiles) return;
+    int64_t n = 0;
+    int32_t *rec = fill ? a.steps + a.step_ptr[t] * (kRB + kCB) : nullptr;
+    panel_merge(a, (int32_t)t, lane, [&](int32_t blk) {
+        if (fill) {
+            if (lane < kRB) rec[n * (kRB + kCB) + lane] = blk;
+            else if (lane >= 8 && lane < 8 + kCB) rec[n * (kRB + kCB) + kRB + lane - 8] = blk;
+        }
+        ++n;
+    });
+    if (!fill && lane == 0) step_cnt[t] = n;
+}
 
 // Drain warp of tensor-memory lanes 32 quarter .. +31 (tile rows) and columns
 // 64 HALF .. +63 of both accumulator buffers: its threads keep the compensated
@@ -444,112 +536,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
     const int32_t no_abort = 0;  // waits that must not be cut short by the abort flag
 
     if (warp == 0) {
-        // ------------------------------------------------------------ merge
-        // k-steps of every tile into the record ring
+        // ------------------------------------------------------------ tiles
+        // hands the tiles of the atomic ticket, with their k-step ranges, to
+        // the copy warps through the ring
         uint32_t rs = 0, rph = 0;
-        auto put = [&](int32_t tile, int32_t flags, int32_t pos) -> bool {
+        bool ok = !dead;
+        for (;;) {
+            int64_t tk = 0;
+            if (lane == 0) tk = (int64_t)atomicAdd(a.work_counter, 1ull);
+            tk = __shfl_sync(0xffffffffu, tk, 0);
+            const bool done = !ok || tk >= a.n_tiles || *(volatile int32_t *)&ctl.abort;
             if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.rec_empty[rs]), rph ^ 1u, &ctl.abort))) {
                 if (lane == 0) fail(ctl, a.status);
-                return false;
+                break;
             }
-            Record &r = ctl.rec[rs];
-            if (lane < kRB) r.a[lane] = pos;
-            else if (lane >= 8 && lane < 8 + kCB) r.b[lane - 8] = pos;
             if (lane == 0) {
-                r.tile = tile;
-                r.flags = flags;
+                TileRec &r = ctl.rec[rs];
+                if (done) {
+                    r.tile = -1;
+                } else {
+                    const int32_t t = a.tile_order[tk];
+                    r.tile = t;
+                    r.s0 = a.step_ptr[t];
+                    r.s1 = a.step_ptr[t + 1];
+                }
+                mbar_arrive(saddr(&ctl.rec_full[rs]));
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&ctl.rec_full[rs]));
             if (++rs == kRing) {
                 rs = 0;
                 rph ^= 1u;
             }
-            return true;
-        };
-        bool ok = !dead;
-        while (ok) {
-            int64_t tk = 0;
-            if (lane == 0) tk = (int64_t)atomicAdd(a.work_counter, 1ull);
-            tk = __shfl_sync(0xffffffffu, tk, 0);
-            if (tk >= a.n_tiles || *(volatile int32_t *)&ctl.abort) break;
-            const int32_t t = a.tile_order[tk];
-            const int32_t g = a.tile_g[t], h = a.tile_h[t];
-            // cursors: lanes 0..4 walk A's rows, lanes 8..12 B's columns; the
-            // next kPre entries of every list are loaded ahead
-            int64_t p = 0, pe = 0;
-            const bool is_b = lane >= 8 && lane < 8 + kCB;
-            const int32_t *list = is_b ? a.b_t_row : a.a_col_idx;
-            if (lane < kRB) {
-                const int pr = g * kRB + lane;
-                if (pr < a.nbr) {
-                    const int i = a.ord_r[pr];
-                    p = a.a_row_ptr[i];
-                    pe = a.a_row_ptr[i + 1];
-                }
-            } else if (is_b) {
-                const int pc = h * kCB + lane - 8;
-                if (pc < a.nbc) {
-                    const int j = a.ord_c[pc];
-                    p = a.b_t_ptr[j];
-                    pe = a.b_t_ptr[j + 1];
-                }
-            }
-            // q: block index k of the next entries; bq: their block (B: from
-            // the column-major list; A: the CSR position itself)
-            uint32_t q[kPre];
-            int32_t bq[kPre];
-#pragma unroll
-            for (int d = 0; d < kPre; ++d) {
-                q[d] = p + d < pe ? (uint32_t)list[p + d] : 0xFFFFFFFFu;
-                bq[d] = p + d < pe ? (is_b ? a.b_t_blk[p + d] : (int32_t)(p + d)) : -1;
-            }
-            auto next_step = [&](int32_t &blk) -> bool {
-                for (;;) {
-                    const uint32_t k = __reduce_min_sync(0xffffffffu, q[0]);
-                    if (k == 0xFFFFFFFFu) return false;
-                    const bool mine = q[0] == k;
-                    const uint32_t am = __ballot_sync(0xffffffffu, mine && lane < kRB);
-                    const uint32_t bm = __ballot_sync(0xffffffffu, mine && is_b);
-                    blk = mine ? bq[0] : -1;
-                    if (mine) {
-                        ++p;
-#pragma unroll
-                        for (int d = 0; d + 1 < kPre; ++d) {
-                            q[d] = q[d + 1];
-                            bq[d] = bq[d + 1];
-                        }
-                        const int64_t n = p + kPre - 1;
-                        q[kPre - 1] = n < pe ? (uint32_t)list[n] : 0xFFFFFFFFu;
-                        bq[kPre - 1] = n < pe ? (is_b ? a.b_t_blk[n] : (int32_t)n) : -1;
-                    }
-                    if (am && bm) return true;
-                }
-            };
-            int32_t cur = -1, nxt = -1;
-            bool have = next_step(cur);
-            if (!have) {  // only blocks kept from the old C (beta != 0): one all-zero step
-                ok = put(t, kFirst | kLast, -1);
-                continue;
-            }
-            int32_t flags = kFirst;
-            while (have && ok) {
-                const bool more = next_step(nxt);
-                ok = put(t, flags | (more ? 0 : kLast), cur);
-                flags = 0;
-                cur = nxt;
-                have = more;
-            }
+            if (done) break;
         }
-        if (ok) put(0, kDone, -1);
     } else if (warp <= kCopyWarps) {
         // ------------------------------------------------------------ copy
         // warp 1 stages A's 5 blocks of every k-step, warp 2 B's: one bulk
         // copy of 4608 bytes per block (absent blocks from a zero block),
-        // completion counted in bytes on the stage's "full" barrier
+        // completion counted in bytes on the stage's "full" barrier.  The
+        // block indices of 32 k-steps come in with one load per lane.
         const int cw = warp - 1;
         const bool is_a = cw == 0;
-        const int s0 = 0, ns = kRB;
         const uint8_t *pk = is_a ? a.a_pack : a.b_pack;
         uint32_t st = 0, ph = 0, rs = 0, rph = 0;
         int64_t issued = 0;
@@ -560,39 +586,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
                 ok = false;
                 break;
             }
-            const Record &r = ctl.rec[rs];
-            const int32_t tile = r.tile, flags = r.flags;
-            const int32_t blk = lane < ns ? (is_a ? r.a[s0 + lane] : r.b[s0 + lane]) : -1;
+            const TileRec r = ctl.rec[rs];
             __syncwarp();
             if (lane == 0) mbar_arrive(saddr(&ctl.rec_empty[rs]));
             if (++rs == kRing) {
                 rs = 0;
                 rph ^= 1u;
             }
-            if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort))) {
-                if (lane == 0) fail(ctl, a.status);
-                ok = false;
+            if (r.tile < 0) {  // the end marker for the MMA lane
+                if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort))) {
+                    if (lane == 0) fail(ctl, a.status);
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) {
+                    if (is_a) ctl.smeta_f[st] = kDone;
+                    mbar_arrive(saddr(&ctl.full[st]));
+                }
                 break;
             }
-            if (lane == 0) {
-                if (cw == 0) {
-                    ctl.smeta_t[st] = tile;
-                    ctl.smeta_f[st] = flags;
+            for (int64_t base = r.s0; base < r.s1 && ok; base += 32) {
+                // lane l: the 5 block indices of this warp's operand for k-step base + l
+                int32_t f[kRB];
+                const int64_t sl = base + lane;
+#pragma unroll
+                for (int q = 0; q < kRB; ++q) f[q] = sl < r.s1 ? a.steps[sl * (kRB + kCB) + (is_a ? 0 : kRB) + q] : -1;
+                const int n = (int)(r.s1 - base < 32 ? r.s1 - base : 32);
+                for (int j = 0; j < n; ++j) {
+                    int32_t blk = -1;
+#pragma unroll
+                    for (int q = 0; q < kRB; ++q) {
+                        const int32_t x = __shfl_sync(0xffffffffu, f[q], j);
+                        if (lane == q) blk = x;
+                    }
+                    if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort))) {
+                        if (lane == 0) fail(ctl, a.status);
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        if (is_a) {
+                            const int64_t sidx = base + j;
+                            ctl.smeta_t[st] = r.tile;
+                            ctl.smeta_f[st] = (sidx == r.s0 ? kFirst : 0) | (sidx + 1 == r.s1 ? kLast : 0);
+                        }
+                        mbar_arrive_tx(saddr(&ctl.full[st]), kRB * kBlk);
+                    }
+                    __syncwarp();
+                    if (lane < kRB) {
+                        const void *src = blk >= 0 ? (const void *)(pk + (int64_t)blk * kBlk) : (const void *)a.zeros;
+                        bulk_copy(saddr(stages + st * kStageBytes + (is_a ? 0 : kOperand) + lane * kBlk), src, kBlk,
+                                  saddr(&ctl.full[st]));
+                    }
+                    ++issued;
+                    if (++st == kStages) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
-                if (flags & kDone) mbar_arrive(saddr(&ctl.full[st]));
-                else mbar_arrive_tx(saddr(&ctl.full[st]), ns * kBlk);
-            }
-            if (flags & kDone) break;
-            __syncwarp();
-            if (lane < ns) {
-                const void *src = blk >= 0 ? (const void *)(pk + (int64_t)blk * kBlk) : (const void *)a.zeros;
-                bulk_copy(saddr(stages + st * kStageBytes + (is_a ? 0 : kOperand) + (s0 + lane) * kBlk), src, kBlk,
-                          saddr(&ctl.full[st]));
-            }
-            ++issued;
-            if (++st == kStages) {
-                st = 0;
-                ph ^= 1u;
             }
         }
         if (!ok) {
@@ -736,6 +787,13 @@ cudaError_t launch_panel_tile_keys(int64_t ntiles, const int32_t *tile_g, const 
     if (ntiles == 0) return cudaSuccess;
     k_panel_tile_keys<<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(ntiles, tile_g, tile_h, sg, sh, ngc, keys,
                                                                        iota);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_panel_steps(const PanelArgs &a, int fill, int64_t *step_cnt, cudaStream_t s) {
+    if (a.n_tiles == 0) return cudaSuccess;
+    k_panel_steps<<<(unsigned)((a.n_tiles * 32 + 255) / 256), 256, 0, s>>>(a, fill, step_cnt);
     count_launch(1);
     return cudaGetLastError();
 }
