@@ -21,16 +21,19 @@
 // be computed inside the dense tile, so the launcher uses this kernel only
 // when the filter removed none.
 //
-// Roles in one persistent CTA per SM (12 warps):
-//   warp 0      merge: takes tiles from an atomic ticket and merges the five
-//               A rows' and five B columns' sorted block-index lists (each
-//               read 4 entries ahead, with the blocks they name) into k-step
-//               records in a shared ring;
+// The k-steps of every tile (a merge of its five A rows' and five B columns'
+// sorted block-index lists) are written beforehand by k_panel_steps, one warp
+// per tile, as records of 10 block indices.  Roles in one persistent CTA per
+// SM of the numeric kernel (12 warps):
+//   warp 0      tickets: takes tiles from an atomic ticket and hands each,
+//               with its range of k-step records, to the copy warps through a
+//               shared ring;
 //   warps 1, 2  copy: stage the 10 blocks of every k-step (warp 1 A's, warp 2
-//               B's), one bulk copy of 4608 bytes per block pre-packed in the
-//               tensor core's shared-memory layout (absent blocks from a zero
-//               block), completion counted in bytes on the stage's "full"
-//               barrier (4-stage ring);
+//               B's; the block indices of 32 k-steps per coalesced load), one
+//               bulk copy of 4608 bytes per block pre-packed in the tensor
+//               core's shared-memory layout (absent blocks from a zero block),
+//               completion counted in bytes on the stage's "full" barrier
+//               (4-stage ring);
 //   warp 3      allocates tensor memory; one lane issues the MMAs of a k-step
 //               into accumulator buffer b and commits them to the stage's
 //               "empty" barrier and, every third k-step, to the buffer's
