@@ -17,8 +17,8 @@
  *     C = alpha*A.B + beta*C;
  *   - the traversal loops over A's row-blocks and, for each, over the B
  *     blocks reachable from that row (Gustavson's row-by-row SpGEMM, §1.1);
- *   - a block product is performed only if the product of the two block
- *     norms exceeds the filter threshold (on-the-fly filtering, §2).
+ *   - a block product is skipped unless the two block norms multiplied
+ *     together are above the filter threshold (on-the-fly filtering, §2).
  *
  * Readings taken where the paper is silent:
  *   - block norm = Frobenius norm, accumulated as an fma chain x*x + n over
