@@ -141,7 +141,9 @@ bsm_status bsm_get_launch_count(int64_t *count);
  * bsm_get_variant returns the variant in effect.
  * Process-wide; the autotuner (paper_1708_03604_gb300/autotune.py) sets it
  * from measurements.  Applies to multiplies issued afterwards (a no-sync
- * multiply keeps the choice of its eager call). */
+ * multiply keeps the choice of its eager call).  BSM_P_TF32x3_PANEL has no
+ * variants (BSM_ERR_ARG); when it falls back to the BSM_P_TF32x3 kernel, that
+ * kernel uses the BSM_P_TF32x3 table. */
 bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant);
 bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant);
 

@@ -42,7 +42,11 @@ def _numeric_ms(A, B, eps, prec, reps, Cm):
 def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", reps: int = 3,
          gain: float = 0.01) -> dict:
     """Choose the variant of every output shape of A.B for `prec`; returns
-    {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}."""
+    {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}.  The
+    tcgen05 row-panel engine has no per-shape variants: tune "tf32x3" for the
+    kernel it falls back to."""
+    if prec == "tf32x3_panel":
+        raise ValueError("the tf32x3_panel engine has no per-shape variants")
     # larger shapes have one variant
     fp64 = prec in ("fp64", "fp64_dmma", "ozaki")  # lane variant = plain FP64 FMA
     shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16 or (fp64 and (m, n) in ((5, 5), (6, 6)))]
