@@ -70,3 +70,17 @@ def test_host_side_argument_errors_need_no_gpu(libbsm):
     o = bsm.Opts()
     o.prec = 99
     assert L.bsm_multiply(1.0, None, None, 0.0, None, 0.0, ctypes.byref(o)) == bsm.BSM_ERR_ARG
+
+
+def test_engine_query_and_variant_range_on_host(libbsm):
+    """The engine query and the variant table check their arguments on the
+    host; the panel precision has no variant table."""
+    from paper_1708_03604_gb300 import bsm
+    L = bsm.lib()
+    v = ctypes.c_int32()
+    assert L.bsm_get_engine(None, ctypes.byref(v)) == bsm.BSM_ERR_ARG
+    assert L.bsm_set_variant(bsm.BSM_P_TF32x3_PANEL, 4, 4, 1) == bsm.BSM_ERR_ARG
+    assert L.bsm_set_variant(bsm.BSM_P_TF32x3, 4, 4, 1) == bsm.BSM_OK
+    assert L.bsm_get_variant(bsm.BSM_P_TF32x3, 4, 4, ctypes.byref(v)) == bsm.BSM_OK and v.value == 1
+    assert L.bsm_set_variant(bsm.BSM_P_TF32x3, 4, 4, -1) == bsm.BSM_OK
+    assert L.bsm_get_variant(bsm.BSM_P_TF32x3, 4, 4, ctypes.byref(v)) == bsm.BSM_OK and v.value == 1
