@@ -25,8 +25,9 @@
  *     so both work (pageable, pinned or device memory).
  *   - Handles are not thread-safe; distinct handles may be used from
  *     distinct threads only with distinct streams.
- *   - Device memory owned by the library is allocated stream-ordered
- *     (cudaMallocAsync) on the library stream and freed the same way.
+ *   - Device memory owned by the library is allocated stream-ordered on the
+ *     library stream, from the device pool (cudaMallocAsync) or from the
+ *     hooks installed with bsm_set_allocator, and freed the same way.
  */
 #ifndef BSM_H
 #define BSM_H
@@ -57,7 +58,10 @@ typedef enum { BSM_FP64 = 0, BSM_FP32 = 1 } bsm_dtype;
  * final alpha/beta combination are FP64 for every choice). */
 typedef enum {
     BSM_P_FP64 = 0,       /* FP64 FMA (FP32 FMA for FP32 data), FP64 sum     */
-    BSM_P_FP64_DMMA = 1,  /* accepted; runs the FP64 FMA path (same FP64 pipe rate) */
+    BSM_P_FP64_DMMA = 1,  /* FP64 tensor-core MMA (mma.sync m8n8k4, FP64 accumulate)
+                             for output blocks of at least 8 x 8 elements, FP64 FMA
+                             for smaller ones; FP64 data (FP32 data runs the FMA
+                             path).  Same products and order of k as BSM_P_FP64. */
     BSM_P_TF32x3 = 2,     /* hi/lo TF32 split, 3 tensor-core products, FP32 accumulate, FP64 sum */
     BSM_P_BF16x3 = 3,     /* hi/lo BF16 split, 3 products                    */
     BSM_P_BF16x6 = 4,     /* hi/mid/lo BF16 split, 6 products                */
@@ -123,6 +127,63 @@ const char *bsm_last_error(void);
  * selects the legacy default stream). */
 bsm_status bsm_set_stream(void *stream);
 
+/*
+ * Device-memory provider (a library service; the paper has no counterpart:
+ * §2 only says that data is organised so that host-device transfers are
+ * few).  By default the library allocates
+ * from the device's stream-ordered pool (cudaMallocAsync / cudaFreeAsync on
+ * the library stream).  A framework that owns device memory (PyTorch's
+ * caching allocator, an arena) installs hooks instead:
+ *   alloc(bytes, stream, ctx) returns device memory that may be used in
+ *     stream order on `stream` (a cudaStream_t), or NULL on failure -- the
+ *     call that needed it then returns BSM_ERR_ALLOC after releasing what it
+ *     had taken;
+ *   free_fn(ptr, bytes, stream, ctx) takes back a block from alloc; the
+ *     library calls it after queueing the last work that touches ptr on
+ *     `stream`, so the provider may reuse ptr for later work on that stream
+ *     at once and for other streams only after synchronising with it (the
+ *     rule of cudaFreeAsync and of stream-aware caching allocators).
+ * Both hooks NULL restores the built-in pool; exactly one NULL is
+ * BSM_ERR_ARG.  Process-wide; blocks keep going back to the hooks that made
+ * them even after a change.  The hooks may be called from any library call
+ * that allocates (never from bsm_count_products_static) and must not call
+ * back into the library.
+ */
+typedef void *(*bsm_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*bsm_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+bsm_status bsm_set_allocator(bsm_alloc_fn alloc, bsm_free_fn free_fn, void *ctx);
+
+/* Limit, in seconds within [0, 2], of the waits in the main loop of the
+ * BSM_P_TF32x3_PANEL kernel (default 2).  A wait that runs out makes the
+ * multiply return BSM_ERR_TIMEOUT after every CTA has waited (at most 2 s)
+ * for its copies and tensor-core products in flight and freed its tensor
+ * memory, so the context stays usable.  Exists so that tests can make a wait
+ * run out on purpose (a limit of 0 gives up on the first wait that does not
+ * complete at once); process-wide. */
+bsm_status bsm_set_wait_limit(double seconds);
+
+/* Arithmetic units bsm_measure_peak can time. */
+enum {
+    BSM_U_FP64_FMA = 0,   /* FP64 fused multiply-add on the CUDA cores (DFMA)        */
+    BSM_U_FP64_MMA = 1,   /* FP64 tensor-core mma.sync m8n8k4 (DMMA)                 */
+    BSM_U_TF32_MMA = 2,   /* TF32 mma.sync m16n8k8, FP32 accumulate                  */
+    BSM_U_BF16_MMA = 3,   /* BF16 mma.sync m16n8k16, FP32 accumulate                 */
+    BSM_U_FP32_FMA = 4    /* FP32 fused multiply-add on the CUDA cores               */
+};
+
+/* Measured throughput of one arithmetic unit of the current GPU, the
+ * denominator of the numeric kernels' roofline fractions (a library service;
+ * the paper has no counterpart).  Runs a fixed-length loop of independent
+ * instruction chains, 4 CTAs of 256 threads per SM, `reps` timed launches
+ * (1..100) after one warm-up, CUDA events on the library stream; returns the
+ * best rate in FLOP/s (a fused multiply-add counts 2, an MMA 2*M*N*K).
+ * Synchronises the stream; allocates 16 bytes. */
+bsm_status bsm_measure_peak(int32_t unit, int32_t reps, double *flop_per_s);
+
+/* Number of blocks obtained from the installed hooks and not yet returned
+ * (0 when every handle holding hook memory has been destroyed). */
+bsm_status bsm_get_allocator_stats(int64_t *outstanding);
+
 /* 1: record per-phase CUDA-event timings in every multiply (bsm_get_timings). */
 bsm_status bsm_set_profiling(int32_t on);
 
@@ -146,6 +207,49 @@ bsm_status bsm_get_launch_count(int64_t *count);
  * kernel uses the BSM_P_TF32x3 table. */
 bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant);
 bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant);
+
+/*
+ * Launch shape and pass shape of the numeric kernels, per precision (the
+ * paper's GPU library finds kernel parameters per block shape by
+ * auto-tuning, §2; paper_1708_03604_gb300/autotune.py measures these and
+ * sets them).  value -1 restores the default.  Process-wide; applies to
+ * multiplies and adjoints issued afterwards (a no-sync multiply keeps the
+ * settings of its eager call only for sizes, not for these).
+ *   BSM_TUNE_CTA_WARPS   warps per CTA of the persistent kernel: 4 or 8 for
+ *                        BSM_P_TF32x3 / BF16x3 / BF16x6 / OZAKI (default 4);
+ *                        4 only for the FP64 kernels
+ *   BSM_TUNE_CTAS_PER_SM persistent CTAs per SM, 1..16, capped by what fits;
+ *                        0 = as many as fit (default)
+ *   BSM_TUNE_PASS_MT     fragment tiles along the output rows per pass over
+ *                        a block's products: split paths 1..2 (default 2,
+ *                        16-row tiles), FP64_DMMA 1..3 (default 3, 8-row tiles)
+ *   BSM_TUNE_PASS_NT     along the columns: split paths 1..3 (default 3,
+ *                        8-column tiles), OZAKI 1..2 (default 2), FP64_DMMA
+ *                        1..3 (default 3)
+ *   BSM_TUNE_FP64_BUILD  BSM_P_FP64 only: FP64 FMA kernel build, 0 chosen by
+ *                        the largest output block (default), 1 narrow (up to
+ *                        9 elements per lane per pass), 2 wide (up to 24);
+ *                        output blocks of at most 16 elements always run the
+ *                        small build
+ * Values outside these ranges are BSM_ERR_ARG.
+ */
+enum {
+    BSM_TUNE_CTA_WARPS = 0, BSM_TUNE_CTAS_PER_SM = 1, BSM_TUNE_PASS_MT = 2, BSM_TUNE_PASS_NT = 3,
+    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_COUNT = 5
+};
+bsm_status bsm_set_tuning(int32_t prec, int32_t param, int32_t value);
+bsm_status bsm_get_tuning(int32_t prec, int32_t param, int32_t *value);
+
+/* Numeric kernels (bsm_get_launch_config). */
+enum {
+    BSM_K_NONE = -1, BSM_K_FP64_CORES = 0, BSM_K_FP64_MMA = 1, BSM_K_SPLIT_MMA = 2, BSM_K_OZAKI_MMA = 3,
+    BSM_K_PANEL_TCGEN05 = 4
+};
+/* What the last numeric launch into C ran: cfg[0] kernel (BSM_K_*),
+ * cfg[1] FP64 kernel build (0 small, 1 narrow, 2 wide; -1 for the others),
+ * cfg[2] threads per CTA, cfg[3] CTAs, cfg[4] / cfg[5] fragment tiles per pass
+ * along rows / columns (0 where the kernel has no passes). */
+bsm_status bsm_get_launch_config(bsm_t C, int32_t *cfg);
 
 /* Fills `opts` with the defaults (FP64, no post filter, stacks built). */
 bsm_status bsm_opts_default(bsm_opts *opts);
@@ -329,8 +433,10 @@ bsm_status bsm_get_stacks(bsm_t C, int32_t *nshapes, int64_t *nprod, int32_t *sh
  * filter_eps > 0 it accepts nnzb(A) + nnzb(B) <= 2,097,152 and returns
  * BSM_ERR_CAPACITY beyond that.  The first call on each device looks the
  * array up (cudaGetSymbolAddress) and should come before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
- * streams, other threads) race on it.
+ * capture; the lookup is repeated when the device's CUDA context has
+ * changed (for instance after cudaDeviceReset, which reloads the module).
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race on it.
  */
 bsm_status bsm_count_products_static(bsm_t A, bsm_t B, double filter_eps, int64_t *prod_cnt,
                                      int64_t *cblk_cnt, int64_t *totals);

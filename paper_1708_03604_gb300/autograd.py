@@ -157,26 +157,32 @@ def block_pair_index(X, W, transpose_w: bool = False):
     transposed when transpose_w.  Host-side bookkeeping for losses."""
     xr, xc, xo = (np.asarray(v) for v in X.pattern())
     wr, wc, wo = (np.asarray(v) for v in W.pattern())
-    xrow = np.repeat(np.arange(len(xr) - 1), np.diff(xr))
-    wrow = np.repeat(np.arange(len(wr) - 1), np.diff(wr))
-    wpos = {(int(i), int(j)): q for q, (i, j) in enumerate(zip(wrow, wc))}
-    ix, iw = [], []
-    rbs, cbs = np.asarray(X.row_bs), np.asarray(X.col_bs)
-    for q, (i, j) in enumerate(zip(xrow, xc)):
-        key = (int(j), int(i)) if transpose_w else (int(i), int(j))
-        if key not in wpos:
-            continue
-        m, n = int(rbs[i]), int(cbs[j])
-        e = np.arange(m * n)
-        ix.append(xo[q] + e)
-        if transpose_w:
-            r, c = np.divmod(e, n)
-            iw.append(wo[wpos[key]] + c * m + r)
-        else:
-            iw.append(wo[wpos[key]] + e)
-    if not ix:
+    rbs, cbs = np.asarray(X.row_bs, np.int64), np.asarray(X.col_bs, np.int64)
+    nbc = max(len(cbs), len(rbs))
+    xrow = np.repeat(np.arange(len(xr) - 1, dtype=np.int64), np.diff(xr))
+    wrow = np.repeat(np.arange(len(wr) - 1, dtype=np.int64), np.diff(wr))
+    wkey = wrow * nbc + wc.astype(np.int64)          # ascending (CSR order)
+    xcol = xc.astype(np.int64)
+    xkey = xcol * nbc + xrow if transpose_w else xrow * nbc + xcol
+    pos = np.searchsorted(wkey, xkey)
+    hit = pos < len(wkey)
+    hit[hit] = wkey[pos[hit]] == xkey[hit]
+    if not hit.any():
         return (torch.zeros(0, dtype=torch.int64, device="cuda"),) * 2
-    return (torch.tensor(np.concatenate(ix), device="cuda"), torch.tensor(np.concatenate(iw), device="cuda"))
+    qx = np.nonzero(hit)[0]
+    m, n = rbs[xrow[qx]], cbs[xcol[qx]]
+    size = m * n
+    start = np.concatenate([[0], np.cumsum(size)[:-1]])
+    blk = np.repeat(np.arange(len(qx)), size)
+    e = np.arange(int(size.sum()), dtype=np.int64) - start[blk]     # element inside the block
+    ix = xo[qx][blk] + e
+    if transpose_w:
+        nn = n[blk]
+        r, c = e // nn, e % nn
+        iw = wo[pos[qx]][blk] + c * m[blk] + r
+    else:
+        iw = wo[pos[qx]][blk] + e
+    return torch.tensor(ix, device="cuda"), torch.tensor(iw, device="cuda")
 
 
 def trace_product(X: BlockSparseTensor, W: BlockSparseTensor) -> torch.Tensor:

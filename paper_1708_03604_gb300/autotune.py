@@ -1,28 +1,51 @@
-"""Autotuner of the numeric kernels' per-shape variants.
+"""Autotuner of the numeric kernels (the paper's GPU library finds its kernel
+parameters per block shape by auto-tuning, §2; this is the same idea over
+the knobs of this library's kernels).
 
-For every output block shape (m, n) that a multiply produces there are two
-ways to compute its block products:
+What it searches, per precision, by timing the numeric kernel (CUDA events
+recorded by the library around the launch) on the caller's operands:
 
-* variant 0: one warp per output block (FP64: lanes over its elements;
-  split paths: tensor-core MMAs on packed fragments);
-* variant 1, for blocks of at most 16 elements (FP64 also 5 x 5 and 6 x 6):
-  one lane per output block on CUDA cores (split paths: the same narrow
-  pieces multiplied with FP32 FMA).
+* per output block shape (m, n): the variant -- one warp per block (FP64:
+  lanes over its elements; split and Ozaki paths: tensor-core MMAs on packed
+  fragments) or, for blocks of at most 16 elements (FP64 and Ozaki also 5 x 5
+  and 6 x 6), one lane per block on the CUDA cores;
+* the FP64 FMA kernel build (how many output elements a lane holds per pass:
+  up to 9 or up to 24) -- BSM_P_FP64;
+* warps per CTA (4 or 8) of the persistent mma.sync kernels;
+* persistent CTAs per SM;
+* the fragment-tile pass shape (tiles along rows and columns that one pass
+  over a block's products covers) of the split, Ozaki and FP64-MMA kernels;
+* for the split paths, the interval F of the FP64 running sum (FP32
+  accumulation over at most F block products), the fastest F whose result is
+  within ``err_target`` (relative Frobenius) of the FP64 path on the same
+  operands.
 
-Which is faster depends on the shape and the product mix, so it is measured:
-starting from variant 0 everywhere, each shape in turn is switched to
-variant 1 and kept there if the numeric kernel (timed with CUDA events by
-the library) gets faster.  The table is process-wide in libbsm and can be
-saved to / loaded from JSON.
+Each knob is searched in turn (coordinate descent from the library
+defaults), a value kept only when it is faster by more than ``gain``.  The
+chosen table is process-wide in libbsm, saved to / loaded from JSON.
+
+Run as a module to tune the bench workloads and write a table:
+``python -m paper_1708_03604_gb300.autotune --workload mixed3000 --out t.json``.
 """
 from __future__ import annotations
 
+import argparse
 import json
 import statistics
 
 import numpy as np
 
 from . import bsm
+
+SPLIT = ("tf32x3", "bf16x3", "bf16x6")
+SEARCH = {
+    "fp64": [("fp64_build", [0, 1, 2]), ("ctas_per_sm", [0, 1, 2, 3, 4])],
+    "fp64_dmma": [("pass_mt", [3, 2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 4])],
+    "ozaki": [("cta_warps", [4, 8]), ("pass_nt", [2, 1]), ("ctas_per_sm", [0, 1, 2, 3])],
+}
+for _p in SPLIT:
+    SEARCH[_p] = [("cta_warps", [4, 8]), ("pass_mt", [2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 3, 4])]
+FLUSH_CANDIDATES = [-1, 1, 2, 4, 8, 16]
 
 
 def _shapes(A: bsm.Matrix, B: bsm.Matrix):
@@ -31,59 +54,97 @@ def _shapes(A: bsm.Matrix, B: bsm.Matrix):
     return sorted(((m, n) for m in ms for n in ns), key=lambda t: (t[0] * t[1], t))
 
 
-def _numeric_ms(A, B, eps, prec, reps, Cm):
+def _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=0):
     t = []
     for _ in range(reps):
-        bsm.multiply(1.0, A, B, 0.0, Cm, eps, prec=prec, build_stacks=False)
+        bsm.multiply(1.0, A, B, 0.0, Cm, eps, prec=prec, build_stacks=False, flush_every=flush_every)
         t.append(Cm.timings()["numeric"])
     return statistics.median(t)
 
 
+def reset(prec: str, sizes=()):
+    """Back to the library's defaults for `prec` (launch knobs, and the
+    variants of these block sizes)."""
+    for name, _ in SEARCH.get(prec, []):
+        bsm.bsm_set_tuning(prec, name, -1)
+    for m in sizes:
+        for n in sizes:
+            bsm.bsm_set_variant(prec, int(m), int(n), -1)
+
+
+def _rel_err(torch, x, ref):
+    return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
+
+
 def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", reps: int = 3,
-         gain: float = 0.01) -> dict:
-    """Choose the variant of every output shape of A.B for `prec`; returns
-    {"prec": ..., "variants": {"m x n": 0|1}, "numeric_ms": {...}}.  The
-    tcgen05 row-panel engine has no per-shape variants: tune "tf32x3" for the
-    kernel it falls back to."""
+         gain: float = 0.01, tune_flush: bool = True, err_target: float = 1e-6) -> dict:
+    """Choose the variants and launch knobs of `prec` for A.B; returns the
+    table (also left in effect in the library)."""
     if prec == "tf32x3_panel":
-        raise ValueError("the tf32x3_panel engine has no per-shape variants")
-    # larger shapes have one variant
-    fp64 = prec in ("fp64", "fp64_dmma", "ozaki")  # lane variant = plain FP64 FMA
-    shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16 or (fp64 and (m, n) in ((5, 5), (6, 6)))]
+        raise ValueError("the tf32x3_panel engine has no tuning knobs: tune 'tf32x3' for the kernel it falls back to")
+    fp64_like = prec in ("fp64", "fp64_dmma", "ozaki")  # lane variant = plain FP64 FMA
+    shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16 or (fp64_like and (m, n) in ((5, 5), (6, 6)))]
+    reset(prec)
     for m, n in shapes:
         bsm.bsm_set_variant(prec, m, n, 0)
     Cm = bsm.Matrix.empty(A.row_bs, B.col_bs)
     bsm.bsm_set_profiling(True)
     try:
         _numeric_ms(A, B, eps, prec, 1, Cm)  # warm-up
-        best = _numeric_ms(A, B, eps, prec, reps, Cm)
-        start = best
-        chosen = {}
+        start = best = _numeric_ms(A, B, eps, prec, reps, Cm)
+        variants = {}
         for m, n in shapes:
             bsm.bsm_set_variant(prec, m, n, 1)
             t = _numeric_ms(A, B, eps, prec, reps, Cm)
             if t < best * (1.0 - gain):
                 best = t
-                chosen[f"{m}x{n}"] = 1
+                variants[f"{m}x{n}"] = 1
             else:
                 bsm.bsm_set_variant(prec, m, n, 0)
-                chosen[f"{m}x{n}"] = 0
+                variants[f"{m}x{n}"] = 0
+        params = {}
+        for name, values in SEARCH.get(prec, []):
+            chosen = values[0]
+            bsm.bsm_set_tuning(prec, name, chosen)
+            for v in values[1:]:
+                bsm.bsm_set_tuning(prec, name, v)
+                t = _numeric_ms(A, B, eps, prec, reps, Cm)
+                if t < best * (1.0 - gain):
+                    best, chosen = t, v
+            bsm.bsm_set_tuning(prec, name, chosen)
+            params[name] = chosen
+        flush = None
+        flush_trials = {}
+        if tune_flush and prec in SPLIT:
+            import torch
+            ref = bsm.multiply(1.0, A, B, 0.0, None, eps, build_stacks=False).data_tensor()
+            fbest = None
+            for f in FLUSH_CANDIDATES:
+                t = _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=f)
+                err = _rel_err(torch, Cm.data_tensor_view(), ref)
+                flush_trials[str(f)] = {"numeric_ms": t, "rel_fro_err_vs_fp64_path": err}
+                if err <= err_target and (fbest is None or t < fbest[1]):
+                    fbest = (f, t)
+            if fbest is not None:
+                flush = fbest[0]
+                best = min(best, fbest[1])
+        tuned_ms = _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=flush or 0)
     finally:
         bsm.bsm_set_profiling(False)
-    return {"prec": prec, "variants": chosen, "numeric_ms": {"all_mma": start, "tuned": best}}
+    return {"prec": prec, "variants": variants, "params": params, "flush_every": flush,
+            "flush_trials": flush_trials, "numeric_ms": {"default": start, "tuned": tuned_ms},
+            "workload": {"nbr": int(len(A.row_bs)), "block_sizes": sorted(set(int(x) for x in np.asarray(A.row_bs))),
+                         "eps": eps}}
 
 
 def apply(table: dict):
-    for key, v in table["variants"].items():
+    """Put a table (from tune or load) into effect in the library."""
+    prec = table["prec"]
+    for key, v in table.get("variants", {}).items():
         m, n = (int(x) for x in key.split("x"))
-        bsm.bsm_set_variant(table["prec"], m, n, int(v))
-
-
-def reset(prec: str, sizes):
-    """Back to the library's default variants for these block sizes."""
-    for m in sizes:
-        for n in sizes:
-            bsm.bsm_set_variant(prec, int(m), int(n), -1)
+        bsm.bsm_set_variant(prec, m, n, int(v))
+    for name, v in table.get("params", {}).items():
+        bsm.bsm_set_tuning(prec, name, int(v))
 
 
 def save(tables, path: str):
@@ -92,8 +153,35 @@ def save(tables, path: str):
 
 
 def load(path: str):
+    """Load a table or a list of tables and put them into effect."""
     with open(path) as f:
         tables = json.load(f)
     for t in (tables if isinstance(tables, list) else [tables]):
         apply(t)
     return tables
+
+
+def main():
+    import torch
+    from . import inputs as I
+    p = argparse.ArgumentParser(description="tune the numeric kernels on a bench workload and write the table")
+    p.add_argument("--workload", default="mixed3000", choices=["mixed3000", "banded23_6912"])
+    p.add_argument("--nb", type=int, default=0, help="block rows/cols (default: the workload's)")
+    p.add_argument("--precs", default="fp64,ozaki,tf32x3,bf16x6,bf16x3,fp64_dmma")
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--out", required=True)
+    a = p.parse_args()
+    torch.cuda.set_device(0)
+    w = (I.mixed_banded(nb=a.nb or 3000) if a.workload == "mixed3000" else I.large_banded_23(nb=a.nb or 6912))
+    A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+    tables = []
+    for prec in a.precs.split(","):
+        t = tune(A, B, w["eps"], prec=prec, reps=a.reps)
+        t["workload"]["name"] = a.workload
+        tables.append(t)
+        print(json.dumps({k: t[k] for k in ("prec", "params", "flush_every", "numeric_ms")}), flush=True)
+    save(tables, a.out)
+
+
+if __name__ == "__main__":
+    main()

@@ -9,6 +9,7 @@ fallback: if libbsm.so is missing the first call raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 from types import SimpleNamespace
@@ -38,7 +39,9 @@ EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_lau
            "bsm_copy_data", "bsm_set_data", "bsm_data_ptr", "bsm_block_norms", "bsm_multiply",
            "bsm_multiply_backward", "bsm_get_counts", "bsm_get_timings", "bsm_get_products",
            "bsm_get_stacks", "bsm_add", "bsm_count_products_static", "bsm_borrow_data", "bsm_add_backward",
-           "bsm_get_status", "bsm_set_variant", "bsm_get_variant", "bsm_get_engine"]
+           "bsm_get_status", "bsm_set_variant", "bsm_get_variant", "bsm_get_engine", "bsm_set_allocator",
+           "bsm_get_allocator_stats", "bsm_measure_peak",
+           "bsm_set_wait_limit", "bsm_set_tuning", "bsm_get_tuning", "bsm_get_launch_config"]
 
 
 class BsmError(RuntimeError):
@@ -55,6 +58,13 @@ class Opts(C.Structure):
 _lib = None
 _vp, _i32, _i64, _f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _P = C.POINTER
+# device-memory hooks of bsm_set_allocator
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+# Every hook pair ever installed stays referenced here: the library returns
+# each block to the hooks that made it, even after another pair is installed,
+# so a released ctypes thunk would be called after it is gone.
+_hooks_alive: list = []
 
 
 def lib() -> C.CDLL:
@@ -96,13 +106,96 @@ def lib() -> C.CDLL:
         "bsm_count_products_static": ([_vp, _vp, _f64, _vp, _vp, _vp], _i32),
         "bsm_borrow_data": ([_vp, _vp], _i32),
         "bsm_add_backward": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
+        "bsm_set_allocator": ([ALLOC_FN, FREE_FN, _vp], _i32),
+        "bsm_get_allocator_stats": ([_P(_i64)], _i32),
+        "bsm_measure_peak": ([_i32, _i32, _P(_f64)], _i32),
+        "bsm_set_wait_limit": ([_f64], _i32),
+        "bsm_set_tuning": ([_i32, _i32, _i32], _i32),
+        "bsm_get_tuning": ([_i32, _i32, _P(_i32)], _i32),
+        "bsm_get_launch_config": ([_vp, _P(_i32)], _i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
         fn.argtypes = args
         fn.restype = res
     _lib = L
+    if os.environ.get("BSM_ALLOCATOR", "torch") == "torch":
+        use_torch_allocator()
     return L
+
+
+_exiting = False
+
+
+def _at_exit():
+    # handles destroyed while the interpreter shuts down leave their memory to
+    # the process exit instead of calling into a half-finalised torch
+    global _exiting
+    _exiting = True
+
+
+atexit.register(_at_exit)
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    import torch
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+    except Exception:   # out of memory: the library reports BSM_ERR_ALLOC
+        return None
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    if _exiting:
+        return
+    import torch
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def set_allocator(alloc=None, free=None):
+    """Install Python callables as the library's device-memory provider
+    (``alloc(nbytes, stream) -> int | None``, ``free(ptr, nbytes, stream)``);
+    no arguments restore the library's own stream-ordered pool."""
+    L = lib() if _lib is None else _lib
+    if alloc is None and free is None:
+        _check(L.bsm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        return
+    a = ALLOC_FN(lambda n, s, c: alloc(n, s))
+    f = FREE_FN(lambda p, n, s, c: free(p, n, s))
+    _hooks_alive.append((a, f, alloc, free))
+    _check(L.bsm_set_allocator(a, f, None))
+
+
+_torch_hooks = None
+
+
+def use_torch_allocator():
+    """Route every library allocation through PyTorch's caching allocator on
+    the library's stream (the default of this binding; BSM_ALLOCATOR=pool in
+    the environment keeps the library's own pool instead)."""
+    global _torch_hooks
+    if _torch_hooks is None:
+        _torch_hooks = (ALLOC_FN(_torch_alloc), FREE_FN(_torch_free))
+        _hooks_alive.append(_torch_hooks)
+    _check(_lib.bsm_set_allocator(_torch_hooks[0], _torch_hooks[1], None))
+
+
+def allocator_outstanding() -> int:
+    """Blocks the library holds from the installed hooks."""
+    n = _i64()
+    _check(lib().bsm_get_allocator_stats(C.byref(n)))
+    return n.value
+
+
+PEAK_UNITS = {"fp64_fma": 0, "fp64_mma": 1, "tf32_mma": 2, "bf16_mma": 3, "fp32_fma": 4}
+
+
+def measure_peak(unit: str, reps: int = 5) -> float:
+    """Measured FLOP/s of one arithmetic unit (PEAK_UNITS) on the current GPU."""
+    _sync_stream()
+    v = _f64()
+    _check(lib().bsm_measure_peak(PEAK_UNITS[unit], int(reps), C.byref(v)))
+    return v.value
 
 
 def _check(st: int):
@@ -208,6 +301,28 @@ def bsm_get_variant(prec, m: int, n: int) -> int:
     v = _i32()
     _check(lib().bsm_get_variant(PREC[prec] if isinstance(prec, str) else int(prec), int(m), int(n), C.byref(v)))
     return v.value
+
+
+TUNE_PARAMS = {"cta_warps": 0, "ctas_per_sm": 1, "pass_mt": 2, "pass_nt": 3, "fp64_build": 4}
+KERNEL_NAMES = {-1: "none", 0: "fp64_cores", 1: "fp64_mma", 2: "split_mma", 3: "ozaki_mma", 4: "panel_tcgen05"}
+
+
+def bsm_set_tuning(prec, param: str, value: int):
+    _check(lib().bsm_set_tuning(PREC[prec] if isinstance(prec, str) else int(prec), TUNE_PARAMS[param], int(value)))
+
+
+def bsm_get_tuning(prec, param: str) -> int:
+    v = _i32()
+    _check(lib().bsm_get_tuning(PREC[prec] if isinstance(prec, str) else int(prec), TUNE_PARAMS[param], C.byref(v)))
+    return v.value
+
+
+def bsm_get_launch_config(Cm: int) -> dict:
+    """What the last numeric launch into Cm ran."""
+    cfg = (C.c_int32 * 6)()
+    _check(lib().bsm_get_launch_config(Cm, cfg))
+    return {"kernel": KERNEL_NAMES.get(cfg[0], str(cfg[0])), "fp64_build": cfg[1], "cta_threads": cfg[2],
+            "grid": cfg[3], "pass_mt": cfg[4], "pass_nt": cfg[5]}
 
 
 def bsm_get_status(X: int) -> int:
@@ -328,6 +443,22 @@ class Matrix:
         _check(lib().bsm_copy_data(self.h, _ptr(t)))
         return t
 
+    def data_tensor_view(self):
+        """The handle's device data as a CUDA tensor without a copy (valid
+        while the handle keeps this storage: until its pattern is replaced or
+        it is destroyed)."""
+        import torch
+        inf = self.info()
+        if inf.data_len == 0:
+            return torch.empty(0, dtype=torch.float64 if inf.dtype == BSM_FP64 else torch.float32, device="cuda")
+
+        class _View:
+            pass
+        v = _View()
+        v.__cuda_array_interface__ = {"shape": (inf.data_len,), "typestr": "<f8" if inf.dtype == BSM_FP64 else "<f4",
+                                      "data": (self.data_ptr(), False), "version": 3, "strides": None}
+        return torch.as_tensor(v, device="cuda")
+
     def set_data(self, src):
         _sync_stream()
         _check(lib().bsm_set_data(self.h, _ptr(src)))
@@ -364,6 +495,9 @@ class Matrix:
     def engine(self) -> str:
         return bsm_get_engine(self.h)
 
+    def launch_config(self) -> dict:
+        return bsm_get_launch_config(self.h)
+
     def products(self):
         n = _i64()
         _check(lib().bsm_get_products(self.h, C.byref(n), None, None, None))
@@ -374,6 +508,18 @@ class Matrix:
             _sync_stream()
             _check(lib().bsm_get_products(self.h, C.byref(n), _ptr(a), _ptr(b), _ptr(c)))
         return SimpleNamespace(a=a, b=b, c=c)
+
+    def stack_shapes(self):
+        """Shapes (m, n, k) of the last multiply's stacks and the number of
+        products in each (the triples stay on the device)."""
+        ns, npr = _i32(), _i64()
+        _check(lib().bsm_get_stacks(self.h, C.byref(ns), C.byref(npr), None, None, None))
+        shapes = np.zeros((ns.value, 3), np.int32)
+        ptr = np.zeros(ns.value + 1, np.int64)
+        if ns.value:
+            _sync_stream()
+            _check(lib().bsm_get_stacks(self.h, C.byref(ns), C.byref(npr), _ptr(shapes), _ptr(ptr), None))
+        return shapes, np.diff(ptr)
 
     def stacks(self):
         ns, npr = _i32(), _i64()

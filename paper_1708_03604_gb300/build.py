@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbsm.so")
-SOURCES = ["bsm_api.cu", "k_symbolic.cu", "k_numeric.cu", "k_add.cu", "k_panel.cu", "bsm_static.cu"]
+SOURCES = ["bsm_api.cu", "k_symbolic.cu", "k_numeric.cu", "k_add.cu", "k_panel.cu", "bsm_static.cu", "k_probe.cu"]
 HEADERS = [os.path.join(CSRC, "bsm_internal.cuh"), os.path.join(ROOT, "include", "bsm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

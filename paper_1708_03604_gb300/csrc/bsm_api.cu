@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "bsm_internal.cuh"
@@ -20,6 +22,8 @@ thread_local std::string t_err;
 cudaStream_t g_stream = nullptr;
 bool g_prof = false;
 bool g_pool_configured = false;
+// limit of the panel kernel's main-loop waits (bsm_set_wait_limit)
+std::atomic<unsigned long long> g_wait_ns{2000000000ull};
 int64_t *g_host = nullptr;  // pinned host words for small device->host reads
 // numeric variant per (precision, rows, cols) of the output block; -1 = the
 // library default (see variant_of)
@@ -58,6 +62,45 @@ bool all_lane(int prec, const std::vector<int32_t> &rows, const std::vector<int3
     return true;
 }
 std::atomic<int64_t> g_launches{0};
+// launch and pass shape per precision (bsm_set_tuning); -1 = the default
+int32_t g_tune[7][BSM_TUNE_COUNT] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1},
+                                     {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1},
+                                     {-1, -1, -1, -1, -1}};
+// allowed range of a tuning value for a precision: [lo, hi], lo > hi = none
+void tune_range(int prec, int param, int *lo, int *hi) {
+    const bool split = prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6;
+    *lo = 1;
+    *hi = 0;
+    switch (param) {
+        case BSM_TUNE_CTA_WARPS:
+            if (split || prec == BSM_P_OZAKI) { *lo = 4; *hi = 8; }
+            else if (prec != BSM_P_TF32x3_PANEL) { *lo = 4; *hi = 4; }
+            break;
+        case BSM_TUNE_CTAS_PER_SM:
+            if (prec != BSM_P_TF32x3_PANEL) { *lo = 0; *hi = 16; }
+            break;
+        case BSM_TUNE_PASS_MT:
+            if (split) { *lo = 1; *hi = 2; }
+            else if (prec == BSM_P_FP64_DMMA) { *lo = 1; *hi = 3; }
+            break;
+        case BSM_TUNE_PASS_NT:
+            if (split || prec == BSM_P_FP64_DMMA) { *lo = 1; *hi = 3; }
+            else if (prec == BSM_P_OZAKI) { *lo = 1; *hi = 2; }
+            break;
+        case BSM_TUNE_FP64_BUILD:
+            if (prec == BSM_P_FP64) { *lo = 0; *hi = 2; }
+            break;
+    }
+}
+// the tuning of `prec` into the numeric launch arguments
+void apply_tuning(int prec, NumericArgs &na) {
+    const int32_t *t = g_tune[prec];
+    na.cta_warps = t[BSM_TUNE_CTA_WARPS] > 0 ? t[BSM_TUNE_CTA_WARPS] : 4;
+    na.ctas_per_sm = t[BSM_TUNE_CTAS_PER_SM] > 0 ? t[BSM_TUNE_CTAS_PER_SM] : 0;
+    na.pass_mt = t[BSM_TUNE_PASS_MT] > 0 ? t[BSM_TUNE_PASS_MT] : 0;
+    na.pass_nt = t[BSM_TUNE_PASS_NT] > 0 ? t[BSM_TUNE_PASS_NT] : 0;
+    na.fp64_build = t[BSM_TUNE_FP64_BUILD] > 0 ? t[BSM_TUNE_FP64_BUILD] : 0;
+}
 
 struct Scratch {
     std::vector<void *> ptrs;
@@ -656,6 +699,7 @@ bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const Panel
     pa.old_data = o.old_data; pa.old_off = o.old_off;
     pa.status = o.status;
     pa.work_counter = counter;
+    pa.wait_ns = panel_wait_ns();
     ev.mark(5);
     if ((st = cuda_check(launch_panel_numeric(pa, g_stream), "panel numeric"))) return st;
     ev.mark(6);
@@ -665,6 +709,7 @@ bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const Panel
 }  // namespace
 
 cudaStream_t stream() { return g_stream; }
+unsigned long long panel_wait_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 bool profiling() { return g_prof; }
@@ -680,9 +725,43 @@ bsm_status cuda_check(cudaError_t e, const char *what) {
                      std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Device memory provider: the built-in stream-ordered pool (cudaMallocAsync /
+// cudaFreeAsync on the library stream) unless bsm_set_allocator installed
+// hooks.  Every block obtained from hooks is remembered with its size and the
+// hooks that made it, so it goes back to them even if the provider changes.
+namespace {
+struct Provider {
+    bsm_alloc_fn alloc = nullptr;
+    bsm_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+struct HookBlock {
+    size_t bytes;
+    Provider prov;
+};
+std::mutex g_alloc_mu;
+Provider g_provider;
+std::unordered_map<void *, HookBlock> g_hook_blocks;
+}  // namespace
+
 bsm_status dalloc(void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    Provider prov;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        prov = g_provider;
+    }
+    if (prov.alloc) {
+        void *q = prov.alloc(bytes, static_cast<void *>(g_stream), prov.ctx);
+        if (!q)
+            return set_error(BSM_ERR_ALLOC, std::string("the installed allocator returned NULL for ") +
+                                                std::to_string(bytes) + " bytes");
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        g_hook_blocks[q] = HookBlock{bytes, prov};
+        *p = q;
+        return BSM_OK;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, g_stream);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -694,7 +773,25 @@ bsm_status dalloc(void **p, size_t bytes) {
 }
 
 void dfree(void *p) {
-    if (p) cudaFreeAsync(p, g_stream);
+    if (!p) return;
+    HookBlock hb{};
+    bool hooked = false;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        auto it = g_hook_blocks.find(p);
+        if (it != g_hook_blocks.end()) {
+            hb = it->second;
+            hooked = true;
+            g_hook_blocks.erase(it);
+        }
+    }
+    if (hooked) hb.prov.free(p, hb.bytes, static_cast<void *>(g_stream), hb.prov.ctx);
+    else cudaFreeAsync(p, g_stream);
+}
+
+int64_t hook_blocks_outstanding() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    return (int64_t)g_hook_blocks.size();
 }
 
 // --------------------------------------------------------------------------
@@ -811,6 +908,26 @@ bsm_status bsm_get_launch_count(int64_t *count) {
     return BSM_OK;
 }
 
+bsm_status bsm_set_allocator(bsm_alloc_fn alloc, bsm_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return set_error(BSM_ERR_ARG, "bsm_set_allocator needs both hooks or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_provider = Provider{alloc, free_fn, alloc ? ctx : nullptr};
+    return BSM_OK;
+}
+
+bsm_status bsm_set_wait_limit(double seconds) {
+    if (!(seconds >= 0.0 && seconds <= 2.0)) return set_error(BSM_ERR_ARG, "wait limit outside [0, 2] seconds");
+    g_wait_ns.store((unsigned long long)(seconds * 1e9), std::memory_order_relaxed);
+    return BSM_OK;
+}
+
+bsm_status bsm_get_allocator_stats(int64_t *outstanding) {
+    if (!outstanding) return set_error(BSM_ERR_ARG, "outstanding is NULL");
+    *outstanding = hook_blocks_outstanding();
+    return BSM_OK;
+}
+
 bsm_status bsm_set_profiling(int32_t on) {
     g_prof = on != 0;
     return BSM_OK;
@@ -848,6 +965,8 @@ static bsm_status create_common(bsm_t *out, int32_t nbr, int32_t nbc, const int3
     for (int32_t v : X->h_row_bs) X->max_bs_row = std::max(X->max_bs_row, v);
     for (int32_t v : X->h_col_bs) X->max_bs_col = std::max(X->max_bs_col, v);
     if ((st = dalloc_t(&X->row_bs, nbr)) || (st = dalloc_t(&X->col_bs, nbc))) {
+        dfree(X->row_bs);
+        dfree(X->col_bs);
         delete X;
         return st;
     }
@@ -1346,6 +1465,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     ev.mark(4);
 
     // ---- a5/a6: numeric
+    NumericLaunch nl{use_panel ? BSM_K_PANEL_TCGEN05 : BSM_K_NONE, -1, 0, 0, 0, 0};
     OzLines olA, olB;
     int32_t *order = nullptr;
     int64_t *n_marked = nullptr;
@@ -1424,8 +1544,9 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         na.y_plain = B == A ? xp : yp;
     }
     na.item_order = order;
+    apply_tuning(rprec, na);
     ev.mark(5);
-    if ((st = cuda_check(launch_numeric(na, g_stream), "numeric"))) return st;
+    if ((st = cuda_check(launch_numeric(na, g_stream, &nl), "numeric"))) return st;
     ev.mark(6);
     }
     if (no_sync) return BSM_OK;  // C's storage, counts and plan are unchanged
@@ -1454,6 +1575,8 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     C->triples = triples;
     C->prod_A = A; C->prod_B = B;
     C->prod_A_nnzb = A->nnzb; C->prod_B_nnzb = B->nnzb;
+    C->launch_cfg[0] = nl.kernel; C->launch_cfg[1] = nl.build; C->launch_cfg[2] = nl.cta_threads;
+    C->launch_cfg[3] = nl.grid; C->launch_cfg[4] = nl.pass_mt; C->launch_cfg[5] = nl.pass_nt;
     C->engine = nnzbC == 0 ? BSM_E_NONE
                 : use_panel ? BSM_E_PANEL_TCGEN05
                 : kprec == BSM_P_OZAKI ? BSM_E_OZAKI_MMA
@@ -1637,6 +1760,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
             na.y_plain = yp;
         }
         na.item_order = item_order;
+        apply_tuning(opts.prec, na);
         if ((st = cuda_check(launch_numeric(na, g_stream), "adjoint numeric"))) return st;
     }
     return BSM_OK;
@@ -1818,6 +1942,33 @@ bsm_status bsm_add_backward(bsm_t Z, const void *dZ_data, bsm_t X, bsm_t Y, void
         e = launch_add_backward(Z->nnzb, Z->blk_off, Z->blk_rc, Z->add_xsrc, Z->add_ysrc, Z->add_a, Z->add_b, dZ_data,
                                 dX_data, dY_data, Z->dtype, g_stream);
     return cuda_check(e, "add backward");
+}
+
+bsm_status bsm_set_tuning(int32_t prec, int32_t param, int32_t value) {
+    if (prec < BSM_P_FP64 || prec > BSM_P_TF32x3_PANEL) return set_error(BSM_ERR_ARG, "prec out of range");
+    if (param < 0 || param >= BSM_TUNE_COUNT) return set_error(BSM_ERR_ARG, "unknown tuning parameter");
+    int lo, hi;
+    tune_range(prec, param, &lo, &hi);
+    if (lo > hi) return set_error(BSM_ERR_ARG, "this precision has no such tuning parameter");
+    if (value != -1 && (value < lo || value > hi)) return set_error(BSM_ERR_ARG, "tuning value out of range");
+    if (param == BSM_TUNE_CTA_WARPS && value != -1 && value != 4 && value != 8)
+        return set_error(BSM_ERR_ARG, "warps per CTA must be 4 or 8");
+    g_tune[prec][param] = value;
+    return BSM_OK;
+}
+
+bsm_status bsm_get_tuning(int32_t prec, int32_t param, int32_t *value) {
+    if (!value) return set_error(BSM_ERR_ARG, "value is NULL");
+    if (prec < BSM_P_FP64 || prec > BSM_P_TF32x3_PANEL) return set_error(BSM_ERR_ARG, "prec out of range");
+    if (param < 0 || param >= BSM_TUNE_COUNT) return set_error(BSM_ERR_ARG, "unknown tuning parameter");
+    *value = g_tune[prec][param];
+    return BSM_OK;
+}
+
+bsm_status bsm_get_launch_config(bsm_t C, int32_t *cfg) {
+    if (!C || !cfg) return set_error(BSM_ERR_ARG, "NULL argument");
+    for (int q = 0; q < 6; ++q) cfg[q] = C->launch_cfg[q];
+    return BSM_OK;
 }
 
 bsm_status bsm_set_variant(int32_t prec, int32_t m, int32_t n, int32_t variant) {

@@ -97,8 +97,10 @@ struct bsm_mat {
     // first global row / column of every block row / column ([nbr+1], [nbc+1];
     // built on demand, kept until the handle is destroyed)
     int32_t *row_start = nullptr, *col_start = nullptr;
-    // numeric engine of the last multiply into this matrix (bsm_engine)
+    // numeric engine of the last multiply into this matrix (bsm_engine) and
+    // what its numeric launch ran (bsm_get_launch_config)
     int32_t engine = -1;
+    int32_t launch_cfg[6] = {-1, -1, 0, 0, 0, 0};
     // row-panel tiling of this matrix as the left operand of a multiply with
     // panel_B (built on demand, dropped with the pattern): block rows in
     // ord_r order, the right operand's block columns in ord_c order (pos_c
@@ -265,8 +267,19 @@ struct NumericArgs {
     // Ozaki path: biased FP64 exponent field of the largest |x| of every global
     // line (logical rows of X, logical columns of Y) and the first line of every block
     const int32_t *x_exp, *x_line0, *y_exp, *y_line0;
+    // launch shape and pass caps (bsm_set_tuning; 0 = the kernel's default)
+    int32_t pass_mt, pass_nt;   // fragment tiles per pass along M / N
+    int32_t cta_warps;          // warps per CTA (4 or 8; mma.sync kernels)
+    int32_t ctas_per_sm;        // persistent CTAs per SM (0: as many as fit)
+    int32_t fp64_build;         // FP64 FMA kernel build: 0 by the largest block, 1 narrow, 2 wide
 };
-cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s);
+// What a numeric launch ran (bsm_get_launch_config).
+struct NumericLaunch {
+    int32_t kernel;     // BSM_K_* of include/bsm.h
+    int32_t build;      // FP64 FMA kernel build (0 small, 1 narrow, 2 wide) or -1
+    int32_t cta_threads, grid, pass_mt, pass_nt;
+};
+cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *info = nullptr);
 
 // Ozaki path: line0[b] = first global line of block b, lines being the stored
 // rows (by_rows) or the stored columns of M's blocks; exps[line] = max biased
@@ -379,7 +392,11 @@ struct PanelArgs {
     const void *old_data; const int64_t *old_off;  // beta != 0: old values (or null)
     int32_t *status;                      // set to BSM_ERR_TIMEOUT when a wait gives up
     unsigned long long *work_counter;     // zeroed by the caller
+    unsigned long long wait_ns;           // limit of the main-loop waits (the drain of
+                                          // work in flight always allows 2 s)
 };
+// limit of the panel kernel's main-loop waits (bsm_set_wait_limit)
+unsigned long long panel_wait_ns();
 int64_t panel_pack_bytes(int64_t nblk);
 int panel_slot();
 int panel_tile_rows();

@@ -27,10 +27,47 @@ constexpr int kThreads = 256;
 
 static __device__ __align__(256) double g_static_norms[kStaticNormCapacity];
 
-// Host copy of each device's address of g_static_norms, filled on the first
-// call made while that device is current.  In host code the name
-// g_static_norms is only a stand-in for the symbol, never a device address.
-double *g_static_norms_addr[kMaxDevices] = {};
+// Host copy of each device's address of g_static_norms, with the id of the
+// CUDA context it was looked up in.  In host code the name g_static_norms is
+// only a stand-in for the symbol, never a device address.  The address is
+// looked up again when the current context is not the recorded one (after
+// cudaDeviceReset the primary context is re-created and the module reloaded,
+// so the array may move), and on every call when the context id cannot be
+// read.
+struct StaticAddr {
+    double *addr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+StaticAddr g_static_norms_addr[kMaxDevices];
+
+// Id of the current CUDA context (0 if there is none or it cannot be read),
+// through the driver entry points the runtime exposes, so the library does
+// not link the driver library itself.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        cudaGetLastError();
+    }
+    if (!get_cur || !get_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != 0 || !ctx) return 0;
+    if (get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -91,19 +128,22 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Device address of the static scratch for the current device.
+// Device address of the static scratch for the current device (and context).
 bsm_status static_norms(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return set_error(BSM_ERR_UNSUPPORTED, "device index above 63");
-    if (!g_static_norms_addr[dev]) {
+    StaticAddr &sa = g_static_norms_addr[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!sa.addr || id == 0 || id != sa.ctx_id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_norms);
         if (e != cudaSuccess) return cuda_check(e, "cudaGetSymbolAddress of the static norm scratch");
-        g_static_norms_addr[dev] = static_cast<double *>(p);
+        sa.addr = static_cast<double *>(p);
+        sa.ctx_id = current_ctx_id();  // the lookup made the device's context current
     }
-    *out = g_static_norms_addr[dev];
+    *out = sa.addr;
     return BSM_OK;
 }
 

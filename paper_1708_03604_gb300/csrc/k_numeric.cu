@@ -28,8 +28,9 @@ namespace bsm {
 
 namespace {
 
-constexpr int kWarpsPerCta = 4;
+constexpr int kWarpsPerCta = 4;             // default warps per CTA
 constexpr int kThreadsNum = kWarpsPerCta * 32;
+constexpr int kMaxThreadsTc = 8 * 32;        // the mma.sync kernels take 4 or 8 warps per CTA
 
 // =====================================================================
 // CUDA-core path
@@ -326,6 +327,141 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
 }
 
 // =====================================================================
+// FP64 tensor-core path (BSM_P_FP64_DMMA): mma.sync m8n8k4 with FP64
+// operands and accumulators.  Fragment layout of m8n8k4 (lane = 4 g + t4):
+// A (8 x 4, row) holds X(g, t4); B (4 x 8, col) holds Y(t4, g); the
+// accumulator holds D(g, 2 t4) and D(g, 2 t4 + 1).  One warp per output
+// block; blocks of at least 8 x 8 elements run here, in passes of up to
+// 3 x 3 tiles of 8 x 8 (24 x 24 elements), every block product in ascending
+// k steps of 4 with zero padding past the block edges.  Smaller output
+// blocks run the FP64 FMA code.
+// =====================================================================
+__device__ __forceinline__ void dmma(double (&d)[2], double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(d[0]), "+d"(d[1])
+                 : "d"(a), "d"(b));
+}
+
+template <int MTC, int NTC>
+__device__ __forceinline__ void dmma_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0) {
+    const double *__restrict__ X = static_cast<const double *>(a.x_data);
+    const double *__restrict__ Y = static_cast<const double *>(a.y_data);
+    const int32_t orc = a.out_blk_rc[q];
+    const int R = rc_rows(orc), S = rc_cols(orc);
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    const int g = lane >> 2, t4 = lane & 3;
+    double acc[MTC][NTC][2];
+#pragma unroll
+    for (int i = 0; i < MTC; ++i)
+#pragma unroll
+        for (int j = 0; j < NTC; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+    // rows of X and columns of Y this lane loads (clamped reads are masked)
+    int xr[MTC], ys[NTC];
+    bool xv[MTC], yv[NTC];
+#pragma unroll
+    for (int i = 0; i < MTC; ++i) {
+        xr[i] = (mt0 + i) * 8 + g;
+        xv[i] = xr[i] < R;
+    }
+#pragma unroll
+    for (int j = 0; j < NTC; ++j) {
+        ys[j] = (nt0 + j) * 8 + g;
+        yv[j] = ys[j] < S;
+    }
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t ix = a.px[p], iy = a.py[p];
+        const double *xb = X + a.x_blk_off[ix];
+        const double *yb = Y + a.y_blk_off[iy];
+        const int32_t xrc = a.x_blk_rc[ix];
+        const int Tn = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+        const int xs_r = a.x_trans ? 1 : Tn, xs_t = a.x_trans ? R : 1;
+        const int ys_t = a.y_trans ? 1 : S, ys_s = a.y_trans ? Tn : 1;
+        for (int t0 = 0; t0 < Tn; t0 += 4) {
+            const int t = t0 + t4;
+            const bool tv = t < Tn;
+            double fa[MTC], fb[NTC];
+#pragma unroll
+            for (int i = 0; i < MTC; ++i) fa[i] = (tv && xv[i]) ? __ldg(xb + xr[i] * xs_r + t * xs_t) : 0.0;
+#pragma unroll
+            for (int j = 0; j < NTC; ++j) fb[j] = (tv && yv[j]) ? __ldg(yb + t * ys_t + ys[j] * ys_s) : 0.0;
+#pragma unroll
+            for (int i = 0; i < MTC; ++i)
+#pragma unroll
+                for (int j = 0; j < NTC; ++j) dmma(acc[i][j], fa[i], fb[j]);
+        }
+    }
+    double *O = static_cast<double *>(a.out_data);
+    const double *OLD = static_cast<const double *>(a.old_data);
+    const int64_t out_off = a.out_blk_off[q];
+    const int64_t old = (a.beta != 0.0 && a.old_off) ? a.old_off[q] : -1;
+#pragma unroll
+    for (int i = 0; i < MTC; ++i)
+#pragma unroll
+        for (int j = 0; j < NTC; ++j)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int r = (mt0 + i) * 8 + g, c = (nt0 + j) * 8 + 2 * t4 + v;
+                if (r < R && c < S) {
+                    const int64_t e = (int64_t)r * S + c;
+                    double val = a.alpha * acc[i][j][v];
+                    if (old >= 0) val = fma(a.beta, OLD[old + e], val);
+                    O[out_off + e] = val;
+                }
+            }
+}
+
+__device__ __forceinline__ void dmma_item(const NumericArgs &a, int64_t q, int lane) {
+    const int32_t orc = a.out_blk_rc[q];
+    const int MT = (rc_rows(orc) + 7) >> 3, NT = (rc_cols(orc) + 7) >> 3;
+    const int pm = a.pass_mt > 0 ? a.pass_mt : 3, pn = a.pass_nt > 0 ? a.pass_nt : 3;
+    for (int mt0 = 0; mt0 < MT; mt0 += pm) {
+        const int mtc = min(pm, MT - mt0);
+        for (int nt0 = 0; nt0 < NT; nt0 += pn) {
+            const int ntc = min(pn, NT - nt0);
+            switch (mtc * 4 + ntc) {
+                case 5: dmma_pass<1, 1>(a, q, lane, mt0, nt0); break;
+                case 6: dmma_pass<1, 2>(a, q, lane, mt0, nt0); break;
+                case 7: dmma_pass<1, 3>(a, q, lane, mt0, nt0); break;
+                case 9: dmma_pass<2, 1>(a, q, lane, mt0, nt0); break;
+                case 10: dmma_pass<2, 2>(a, q, lane, mt0, nt0); break;
+                case 11: dmma_pass<2, 3>(a, q, lane, mt0, nt0); break;
+                case 13: dmma_pass<3, 1>(a, q, lane, mt0, nt0); break;
+                case 14: dmma_pass<3, 2>(a, q, lane, mt0, nt0); break;
+                default: dmma_pass<3, 3>(a, q, lane, mt0, nt0); break;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_dmma(NumericArgs a) {
+    const int lane = threadIdx.x & 31;
+    if (a.status && *a.status != 0) return;
+    unsigned long long *ctr = a.work_counter;
+    const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
+    const int64_t n0 = a.n_items - n_lane;
+    const int64_t tickets = n0 + (n_lane + 31) / 32;
+    while (true) {
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= tickets) break;
+        if (t < n0) {
+            int64_t q = t;
+            if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            const int32_t orc = a.out_blk_rc[q];
+            if (rc_rows(orc) >= 8 && rc_cols(orc) >= 8) dmma_item(a, q, lane);
+            else cc_dispatch<double, kCcNarrow>(a, q, lane);
+        } else {
+            const int64_t idx = n0 + (t - n0) * 32 + lane;
+            if (idx < a.n_items) {
+                const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
+                cc_lane_dispatch<double, kCcNarrow>(a, q);
+            }
+        }
+    }
+}
+
+// =====================================================================
 // Tensor-core split path
 // =====================================================================
 // Packed fragment planes.  For a logical R x T operand in role X (mma "A"
@@ -590,10 +726,11 @@ template <int PREC, bool FF>
 __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
-    for (int mt0 = 0; mt0 < MT; mt0 += 2) {
-        const int mtc = min(2, MT - mt0);
-        for (int nt0 = 0; nt0 < NT; nt0 += 3) {
-            const int ntc = min(3, NT - nt0);
+    const int pm = a.pass_mt > 0 ? a.pass_mt : 2, pn = a.pass_nt > 0 ? a.pass_nt : 3;
+    for (int mt0 = 0; mt0 < MT; mt0 += pm) {
+        const int mtc = min(pm, MT - mt0);
+        for (int nt0 = 0; nt0 < NT; nt0 += pn) {
+            const int ntc = min(pn, NT - nt0);
             if (mtc == 1) {
                 switch (ntc) {
                     case 1: tc_pass<PREC, 1, 1, FF>(a, q, lane, mt0, nt0, ring); break;
@@ -809,7 +946,7 @@ __device__ __forceinline__ void cs_lane_dispatch(const NumericArgs &a, int64_t q
 }
 
 template <int PREC, bool FF>
-__global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
+__global__ void __launch_bounds__(kMaxThreadsTc) k_numeric_tc(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t tc_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC>();
@@ -1082,16 +1219,17 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
 __device__ __forceinline__ void oz_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
+    const int pn = a.pass_nt == 1 ? 1 : 2;
     for (int mt0 = 0; mt0 < MT; ++mt0)
-        for (int nt0 = 0; nt0 < NT; nt0 += 2) {
-            if (NT - nt0 >= 2) oz_pass<2>(a, q, lane, mt0, nt0, ring);
+        for (int nt0 = 0; nt0 < NT; nt0 += pn) {
+            if (pn == 2 && NT - nt0 >= 2) oz_pass<2>(a, q, lane, mt0, nt0, ring);
             else oz_pass<1>(a, q, lane, mt0, nt0, ring);
         }
 }
 
 // Items [0, n0): a warp each on the tensor cores; items [n0, n_items): tiny
 // blocks one per lane with plain FP64 FMA (exact enough, no slicing needed).
-__global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
+__global__ void __launch_bounds__(kMaxThreadsTc) k_numeric_oz(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t oz_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ring = oz_smem + warp * oz_ring_words_per_warp();
@@ -1409,71 +1547,95 @@ int num_sms() {
 }
 
 template <typename K>
-int persistent_grid(K kernel, int64_t n_items, size_t smem = 0) {
+int persistent_grid(K kernel, int64_t n_items, size_t smem = 0, int threads = kThreadsNum, int ctas_per_sm = 0) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreadsNum, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     if (per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int64_t g = (int64_t)num_sms() * per_sm;
-    const int64_t need = (n_items + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int warps = threads / 32;
+    const int64_t need = (n_items + warps - 1) / warps;
     if (g > need) g = need;
     if (g < 1) g = 1;
     return (int)g;
 }
 
 template <typename T, int BUILD>
-void launch_cc(const NumericArgs &a, cudaStream_t s) {
-    k_numeric_cc<T, BUILD><<<persistent_grid(k_numeric_cc<T, BUILD>, a.n_items), kThreadsNum, 0, s>>>(a);
+int launch_cc(const NumericArgs &a, cudaStream_t s) {
+    const int g = persistent_grid(k_numeric_cc<T, BUILD>, a.n_items, 0, kThreadsNum, a.ctas_per_sm);
+    k_numeric_cc<T, BUILD><<<g, kThreadsNum, 0, s>>>(a);
+    return g;
 }
 
 template <int PREC, bool FF>
-cudaError_t launch_tc_ff(const NumericArgs &a, cudaStream_t s) {
-    const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC>() * kWarpsPerCta;
+cudaError_t launch_tc_ff(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
+    const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC>() * (threads / 32);
     cudaError_t e = cudaFuncSetAttribute(k_numeric_tc<PREC, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_numeric_tc<PREC, FF><<<persistent_grid(k_numeric_tc<PREC, FF>, a.n_items, smem), kThreadsNum, smem, s>>>(a);
+    *grid = persistent_grid(k_numeric_tc<PREC, FF>, a.n_items, smem, threads, a.ctas_per_sm);
+    k_numeric_tc<PREC, FF><<<*grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int PREC>
-cudaError_t launch_tc(const NumericArgs &a, cudaStream_t s) {
-    return a.flush_every > 0 ? launch_tc_ff<PREC, false>(a, s) : launch_tc_ff<PREC, true>(a, s);
+cudaError_t launch_tc(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
+    return a.flush_every > 0 ? launch_tc_ff<PREC, false>(a, s, threads, grid)
+                             : launch_tc_ff<PREC, true>(a, s, threads, grid);
 }
 
 }  // namespace
 
-cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s) {
+cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *info) {
+    NumericLaunch li{BSM_K_NONE, -1, 0, 0, 0, 0};
+    if (info) *info = li;
     if (a.n_items == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const bool tc = a.prec == BSM_P_TF32x3 || a.prec == BSM_P_BF16x3 || a.prec == BSM_P_BF16x6;
+    const int tc_threads = (a.cta_warps == 8 ? 8 : 4) * 32;
+    int grid = 0;
     if (a.prec == BSM_P_OZAKI) {
-        const size_t smem = sizeof(uint32_t) * (size_t)oz_ring_words_per_warp() * kWarpsPerCta;
+        const size_t smem = sizeof(uint32_t) * (size_t)oz_ring_words_per_warp() * (tc_threads / 32);
         e = cudaFuncSetAttribute(k_numeric_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_numeric_oz<<<persistent_grid(k_numeric_oz, a.n_items, smem), kThreadsNum, smem, s>>>(a);
+        if (e == cudaSuccess) {
+            grid = persistent_grid(k_numeric_oz, a.n_items, smem, tc_threads, a.ctas_per_sm);
+            k_numeric_oz<<<grid, tc_threads, smem, s>>>(a);
+        }
+        li = NumericLaunch{BSM_K_OZAKI_MMA, -1, tc_threads, grid, 1, a.pass_nt == 1 ? 1 : 2};
+    } else if (a.prec == BSM_P_FP64_DMMA && a.dtype == BSM_FP64) {
+        grid = persistent_grid(k_numeric_dmma, a.n_items, 0, kThreadsNum, a.ctas_per_sm);
+        k_numeric_dmma<<<grid, kThreadsNum, 0, s>>>(a);
+        li = NumericLaunch{BSM_K_FP64_MMA, -1, kThreadsNum, grid, a.pass_mt > 0 ? a.pass_mt : 3,
+                           a.pass_nt > 0 ? a.pass_nt : 3};
     } else if (!tc) {
         // the build by the largest output block: all within one narrow pass
         // (<= 288 elements) or beyond the wide ladder's single pass (> 768)
-        // run narrow -- measured faster there -- the rest wide
+        // run narrow -- measured faster there -- the rest wide; the tuner may
+        // ask for narrow or wide instead (the small build only ever runs when
+        // every output block has at most 16 elements)
         const int area = a.max_out_rows * a.max_out_cols;
-        const int build = (area > 0 && area <= 16) ? kCcSmall : (area <= 288 || area > 768) ? kCcNarrow : kCcWide;
+        int build = (area > 0 && area <= 16) ? kCcSmall : (area <= 288 || area > 768) ? kCcNarrow : kCcWide;
+        if (a.fp64_build == 1 && build != kCcSmall) build = kCcNarrow;
+        if (a.fp64_build == 2 && build != kCcSmall) build = kCcWide;
         if (a.dtype == BSM_FP64) {
-            if (build == kCcSmall) launch_cc<double, kCcSmall>(a, s);
-            else if (build == kCcNarrow) launch_cc<double, kCcNarrow>(a, s);
-            else launch_cc<double, kCcWide>(a, s);
+            if (build == kCcSmall) grid = launch_cc<double, kCcSmall>(a, s);
+            else if (build == kCcNarrow) grid = launch_cc<double, kCcNarrow>(a, s);
+            else grid = launch_cc<double, kCcWide>(a, s);
         } else {
-            if (build == kCcSmall) launch_cc<float, kCcSmall>(a, s);
-            else if (build == kCcNarrow) launch_cc<float, kCcNarrow>(a, s);
-            else launch_cc<float, kCcWide>(a, s);
+            if (build == kCcSmall) grid = launch_cc<float, kCcSmall>(a, s);
+            else if (build == kCcNarrow) grid = launch_cc<float, kCcNarrow>(a, s);
+            else grid = launch_cc<float, kCcWide>(a, s);
         }
-    } else if (a.prec == BSM_P_TF32x3) {
-        e = launch_tc<BSM_P_TF32x3>(a, s);
-    } else if (a.prec == BSM_P_BF16x3) {
-        e = launch_tc<BSM_P_BF16x3>(a, s);
+        li = NumericLaunch{BSM_K_FP64_CORES, build, kThreadsNum, grid, 0, 0};
     } else {
-        e = launch_tc<BSM_P_BF16x6>(a, s);
+        if (a.prec == BSM_P_TF32x3) e = launch_tc<BSM_P_TF32x3>(a, s, tc_threads, &grid);
+        else if (a.prec == BSM_P_BF16x3) e = launch_tc<BSM_P_BF16x3>(a, s, tc_threads, &grid);
+        else e = launch_tc<BSM_P_BF16x6>(a, s, tc_threads, &grid);
+        li = NumericLaunch{BSM_K_SPLIT_MMA, -1, tc_threads, grid, a.pass_mt > 0 ? a.pass_mt : 2,
+                           a.pass_nt > 0 ? a.pass_nt : 3};
     }
     if (e != cudaSuccess) return e;
+    if (info) *info = li;
     count_launch(1);
     return cudaGetLastError();
 }

@@ -42,9 +42,11 @@
 //               of the tile) and one half of its columns, reads the buffer
 //               into registers, frees it, adds it into the compensated pair,
 //               and on a tile's last k-step writes C.
-// Every wait is bounded (2 s); a wait that runs out sets the output's status
-// word to BSM_ERR_TIMEOUT, every role then leaves its loop, waits for its own
-// copies and MMAs in flight, and the tensor memory is freed.
+// Every wait is bounded (2 s by default; the main-loop waits take
+// PanelArgs::wait_ns, which tests shorten to make a wait run out); a wait that
+// runs out sets the output's status word to BSM_ERR_TIMEOUT, every role then
+// leaves its loop, waits (bounded by the full 2 s) for its own copies and MMAs
+// in flight, and the tensor memory is freed.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -127,20 +129,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const int32_t *abort) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const int32_t *abort,
+                                          unsigned long long limit_ns = kWaitNs) {
     // each try_wait suspends the thread (no issue slots taken) until the
-    // phase completes or the hinted 20 us pass
+    // phase completes or the hinted time (20 us, less under a shorter limit)
+    // passes
+    const uint32_t hint = limit_ns < 20000ull ? (uint32_t)limit_ns : 20000u;
     const unsigned long long t0 = global_ns();
     for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(mbar), "r"(parity), "r"(20000)
+            : "r"(mbar), "r"(parity), "r"(hint)
             : "memory");
         if (ok) return true;
         if (*(volatile const int32_t *)abort) return false;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -437,7 +442,7 @@ __device__ __forceinline__ void drain(const PanelArgs &a, SmemCtl &ctl, uint32_t
     uint32_t buf = 0, bph = 0;
     bool ok = !dead;
     while (ok) {
-        if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.accf[buf]), bph, &ctl.abort))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.accf[buf]), bph, &ctl.abort, a.wait_ns))) {
             if (lane == 0) fail(ctl, a.status);
             break;
         }
@@ -549,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
             if (lane == 0) tk = (int64_t)atomicAdd(a.work_counter, 1ull);
             tk = __shfl_sync(0xffffffffu, tk, 0);
             const bool done = !ok || tk >= a.n_tiles || *(volatile int32_t *)&ctl.abort;
-            if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.rec_empty[rs]), rph ^ 1u, &ctl.abort))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.rec_empty[rs]), rph ^ 1u, &ctl.abort, a.wait_ns))) {
                 if (lane == 0) fail(ctl, a.status);
                 break;
             }
@@ -584,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
         int64_t issued = 0;
         bool ok = !dead;
         while (ok) {
-            if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.rec_full[rs]), rph, &ctl.abort))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.rec_full[rs]), rph, &ctl.abort, a.wait_ns))) {
                 if (lane == 0) fail(ctl, a.status);
                 ok = false;
                 break;
@@ -597,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
                 rph ^= 1u;
             }
             if (r.tile < 0) {  // the end marker for the MMA lane
-                if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort, a.wait_ns))) {
                     if (lane == 0) fail(ctl, a.status);
                     ok = false;
                     break;
@@ -622,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
                         const int32_t x = __shfl_sync(0xffffffffu, f[q], j);
                         if (lane == q) blk = x;
                     }
-                    if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort))) {
+                    if (!__all_sync(0xffffffffu, mbar_wait(saddr(&ctl.empty[st]), ph ^ 1u, &ctl.abort, a.wait_ns))) {
                         if (lane == 0) fail(ctl, a.status);
                         ok = false;
                         break;
@@ -666,13 +671,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
         if (lane == 0) {
             bool ok = !dead;
             while (ok) {
-                if (!mbar_wait(saddr(&ctl.full[st]), ph, &ctl.abort)) {
+                if (!mbar_wait(saddr(&ctl.full[st]), ph, &ctl.abort, a.wait_ns)) {
                     fail(ctl, a.status);
                     break;
                 }
                 tc_fence_after();
                 const int32_t tile = ctl.smeta_t[st], flags = ctl.smeta_f[st];
-                if (in_group == 0 && !mbar_wait(saddr(&ctl.acce[buf]), bph ^ 1u, &ctl.abort)) {
+                if (in_group == 0 && !mbar_wait(saddr(&ctl.acce[buf]), bph ^ 1u, &ctl.abort, a.wait_ns)) {
                     fail(ctl, a.status);
                     break;
                 }

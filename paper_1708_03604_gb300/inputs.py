@@ -154,7 +154,13 @@ def assemble(row_bs, col_bs, rows, cols, dist, seed: int, decay: float | None = 
         raise ValueError(values)
     if decay is not None and dist is not None and total:
         scale = np.exp(-dist.astype(np.float64) / decay)
-        data *= np.repeat(scale, sizes)
+        # block by block (in chunks of blocks, so no element-sized temporary)
+        step = 1 << 20
+        for b0 in range(0, rows.shape[0], step):
+            b1 = min(b0 + step, rows.shape[0])
+            e0 = int(blk_off[b0])
+            e1 = int(blk_off[b1 - 1] + sizes[b1 - 1])
+            data[e0:e1] *= np.repeat(scale[b0:b1], sizes[b0:b1])
     return BCSR(row_bs, col_bs, row_ptr, cols.astype(np.int32), blk_off, data.astype(dtype, copy=False))
 
 

@@ -18,3 +18,23 @@ def oracle():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(autouse=True)
+def _release_device_memory(request):
+    """After every GPU test: collect unreachable handles (autograd graphs hold
+    reference cycles through the handles that borrow their tensors) so that
+    the library's memory goes back to the caching allocator before the next
+    test needs it."""
+    yield
+    if request.node.get_closest_marker("gpu") is None:
+        return
+    import gc
+    gc.collect()
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+    except Exception:
+        pass

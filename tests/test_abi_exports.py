@@ -84,3 +84,27 @@ def test_engine_query_and_variant_range_on_host(libbsm):
     assert L.bsm_get_variant(bsm.BSM_P_TF32x3, 4, 4, ctypes.byref(v)) == bsm.BSM_OK and v.value == 1
     assert L.bsm_set_variant(bsm.BSM_P_TF32x3, 4, 4, -1) == bsm.BSM_OK
     assert L.bsm_get_variant(bsm.BSM_P_TF32x3, 4, 4, ctypes.byref(v)) == bsm.BSM_OK and v.value == 1
+
+
+def test_allocator_wait_limit_and_probe_arguments_on_host(libbsm):
+    """The allocator hooks, the wait limit and the peak probe check their
+    arguments on the host (no CUDA call is reached)."""
+    from paper_1708_03604_gb300 import bsm
+    L = bsm.lib()
+    hook_a = bsm.ALLOC_FN(lambda n, s, c: None)
+    # exactly one hook given
+    assert L.bsm_set_allocator(hook_a, bsm.FREE_FN(), None) == bsm.BSM_ERR_ARG
+    assert b"both" in L.bsm_last_error()
+    n = ctypes.c_int64(-1)
+    assert L.bsm_get_allocator_stats(ctypes.byref(n)) == bsm.BSM_OK and n.value == 0
+    assert L.bsm_get_allocator_stats(None) == bsm.BSM_ERR_ARG
+    # wait limits outside [0, 2] s
+    for bad in (-1.0, 2.5, float("nan")):
+        assert L.bsm_set_wait_limit(bad) == bsm.BSM_ERR_ARG
+    assert L.bsm_set_wait_limit(2.0) == bsm.BSM_OK
+    v = ctypes.c_double()
+    assert L.bsm_measure_peak(9, 1, ctypes.byref(v)) == bsm.BSM_ERR_ARG
+    assert L.bsm_measure_peak(0, 0, ctypes.byref(v)) == bsm.BSM_ERR_ARG
+    assert L.bsm_measure_peak(0, 1, None) == bsm.BSM_ERR_ARG
+    # the binding's hooks are back in place
+    bsm.use_torch_allocator()

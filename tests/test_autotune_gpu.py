@@ -1,0 +1,106 @@
+"""The autotuner's knobs (GPU): every launch and pass shape the tuner may
+choose changes what the numeric launch runs (bsm_get_launch_config) and
+leaves the results within the precision's tolerance against the oracle; a
+tuned table saved to JSON and loaded again puts the same knobs back."""
+import numpy as np
+import pytest
+
+from paper_1708_03604_gb300 import inputs as I
+from tests.helpers import random_bcsr, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp64_dmma": 1e-12, "tf32x3": 1e-6, "bf16x6": 1e-6, "bf16x3": 1e-4, "ozaki": 1e-13}
+
+
+@pytest.fixture(scope="module")
+def bsm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_03604_gb300 import bsm as B
+    B.lib()
+    return B
+
+
+@pytest.fixture(scope="module")
+def operands(bsm, oracle):
+    # blocks up to 40 x 40: several fragment tiles per side, so pass shapes matter
+    bs = I.mixed_sizes(60, (5, 13, 23, 40), (0.4, 0.2, 0.2, 0.2), seed=44)
+    Ah, Bh = random_bcsr(bs, bs, 0.15, seed=171), random_bcsr(bs, bs, 0.15, seed=172)
+    ref = oracle.multiply(1.0, Ah, Bh, eps=0.3)
+    return bsm.Matrix.from_host(Ah), bsm.Matrix.from_host(Bh), ref
+
+
+@pytest.mark.parametrize("prec,knobs", [
+    ("tf32x3", {"cta_warps": 8, "pass_mt": 1, "pass_nt": 1, "ctas_per_sm": 1}),
+    ("bf16x6", {"cta_warps": 8, "pass_nt": 2}),
+    ("bf16x3", {"pass_mt": 1, "pass_nt": 2, "ctas_per_sm": 2}),
+    ("ozaki", {"cta_warps": 8, "pass_nt": 1, "ctas_per_sm": 2}),
+    ("fp64", {"fp64_build": 1}),
+    ("fp64", {"fp64_build": 2, "ctas_per_sm": 1}),
+    ("fp64_dmma", {"pass_mt": 1, "pass_nt": 2, "ctas_per_sm": 3}),
+])
+def test_knobs_change_the_launch_and_keep_results(bsm, operands, prec, knobs):
+    from paper_1708_03604_gb300 import autotune
+    A, B, ref = operands
+    try:
+        for k, v in knobs.items():
+            bsm.bsm_set_tuning(prec, k, v)
+            assert bsm.bsm_get_tuning(prec, k) == v
+        Cg = bsm.multiply(1.0, A, B, eps=0.3, prec=prec)
+        cfg = Cg.launch_config()
+        np.testing.assert_array_equal(Cg.pattern()[1], ref.C.col_idx)
+        assert rel_fro(Cg.data_host(), ref.C.data) <= TOL[prec]
+        if "cta_warps" in knobs:
+            assert cfg["cta_threads"] == 32 * knobs["cta_warps"]
+        if "ctas_per_sm" in knobs:
+            assert 0 < cfg["grid"] <= 152 * knobs["ctas_per_sm"]
+        if "pass_mt" in knobs:
+            assert cfg["pass_mt"] == knobs["pass_mt"]
+        if "pass_nt" in knobs:
+            assert cfg["pass_nt"] == knobs["pass_nt"]
+        if "fp64_build" in knobs:
+            assert cfg["fp64_build"] == knobs["fp64_build"]
+        assert cfg["kernel"] == {"fp64": "fp64_cores", "fp64_dmma": "fp64_mma", "ozaki": "ozaki_mma"}.get(
+            prec, "split_mma")
+    finally:
+        autotune.reset(prec)
+    # back to the defaults
+    Cd = bsm.multiply(1.0, A, B, eps=0.3, prec=prec)
+    d = Cd.launch_config()
+    assert d["cta_threads"] == 128
+    assert rel_fro(Cd.data_host(), ref.C.data) <= TOL[prec]
+
+
+def test_knob_ranges_are_checked(bsm):
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("fp64", "cta_warps", 8)        # the FP64 kernels run 4 warps per CTA
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("tf32x3", "pass_mt", 3)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("ozaki", "fp64_build", 1)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("tf32x3_panel", "ctas_per_sm", 1)
+
+
+def test_tuned_table_roundtrip(bsm, operands, tmp_path):
+    from paper_1708_03604_gb300 import autotune
+    A, B, ref = operands
+    try:
+        table = autotune.tune(A, B, 0.3, prec="tf32x3", reps=1)
+        assert table["numeric_ms"]["tuned"] > 0
+        assert set(table["params"]) == {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm"}
+        # the flush interval the tuner chose keeps the error within its target
+        if table["flush_every"] is not None:
+            assert table["flush_trials"][str(table["flush_every"])]["rel_fro_err_vs_fp64_path"] <= 1e-6
+        path = str(tmp_path / "t.json")
+        autotune.save([table], path)
+        autotune.reset("tf32x3")
+        autotune.load(path)
+        for k, v in table["params"].items():
+            assert bsm.bsm_get_tuning("tf32x3", k) == v
+        Cg = bsm.multiply(1.0, A, B, eps=0.3, prec="tf32x3", flush_every=table["flush_every"] or 0)
+        assert rel_fro(Cg.data_host(), ref.C.data) <= 1e-6
+    finally:
+        autotune.reset("tf32x3")

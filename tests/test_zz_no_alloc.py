@@ -90,3 +90,39 @@ def test_static_count_rejects_sizes_above_capacity(bsm):
     assert st == bsm.BSM_ERR_CAPACITY
     assert b"2097152" in bsm.lib().bsm_last_error()
     assert int(buf.abs().sum().item()) == 0      # refused before any device work
+
+
+def test_static_count_allocates_nothing(bsm):
+    """The property the entry point exists for: after one warm-up call (which
+    loads the kernel and looks the array up), further filtered calls take no
+    memory from the installed allocator hooks and leave the device's free
+    memory unchanged."""
+    import torch
+    w = I.mixed_banded(nb=240, occ=0.1, eps=1.0, decay=8.0)
+    A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+    nbr = A.info().nbr
+    out = torch.zeros(2 * nbr + 3, dtype=torch.int64, device="cuda")
+    calls = []
+
+    def alloc(n, s):
+        calls.append(n)
+        return torch.cuda.caching_allocator_alloc(int(n), torch.cuda.current_device(), int(s or 0))
+
+    def free(p, n, s):
+        torch.cuda.caching_allocator_delete(p)
+
+    args = (A.h, B.h, 1.0, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(out.data_ptr() + 8 * nbr),
+            ctypes.c_void_p(out.data_ptr() + 16 * nbr))
+    bsm._sync_stream()
+    assert bsm.lib().bsm_count_products_static(*args) == bsm.BSM_OK
+    torch.cuda.synchronize()
+    bsm.set_allocator(alloc, free)
+    try:
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            assert bsm.lib().bsm_count_products_static(*args) == bsm.BSM_OK
+        torch.cuda.synchronize()
+        assert calls == []
+        assert torch.cuda.mem_get_info()[0] == free0
+    finally:
+        bsm.use_torch_allocator()
