@@ -192,8 +192,8 @@ bsm_status bsm_set_profiling(int32_t on);
 bsm_status bsm_get_launch_count(int64_t *count);
 
 /* Numeric variant per precision and output block shape (m rows, n columns),
- * for tiny blocks (m*n <= 16, and on the FP64 and Ozaki paths 5 x 5 and
- * 6 x 6; other shapes always use variant 0):
+ * for tiny blocks (m*n <= 16, 5 x 5, and on the FP64 and Ozaki paths 6 x 6;
+ * other shapes always use variant 0):
  * 0 = one warp per output block (FP64: lanes over its elements; split and
  * Ozaki paths: tensor-core MMA on packed fragments), 1 = one lane per output
  * block on CUDA cores (split paths: the same split pieces multiplied with FP32
@@ -215,7 +215,7 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  * sets them).  value -1 restores the default.  Process-wide; applies to
  * multiplies and adjoints issued afterwards (a no-sync multiply keeps the
  * settings of its eager call only for sizes, not for these).
- *   BSM_TUNE_CTA_WARPS   warps per CTA of the persistent kernel: 4 or 8 for
+ *   BSM_TUNE_CTA_WARPS   warps per CTA of the persistent kernel: 2 or 4 for
  *                        BSM_P_TF32x3 / BF16x3 / BF16x6 / OZAKI (default 4);
  *                        4 only for the FP64 kernels
  *   BSM_TUNE_CTAS_PER_SM persistent CTAs per SM, 1..16, capped by what fits;
@@ -231,11 +231,19 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  *                        9 elements per lane per pass), 2 wide (up to 24);
  *                        output blocks of at most 16 elements always run the
  *                        small build
+ *   BSM_TUNE_SCHED_TILE  order of the output blocks inside a block-shape
+ *                        class: 0 (default) by the breadth-first rank of
+ *                        their block row; T in 8..4096 by 2-D tiles of T
+ *                        ranked rows x T ranked columns (columns ranked the
+ *                        same way through B's pattern), so that the blocks in
+ *                        flight share both operands' blocks in L2.  A
+ *                        permutation of independent work: results do not
+ *                        depend on it.  Not for BSM_P_TF32x3_PANEL.
  * Values outside these ranges are BSM_ERR_ARG.
  */
 enum {
     BSM_TUNE_CTA_WARPS = 0, BSM_TUNE_CTAS_PER_SM = 1, BSM_TUNE_PASS_MT = 2, BSM_TUNE_PASS_NT = 3,
-    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_COUNT = 5
+    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_SCHED_TILE = 5, BSM_TUNE_COUNT = 6
 };
 bsm_status bsm_set_tuning(int32_t prec, int32_t param, int32_t value);
 bsm_status bsm_get_tuning(int32_t prec, int32_t param, int32_t *value);

@@ -7,14 +7,17 @@ recorded by the library around the launch) on the caller's operands:
 
 * per output block shape (m, n): the variant -- one warp per block (FP64:
   lanes over its elements; split and Ozaki paths: tensor-core MMAs on packed
-  fragments) or, for blocks of at most 16 elements (FP64 and Ozaki also 5 x 5
-  and 6 x 6), one lane per block on the CUDA cores;
+  fragments) or, for blocks of at most 16 elements and 5 x 5 ones (FP64 and
+  Ozaki also 6 x 6), one lane per block on the CUDA cores;
 * the FP64 FMA kernel build (how many output elements a lane holds per pass:
   up to 9 or up to 24) -- BSM_P_FP64;
-* warps per CTA (4 or 8) of the persistent mma.sync kernels;
+* warps per CTA (4 or 2) of the persistent mma.sync kernels;
 * persistent CTAs per SM;
 * the fragment-tile pass shape (tiles along rows and columns that one pass
   over a block's products covers) of the split, Ozaki and FP64-MMA kernels;
+* the order of the output blocks: by block row, or by 2-D tiles of ranked
+  rows x ranked columns so that the blocks in flight share A's and B's
+  blocks in L2;
 * for the split paths, the interval F of the FP64 running sum (FP32
   accumulation over at most F block products), the fastest F whose result is
   within ``err_target`` (relative Frobenius) of the FP64 path on the same
@@ -38,13 +41,15 @@ import numpy as np
 from . import bsm
 
 SPLIT = ("tf32x3", "bf16x3", "bf16x6")
+TILES = ("sched_tile", [0, 16, 32, 64, 128])
 SEARCH = {
-    "fp64": [("fp64_build", [0, 1, 2]), ("ctas_per_sm", [0, 1, 2, 3, 4])],
-    "fp64_dmma": [("pass_mt", [3, 2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 4])],
-    "ozaki": [("cta_warps", [4, 8]), ("pass_nt", [2, 1]), ("ctas_per_sm", [0, 1, 2, 3])],
+    "fp64": [("fp64_build", [0, 1, 2]), ("ctas_per_sm", [0, 1, 2, 3, 4]), TILES],
+    "fp64_dmma": [("pass_mt", [3, 2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 4]), TILES],
+    "ozaki": [("cta_warps", [4, 2]), ("pass_nt", [2, 1]), ("ctas_per_sm", [0, 1, 2, 3]), TILES],
 }
 for _p in SPLIT:
-    SEARCH[_p] = [("cta_warps", [4, 8]), ("pass_mt", [2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 3, 4])]
+    SEARCH[_p] = [("cta_warps", [4, 2]), ("pass_mt", [2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 3, 4]),
+                  TILES]
 FLUSH_CANDIDATES = [-1, 1, 2, 4, 8, 16]
 
 
@@ -83,7 +88,8 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
     if prec == "tf32x3_panel":
         raise ValueError("the tf32x3_panel engine has no tuning knobs: tune 'tf32x3' for the kernel it falls back to")
     fp64_like = prec in ("fp64", "fp64_dmma", "ozaki")  # lane variant = plain FP64 FMA
-    shapes = [(m, n) for m, n in _shapes(A, B) if m * n <= 16 or (fp64_like and (m, n) in ((5, 5), (6, 6)))]
+    shapes = [(m, n) for m, n in _shapes(A, B)
+              if m * n <= 16 or (m, n) == (5, 5) or (fp64_like and (m, n) == (6, 6))]
     reset(prec)
     for m, n in shapes:
         bsm.bsm_set_variant(prec, m, n, 0)

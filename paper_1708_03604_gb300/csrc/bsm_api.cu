@@ -30,11 +30,13 @@ int64_t *g_host = nullptr;  // pinned host words for small device->host reads
 int8_t g_variant[6][kMaxBlockDim + 1][kMaxBlockDim + 1];
 bool g_variant_init = false;
 
-// shapes the lane-per-block variant takes: up to 16 elements, plus 5 x 5 and
-// 6 x 6 on the paths whose lane variant is plain FP64 FMA
+// shapes the lane-per-block variant takes: up to 16 elements, plus 5 x 5 (on
+// the split paths the same pieces multiplied with FP32 FMA) and, on the paths
+// whose lane variant is plain FP64 FMA, 6 x 6 (a 6 x 6 compensated pair would
+// raise the split kernels' register count for every item)
 bool lane_eligible(int prec, int m, int n) {
     const bool fp64 = prec == BSM_P_FP64 || prec == BSM_P_FP64_DMMA || prec == BSM_P_OZAKI;
-    return m * n <= 16 || (fp64 && ((m == 5 && n == 5) || (m == 6 && n == 6)));
+    return m * n <= 16 || (m == 5 && n == 5) || (fp64 && m == 6 && n == 6);
 }
 
 int variant_of(int prec, int m, int n) {
@@ -63,9 +65,16 @@ bool all_lane(int prec, const std::vector<int32_t> &rows, const std::vector<int3
 }
 std::atomic<int64_t> g_launches{0};
 // launch and pass shape per precision (bsm_set_tuning); -1 = the default
-int32_t g_tune[7][BSM_TUNE_COUNT] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1},
-                                     {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1},
-                                     {-1, -1, -1, -1, -1}};
+int32_t g_tune[7][BSM_TUNE_COUNT];
+bool g_tune_init = false;
+int32_t *tune_of(int prec) {
+    if (!g_tune_init) {
+        for (auto &row : g_tune)
+            for (auto &v : row) v = -1;
+        g_tune_init = true;
+    }
+    return g_tune[prec];
+}
 // allowed range of a tuning value for a precision: [lo, hi], lo > hi = none
 void tune_range(int prec, int param, int *lo, int *hi) {
     const bool split = prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6;
@@ -73,7 +82,7 @@ void tune_range(int prec, int param, int *lo, int *hi) {
     *hi = 0;
     switch (param) {
         case BSM_TUNE_CTA_WARPS:
-            if (split || prec == BSM_P_OZAKI) { *lo = 4; *hi = 8; }
+            if (split || prec == BSM_P_OZAKI) { *lo = 2; *hi = 4; }
             else if (prec != BSM_P_TF32x3_PANEL) { *lo = 4; *hi = 4; }
             break;
         case BSM_TUNE_CTAS_PER_SM:
@@ -90,11 +99,14 @@ void tune_range(int prec, int param, int *lo, int *hi) {
         case BSM_TUNE_FP64_BUILD:
             if (prec == BSM_P_FP64) { *lo = 0; *hi = 2; }
             break;
+        case BSM_TUNE_SCHED_TILE:
+            if (prec != BSM_P_TF32x3_PANEL) { *lo = 0; *hi = 4096; }
+            break;
     }
 }
 // the tuning of `prec` into the numeric launch arguments
 void apply_tuning(int prec, NumericArgs &na) {
-    const int32_t *t = g_tune[prec];
+    const int32_t *t = tune_of(prec);
     na.cta_warps = t[BSM_TUNE_CTA_WARPS] > 0 ? t[BSM_TUNE_CTA_WARPS] : 4;
     na.ctas_per_sm = t[BSM_TUNE_CTAS_PER_SM] > 0 ? t[BSM_TUNE_CTAS_PER_SM] : 0;
     na.pass_mt = t[BSM_TUNE_PASS_MT] > 0 ? t[BSM_TUNE_PASS_MT] : 0;
@@ -191,6 +203,7 @@ void free_pattern(bsm_mat *X) {
     dfree(X->item_order); X->item_order = nullptr;
     dfree(X->n_marked); X->n_marked = nullptr;
     dfree(X->row_rank); X->row_rank = nullptr;
+    dfree(X->col_rank); X->col_rank = nullptr;
     dfree(X->panel_ord_r); X->panel_ord_r = nullptr;
     dfree(X->panel_ord_c); X->panel_ord_c = nullptr;
     dfree(X->panel_pos_c); X->panel_pos_c = nullptr;
@@ -369,6 +382,27 @@ std::vector<int32_t> bfs_row_rank(const HostPattern &h, int32_t nbr, int32_t nbc
     return rank;
 }
 
+// breadth-first rank of the block columns of X through shared block rows
+bsm_status ensure_col_rank(bsm_mat *X) {
+    if (X->col_rank) return BSM_OK;
+    HostPattern h;
+    bsm_status st;
+    if ((st = host_pattern(X, h))) return st;
+    HostPattern t;  // the transposed pattern: columns become rows
+    t.rp = h.cp; t.ci = h.cr; t.cp = h.rp; t.cr = h.ci;
+    std::vector<int32_t> rank = bfs_row_rank(t, X->nbc, X->nbr);
+    int32_t *d = nullptr;
+    if ((st = dalloc_t(&d, X->nbc))) return st;
+    cudaError_t e = cudaMemcpyAsync(d, rank.data(), sizeof(int32_t) * X->nbc, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+    if ((st = cuda_check(e, "upload column order"))) {
+        dfree(d);
+        return st;
+    }
+    X->col_rank = d;
+    return BSM_OK;
+}
+
 bsm_status ensure_row_rank(bsm_mat *X) {
     if (X->row_rank || X->nbr == 0) return BSM_OK;
     const int32_t nbr = X->nbr;
@@ -395,7 +429,8 @@ bsm_status ensure_row_rank(bsm_mat *X) {
 bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std::vector<int32_t> &rsz,
                        const std::vector<int32_t> &csz, int32_t **order, const bsm_mat *rows_of = nullptr,
                        const int32_t *row_rank = nullptr, int prec = -1, bool *uses_cores = nullptr,
-                       int64_t **n_marked = nullptr) {
+                       int64_t **n_marked = nullptr, const int32_t *blk_col = nullptr,
+                       const int32_t *col_rank = nullptr, int32_t ncols = 0, int32_t tile = 0) {
     if (uses_cores) *uses_cores = false;
     *order = nullptr;
     if (n <= 1) return BSM_OK;
@@ -426,8 +461,12 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
         table[cls[q].second] = (int32_t)q + (var[cls[q].second] ? (int32_t)cls.size() : 0);
     const int32_t nbr = rows_of ? rows_of->nbr : 0;
     if (row_rank && 2 * (int64_t)table.size() * std::max(nbr, 1) >= (int64_t(1) << 31)) row_rank = nullptr;
+    // 2-D schedule tiles when asked for and the keys fit in 31 bits
+    const bool tiled = row_rank && blk_col && col_rank && tile > 0;
+    const int64_t nrt = tiled ? (nbr + tile - 1) / tile : 0, nct = tiled ? (ncols + tile - 1) / tile : 0;
+    const bool use_tiles = tiled && 2 * (int64_t)table.size() * nrt * nct < (int64_t(1) << 31);
     int bits = 1;
-    while ((1ll << bits) < 2 * (int64_t)table.size() * (row_rank ? nbr : 1)) ++bits;
+    while ((1ll << bits) < 2 * (int64_t)table.size() * (use_tiles ? nrt * nct : (row_rank ? nbr : 1))) ++bits;
     bsm_status st;
     int32_t *d_sidx, *d_table, *iota, *vals_alt, *out, *brow = nullptr;
     uint32_t *keys, *keys_alt, *keys_sorted;
@@ -446,7 +485,8 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
         e = launch_blk_rows(&view, brow, g_stream);
     }
     if (e == cudaSuccess)
-        e = launch_class_keys(n, blk_rc, d_sidx, ns, d_table, brow, row_rank, nbr, keys, iota, g_stream);
+        e = launch_class_keys(n, blk_rc, d_sidx, ns, d_table, brow, row_rank, nbr, use_tiles ? blk_col : nullptr,
+                              use_tiles ? col_rank : nullptr, use_tiles ? tile : 0, (int32_t)nct, keys, iota, g_stream);
     if (e == cudaSuccess)
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
@@ -1522,11 +1562,14 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         uses_cores = pl.uses_cores;
     } else {
         if ((st = ensure_row_rank(A))) return st;
+        const int32_t tile = tune_of(rprec)[BSM_TUNE_SCHED_TILE];
+        if (tile > 0 && (st = ensure_col_rank(B))) return st;
         bsm_mat rows_view;
         rows_view.nbr = nbr;
         rows_view.row_ptr = crow_ptr;
         if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
-                              rprec, &uses_cores, &n_marked)))
+                              rprec, &uses_cores, &n_marked, c_col, tile > 0 ? B->col_rank : nullptr, nbc,
+                              tile > 0 ? tile : 0)))
             return st;
     }
     na.n_lane_items = n_marked;
@@ -1951,9 +1994,10 @@ bsm_status bsm_set_tuning(int32_t prec, int32_t param, int32_t value) {
     tune_range(prec, param, &lo, &hi);
     if (lo > hi) return set_error(BSM_ERR_ARG, "this precision has no such tuning parameter");
     if (value != -1 && (value < lo || value > hi)) return set_error(BSM_ERR_ARG, "tuning value out of range");
-    if (param == BSM_TUNE_CTA_WARPS && value != -1 && value != 4 && value != 8)
-        return set_error(BSM_ERR_ARG, "warps per CTA must be 4 or 8");
-    g_tune[prec][param] = value;
+    if (param == BSM_TUNE_CTA_WARPS && value == 3) return set_error(BSM_ERR_ARG, "warps per CTA must be 2 or 4");
+    if (param == BSM_TUNE_SCHED_TILE && value > 0 && value < 8)
+        return set_error(BSM_ERR_ARG, "schedule tile must be 0 or 8..4096");
+    tune_of(prec)[param] = value;
     return BSM_OK;
 }
 
@@ -1961,7 +2005,7 @@ bsm_status bsm_get_tuning(int32_t prec, int32_t param, int32_t *value) {
     if (!value) return set_error(BSM_ERR_ARG, "value is NULL");
     if (prec < BSM_P_FP64 || prec > BSM_P_TF32x3_PANEL) return set_error(BSM_ERR_ARG, "prec out of range");
     if (param < 0 || param >= BSM_TUNE_COUNT) return set_error(BSM_ERR_ARG, "unknown tuning parameter");
-    *value = g_tune[prec][param];
+    *value = tune_of(prec)[param];
     return BSM_OK;
 }
 

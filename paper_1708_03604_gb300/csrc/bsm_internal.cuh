@@ -94,6 +94,9 @@ struct bsm_mat {
     // rank of every block row in a breadth-first order through shared block
     // columns (built on demand, dropped with the pattern); schedules numeric work
     int32_t *row_rank = nullptr;        // [nbr]
+    // rank of every block column in a breadth-first order through shared block
+    // rows (the same for columns; built on demand, dropped with the pattern)
+    int32_t *col_rank = nullptr;        // [nbc]
     // first global row / column of every block row / column ([nbr+1], [nbc+1];
     // built on demand, kept until the handle is destroyed)
     int32_t *row_start = nullptr, *col_start = nullptr;
@@ -228,10 +231,14 @@ cudaError_t launch_gather_i32(int64_t n, const int32_t *order, const int32_t *sr
                               cudaStream_t s);
 cudaError_t launch_iota_keys(int64_t n, const int32_t *src, uint32_t *keys, int32_t *iota,
                              cudaStream_t s);
-// Scheduling key of every block: table[size_index[rows] * ns + size_index[cols]] * nbr
-// + row_rank[block row] (row_rank may be null: key = class only).
+// Scheduling key of every block: class = table[size_index[rows] * ns +
+// size_index[cols]], then row_rank[block row] (row_rank may be null: key =
+// class only); with col_rank and tile > 0, the 2-D tile (row_rank / tile,
+// col_rank[block column] / tile) instead of the row rank (nct = number of
+// column tiles).
 cudaError_t launch_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
                               const int32_t *table, const int32_t *blk_row, const int32_t *row_rank, int32_t nbr,
+                              const int32_t *blk_col, const int32_t *col_rank, int32_t tile, int32_t nct,
                               uint32_t *keys, int32_t *iota, cudaStream_t s);
 
 // ---------------------------------------------------------------- numeric

@@ -30,7 +30,6 @@ namespace {
 
 constexpr int kWarpsPerCta = 4;             // default warps per CTA
 constexpr int kThreadsNum = kWarpsPerCta * 32;
-constexpr int kMaxThreadsTc = 8 * 32;        // the mma.sync kernels take 4 or 8 warps per CTA
 
 // =====================================================================
 // CUDA-core path
@@ -941,12 +940,13 @@ __device__ __forceinline__ void cs_lane_dispatch(const NumericArgs &a, int64_t q
         case 0x401: cs_lane_fixed<PREC, FF, 4, 1>(a, q); break;
         case 0x404: cs_lane_fixed<PREC, FF, 4, 4>(a, q); break;
         case 0x202: cs_lane_fixed<PREC, FF, 2, 2>(a, q); break;
+        case 0x505: cs_lane_fixed<PREC, FF, 5, 5>(a, q); break;
         default: cs_lane_item<PREC, FF>(a, q); break;
     }
 }
 
 template <int PREC, bool FF>
-__global__ void __launch_bounds__(kMaxThreadsTc) k_numeric_tc(NumericArgs a) {
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t tc_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC>();
@@ -1229,7 +1229,7 @@ __device__ __forceinline__ void oz_item(const NumericArgs &a, int64_t q, int lan
 
 // Items [0, n0): a warp each on the tensor cores; items [n0, n_items): tiny
 // blocks one per lane with plain FP64 FMA (exact enough, no slicing needed).
-__global__ void __launch_bounds__(kMaxThreadsTc) k_numeric_oz(NumericArgs a) {
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t oz_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ring = oz_smem + warp * oz_ring_words_per_warp();
@@ -1592,7 +1592,9 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     cudaError_t e = cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const bool tc = a.prec == BSM_P_TF32x3 || a.prec == BSM_P_BF16x3 || a.prec == BSM_P_BF16x6;
-    const int tc_threads = (a.cta_warps == 8 ? 8 : 4) * 32;
+    // the mma.sync kernels run 2 or 4 warps per CTA (compiled for at most 4,
+    // which keeps their register count at three CTAs per SM)
+    const int tc_threads = (a.cta_warps == 2 ? 2 : 4) * 32;
     int grid = 0;
     if (a.prec == BSM_P_OZAKI) {
         const size_t smem = sizeof(uint32_t) * (size_t)oz_ring_words_per_warp() * (tc_threads / 32);

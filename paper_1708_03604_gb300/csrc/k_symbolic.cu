@@ -706,12 +706,20 @@ __global__ void k_copy_i64_if_ok(int64_t n, const int64_t *src, int64_t *dst, co
 
 __global__ void k_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
                              const int32_t *table, const int32_t *blk_row, const int32_t *row_rank, int32_t nbr,
+                             const int32_t *blk_col, const int32_t *col_rank, int32_t tile, int32_t nct,
                              uint32_t *keys, int32_t *iota) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t rc = blk_rc[p];
         uint32_t k = (uint32_t)table[size_index[rc_rows(rc)] * ns + size_index[rc_cols(rc)]];
-        if (row_rank) k = k * (uint32_t)nbr + (uint32_t)row_rank[blk_row[p]];
+        if (row_rank && col_rank && tile > 0) {
+            // 2-D tiles of (row rank, column rank), tiles row by row
+            const uint32_t nrt = (uint32_t)((nbr + tile - 1) / tile);
+            k = (k * nrt + (uint32_t)(row_rank[blk_row[p]] / tile)) * (uint32_t)nct +
+                (uint32_t)(col_rank[blk_col[p]] / tile);
+        } else if (row_rank) {
+            k = k * (uint32_t)nbr + (uint32_t)row_rank[blk_row[p]];
+        }
         keys[p] = k;
         iota[p] = (int32_t)p;
     }
@@ -943,10 +951,11 @@ cudaError_t launch_copy_i64_if_ok(int64_t n, const int64_t *src, int64_t *dst, c
 
 cudaError_t launch_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *size_index, int32_t ns,
                               const int32_t *table, const int32_t *blk_row, const int32_t *row_rank, int32_t nbr,
+                              const int32_t *blk_col, const int32_t *col_rank, int32_t tile, int32_t nct,
                               uint32_t *keys, int32_t *iota, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_class_keys<<<grid_for(n), kThreads, 0, s>>>(n, blk_rc, size_index, ns, table, blk_row, row_rank, nbr, keys,
-                                                  iota);
+    k_class_keys<<<grid_for(n), kThreads, 0, s>>>(n, blk_rc, size_index, ns, table, blk_row, row_rank, nbr, blk_col,
+                                                  col_rank, tile, nct, keys, iota);
     count_launch(1);
     return cudaGetLastError();
 }

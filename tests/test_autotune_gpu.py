@@ -33,10 +33,10 @@ def operands(bsm, oracle):
 
 
 @pytest.mark.parametrize("prec,knobs", [
-    ("tf32x3", {"cta_warps": 8, "pass_mt": 1, "pass_nt": 1, "ctas_per_sm": 1}),
-    ("bf16x6", {"cta_warps": 8, "pass_nt": 2}),
+    ("tf32x3", {"cta_warps": 2, "pass_mt": 1, "pass_nt": 1, "ctas_per_sm": 1}),
+    ("bf16x6", {"cta_warps": 2, "pass_nt": 2}),
     ("bf16x3", {"pass_mt": 1, "pass_nt": 2, "ctas_per_sm": 2}),
-    ("ozaki", {"cta_warps": 8, "pass_nt": 1, "ctas_per_sm": 2}),
+    ("ozaki", {"cta_warps": 2, "pass_nt": 1, "ctas_per_sm": 2}),
     ("fp64", {"fp64_build": 1}),
     ("fp64", {"fp64_build": 2, "ctas_per_sm": 1}),
     ("fp64_dmma", {"pass_mt": 1, "pass_nt": 2, "ctas_per_sm": 3}),
@@ -73,15 +73,38 @@ def test_knobs_change_the_launch_and_keep_results(bsm, operands, prec, knobs):
     assert rel_fro(Cd.data_host(), ref.C.data) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "ozaki"])
+def test_schedule_tiles_permute_work_only(bsm, prec):
+    """The 2-D tiled order of the output blocks is a permutation of work
+    that each warp does alone in a fixed order: the result is bit for bit the
+    one of the default (row) order, for banded-then-permuted operands whose
+    ranked rows and columns make the tiles compact."""
+    from paper_1708_03604_gb300 import autotune
+    w = I.mixed_banded(nb=400, occ=0.1, eps=1e-6)
+    A, B = bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"])
+    base = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec).data_host()
+    try:
+        for t in (8, 32, 256):
+            bsm.bsm_set_tuning(prec, "sched_tile", t)
+            got = bsm.multiply(1.0, A, B, eps=w["eps"], prec=prec).data_host()
+            np.testing.assert_array_equal(got, base)
+    finally:
+        autotune.reset(prec)
+
+
 def test_knob_ranges_are_checked(bsm):
     with pytest.raises(bsm.BsmError):
-        bsm.bsm_set_tuning("fp64", "cta_warps", 8)        # the FP64 kernels run 4 warps per CTA
+        bsm.bsm_set_tuning("fp64", "cta_warps", 2)        # the FP64 kernels run 4 warps per CTA
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("tf32x3", "cta_warps", 8)
     with pytest.raises(bsm.BsmError):
         bsm.bsm_set_tuning("tf32x3", "pass_mt", 3)
     with pytest.raises(bsm.BsmError):
         bsm.bsm_set_tuning("ozaki", "fp64_build", 1)
     with pytest.raises(bsm.BsmError):
         bsm.bsm_set_tuning("tf32x3_panel", "ctas_per_sm", 1)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("fp64", "sched_tile", 4)
 
 
 def test_tuned_table_roundtrip(bsm, operands, tmp_path):
@@ -90,7 +113,7 @@ def test_tuned_table_roundtrip(bsm, operands, tmp_path):
     try:
         table = autotune.tune(A, B, 0.3, prec="tf32x3", reps=1)
         assert table["numeric_ms"]["tuned"] > 0
-        assert set(table["params"]) == {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm"}
+        assert set(table["params"]) == {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm", "sched_tile"}
         # the flush interval the tuner chose keeps the error within its target
         if table["flush_every"] is not None:
             assert table["flush_trials"][str(table["flush_every"])]["rel_fro_err_vs_fp64_path"] <= 1e-6
