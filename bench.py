@@ -118,6 +118,25 @@ def load_tuning(spec, name):
                        for t in (tables if isinstance(tables, list) else [tables])]}
 
 
+PROFILE_TRAFFIC = {"banded23_6912": os.path.join(ROOT, "profiles", "numeric_fp64_banded6912.md")}
+
+
+def traffic_from_profile(name):
+    """DRAM bytes per launch of the FP64 numeric kernel from the committed ncu
+    summary of this workload (None when absent or marked stale)."""
+    path = PROFILE_TRAFFIC.get(name)
+    if not path:
+        return None
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null", "stale") else float(v)
+    except OSError:
+        pass
+    return None
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -613,9 +632,13 @@ def run_headline(args, name, world, rank, local_rank):
     phases = {k: statistics.mean(t[k] for t in per_step) for k in per_step[0]}
     shapes, scounts = Cm[0].stack_shapes()
     roofline = leg_roofline("fp64", flop, None, num_ms, peaks, tpk)
+    traffic = traffic_from_profile(name) if world == 1 else None
     roofline.update(kernel=("k_numeric_cc<double> (FP64 FMA, one warp per C block; stream of the multiply, "
                             "CUDA events of the library around the launch)"),
-                    traffic=None, traffic_note="DRAM bytes per launch: profiles/numeric_fp64_banded6912.md")
+                    traffic=traffic,
+                    traffic_note=("dram__bytes_read.sum + dram__bytes_write.sum of one launch at 2000 block rows, "
+                                  "scaled by products to the full launch (profiles/numeric_fp64_banded6912.md)")
+                    if traffic else "no committed capture for this workload")
     c_blocks = Cm[0].nnzb
     pattern = Cm[0].pattern()
     ref_c = Cm[0].data_tensor()    # the FP64 result, kept for the legs' full-C errors

@@ -224,7 +224,8 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  *                        a block's products: split paths 1..2 (default 2,
  *                        16-row tiles), FP64_DMMA 1..3 (default 3, 8-row tiles)
  *   BSM_TUNE_PASS_NT     along the columns: split paths 1..3 (default 3,
- *                        8-column tiles), OZAKI 1..2 (default 2), FP64_DMMA
+ *                        8-column tiles), OZAKI 1..3 (default 2; 3 runs a
+ *                        kernel instance with a larger staging ring), FP64_DMMA
  *                        1..3 (default 3)
  *   BSM_TUNE_FP64_BUILD  BSM_P_FP64 only: FP64 FMA kernel build, 0 chosen by
  *                        the largest output block (default), 1 narrow (up to
@@ -297,19 +298,22 @@ bsm_status bsm_create(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_b
                       const int64_t *blk_off, int32_t dtype, const void *data,
                       int64_t data_len, int32_t data_mode);
 
-/* Create an empty matrix (no blocks) with the given blocking; the usual
- * target of bsm_multiply / bsm_add. */
+/* Create an empty matrix (no blocks) with the given blocking (§2 blocked CSR
+ * format); the usual target of bsm_multiply / bsm_add. */
 bsm_status bsm_create_empty(bsm_t *out, int32_t nbr, int32_t nbc, const int32_t *row_bs,
                             const int32_t *col_bs, int32_t dtype);
 
 /* Create a matrix with X's blocking and pattern and zero-filled, library-
- * owned data (for gradients). */
+ * owned data (for gradients; a library service, the paper has no
+ * counterpart). */
 bsm_status bsm_create_like(bsm_t *out, bsm_t X);
 
 /* Release the handle and the device memory it owns (stream-ordered). */
 bsm_status bsm_destroy(bsm_t X);
 
-/* Sizes of X: any output pointer may be NULL.  Synchronises the stream. */
+/* Sizes of X: any output pointer may be NULL.  Synchronises the stream.
+ * (Handle queries and copies below are library services; the paper has no
+ * counterpart.) */
 bsm_status bsm_get_info(bsm_t X, int32_t *nbr, int32_t *nbc, int64_t *nnzb,
                         int64_t *data_len, int32_t *dtype);
 
@@ -387,11 +391,12 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C,
 bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm_t A, bsm_t B,
                                  void *dA_data, void *dB_data, const bsm_opts *opts);
 
-/* Counts of the last multiply into C: kept products, filtered candidate
- * products and useful FLOPs (sum of 2*m*n*k over kept products). */
+/* Counts of the last multiply into C (§2: the products kept by the
+ * on-the-fly filter): kept products, filtered candidate products and useful
+ * FLOPs (sum of 2*m*n*k over kept products). */
 bsm_status bsm_get_counts(bsm_t C, int64_t *products, int64_t *filtered, double *useful_flop);
 
-/* Numeric engine of the last multiply into C. */
+/* Numeric engine of the last multiply into C (a library service). */
 typedef enum {
     BSM_E_NONE = -1,        /* no multiply (or no output block)                 */
     BSM_E_FP64_CORES = 0,   /* FP64 (or FP32) FMA on the CUDA cores             */
@@ -402,7 +407,7 @@ typedef enum {
 bsm_status bsm_get_engine(bsm_t C, int32_t *engine);
 
 /* Per-phase timings of the last multiply into C (BSM_T_COUNT doubles, ms),
- * valid when profiling was on.  Synchronises the stream. */
+ * valid when profiling was on (a library service).  Synchronises the stream. */
 bsm_status bsm_get_timings(bsm_t C, double *ms);
 
 /*
@@ -462,12 +467,13 @@ bsm_status bsm_count_products_static(bsm_t A, bsm_t B, double filter_eps, int64_
  * rounded sum (no fused multiply-add). */
 bsm_status bsm_add(double a, bsm_t X, double b, bsm_t Y, bsm_t Z, double filter_eps, const bsm_opts *opts);
 
-/* Device status word of the last call that wrote X: BSM_OK, or
+/* Device status word of the last call that wrote X (a library service): BSM_OK, or
  * BSM_ERR_CAPACITY when a no-sync call found sizes different from its eager
  * call (then *status has bit 1 set).  Synchronises the stream. */
 bsm_status bsm_get_status(bsm_t X, int32_t *status);
 
-/* Adjoint of the last bsm_add that wrote Z (Z = a*X + b*Y, blocks with norm
+/* Adjoint of the last bsm_add that wrote Z (the paper has no counterpart:
+ * differentiation through the purification chain; Z = a*X + b*Y, blocks with norm
  * <= eps dropped), at that add's keep-decisions: dX = a*dZ on the X blocks
  * that reached Z, dY = b*dZ likewise, zero elsewhere.  dZ_data has Z's
  * layout; dX_data / dY_data have X's / Y's layout (overwritten; either may be
