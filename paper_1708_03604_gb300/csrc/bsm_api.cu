@@ -93,8 +93,7 @@ void tune_range(int prec, int param, int *lo, int *hi) {
             else if (prec == BSM_P_FP64_DMMA) { *lo = 1; *hi = 3; }
             break;
         case BSM_TUNE_PASS_NT:
-            if (split || prec == BSM_P_FP64_DMMA) { *lo = 1; *hi = 3; }
-            else if (prec == BSM_P_OZAKI) { *lo = 1; *hi = 2; }
+            if (split || prec == BSM_P_FP64_DMMA || prec == BSM_P_OZAKI) { *lo = 1; *hi = 3; }
             break;
         case BSM_TUNE_FP64_BUILD:
             if (prec == BSM_P_FP64) { *lo = 0; *hi = 2; }

@@ -1004,8 +1004,11 @@ constexpr int kOzSpillWindows = 8192;
 constexpr int kOzStages = 3;
 constexpr int kOzXW = 4 * kOzSlices;                 // X words per lane per tile
 constexpr int kOzYW = 2 * kOzSlices;                 // Y words per lane per tile
-constexpr int kOzSW = kOzXW + 2 * kOzYW;             // ring words per lane per stage (1 x 2 tiles)
-__host__ __device__ constexpr int oz_ring_words_per_warp() { return kOzStages * 32 * kOzSW; }
+// ring words per lane per stage for passes of at most MAXN tiles (1 x MAXN)
+template <int MAXN>
+__host__ __device__ constexpr int oz_sw() { return kOzXW + MAXN * kOzYW; }
+template <int MAXN>
+__host__ __device__ constexpr int oz_ring_words_per_warp() { return kOzStages * 32 * oz_sw<MAXN>(); }
 // Packed tiles are chunk-major: chunk c (16 bytes) of lane L at word
 // c * 128 + 4 * L, so one 16-byte cp.async per lane reads 512 contiguous
 // bytes.  X tile: chunk p = plane p (registers v0..v3); Y tile: chunk c =
@@ -1015,11 +1018,12 @@ __host__ __device__ constexpr int oz_ring_words_per_warp() { return kOzStages * 
 // word c * 128 + 4 * L): each 16-byte copy and read of the warp covers 512
 // contiguous bytes of shared memory.
 
-// One pass over a 1 x NTC super tile (16 x 8*NTC output elements) at (mt0, nt0).
-template <int NTC>
+// One pass over a 1 x NTC super tile (16 x 8*NTC output elements) at (mt0, nt0),
+// staged through a ring laid out for passes of at most MAXN tiles.
+template <int NTC, int MAXN>
 __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
                                         uint32_t *ring) {
-    constexpr int ST = kOzStages, SW = kOzSW;
+    constexpr int ST = kOzStages, SW = oz_sw<MAXN>();
     const int32_t orc = a.out_blk_rc[q];
     const int R = rc_rows(orc), S = rc_cols(orc);
     const int MT = (R + 15) >> 4, NT = (S + 7) >> 3;
@@ -1216,23 +1220,32 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
     }
 }
 
+template <int MAXN>
 __device__ __forceinline__ void oz_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
-    const int pn = a.pass_nt == 1 ? 1 : 2;
+    const int pn = MAXN == 3 ? 3 : (a.pass_nt == 1 ? 1 : 2);
     for (int mt0 = 0; mt0 < MT; ++mt0)
         for (int nt0 = 0; nt0 < NT; nt0 += pn) {
-            if (pn == 2 && NT - nt0 >= 2) oz_pass<2>(a, q, lane, mt0, nt0, ring);
-            else oz_pass<1>(a, q, lane, mt0, nt0, ring);
+            const int left = NT - nt0;
+            if constexpr (MAXN == 3) {
+                if (left >= 3) oz_pass<3, MAXN>(a, q, lane, mt0, nt0, ring);
+                else if (left == 2) oz_pass<2, MAXN>(a, q, lane, mt0, nt0, ring);
+                else oz_pass<1, MAXN>(a, q, lane, mt0, nt0, ring);
+            } else {
+                if (pn == 2 && left >= 2) oz_pass<2, MAXN>(a, q, lane, mt0, nt0, ring);
+                else oz_pass<1, MAXN>(a, q, lane, mt0, nt0, ring);
+            }
         }
 }
 
 // Items [0, n0): a warp each on the tensor cores; items [n0, n_items): tiny
 // blocks one per lane with plain FP64 FMA (exact enough, no slicing needed).
+template <int MAXN>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t oz_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *ring = oz_smem + warp * oz_ring_words_per_warp();
+    uint32_t *ring = oz_smem + warp * oz_ring_words_per_warp<MAXN>();
     unsigned long long *ctr = a.work_counter;
     if (a.status && *a.status != 0) return;
     const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
@@ -1246,7 +1259,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
-            oz_item(a, q, lane, ring);
+            oz_item<MAXN>(a, q, lane, ring);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
             if (idx < a.n_items) cc_lane_dispatch<double>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
@@ -1597,13 +1610,24 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     const int tc_threads = (a.cta_warps == 2 ? 2 : 4) * 32;
     int grid = 0;
     if (a.prec == BSM_P_OZAKI) {
-        const size_t smem = sizeof(uint32_t) * (size_t)oz_ring_words_per_warp() * (tc_threads / 32);
-        e = cudaFuncSetAttribute(k_numeric_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) {
-            grid = persistent_grid(k_numeric_oz, a.n_items, smem, tc_threads, a.ctas_per_sm);
-            k_numeric_oz<<<grid, tc_threads, smem, s>>>(a);
+        // passes of up to 3 tiles take the instance with the wider ring
+        const bool wide = a.pass_nt == 3;
+        const size_t smem = sizeof(uint32_t) * (size_t)(wide ? oz_ring_words_per_warp<3>() : oz_ring_words_per_warp<2>()) *
+                            (tc_threads / 32);
+        if (wide) {
+            e = cudaFuncSetAttribute(k_numeric_oz<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) {
+                grid = persistent_grid(k_numeric_oz<3>, a.n_items, smem, tc_threads, a.ctas_per_sm);
+                k_numeric_oz<3><<<grid, tc_threads, smem, s>>>(a);
+            }
+        } else {
+            e = cudaFuncSetAttribute(k_numeric_oz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess) {
+                grid = persistent_grid(k_numeric_oz<2>, a.n_items, smem, tc_threads, a.ctas_per_sm);
+                k_numeric_oz<2><<<grid, tc_threads, smem, s>>>(a);
+            }
         }
-        li = NumericLaunch{BSM_K_OZAKI_MMA, -1, tc_threads, grid, 1, a.pass_nt == 1 ? 1 : 2};
+        li = NumericLaunch{BSM_K_OZAKI_MMA, -1, tc_threads, grid, 1, wide ? 3 : (a.pass_nt == 1 ? 1 : 2)};
     } else if (a.prec == BSM_P_FP64_DMMA && a.dtype == BSM_FP64) {
         grid = persistent_grid(k_numeric_dmma, a.n_items, 0, kThreadsNum, a.ctas_per_sm);
         k_numeric_dmma<<<grid, kThreadsNum, 0, s>>>(a);

@@ -589,7 +589,12 @@ __global__ void __launch_bounds__(kThreads) k_stack_count(int64_t nprod, const i
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
     for (int q = 0; q < kRadixRounds; ++q) {
         const int64_t p = base + (int64_t)q * kThreads + threadIdx.x;
-        if (p < nprod) atomicAdd(&h[product_shape(p, pa, pb, a_rc, b_rc, size_index, ns)], 1);
+        const bool valid = p < nprod;
+        const int d = valid ? (int)product_shape(p, pa, pb, a_rc, b_rc, size_index, ns) : kStackBins;
+        // one shared-memory atomic per distinct shape of the warp (one shape
+        // per warp is the common case: products of a C block share m and n)
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) {

@@ -37,6 +37,7 @@ def operands(bsm, oracle):
     ("bf16x6", {"cta_warps": 2, "pass_nt": 2}),
     ("bf16x3", {"pass_mt": 1, "pass_nt": 2, "ctas_per_sm": 2}),
     ("ozaki", {"cta_warps": 2, "pass_nt": 1, "ctas_per_sm": 2}),
+    ("ozaki", {"pass_nt": 3}),
     ("fp64", {"fp64_build": 1}),
     ("fp64", {"fp64_build": 2, "ctas_per_sm": 1}),
     ("fp64_dmma", {"pass_mt": 1, "pass_nt": 2, "ctas_per_sm": 3}),
