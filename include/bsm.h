@@ -240,11 +240,17 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  *                        flight share both operands' blocks in L2.  A
  *                        permutation of independent work: results do not
  *                        depend on it.  Not for BSM_P_TF32x3_PANEL.
+ *   BSM_TUNE_ENGINE      BSM_P_TF32x3 only: 0 (default) per-C-block mma.sync
+ *                        kernel; 1 the tcgen05 row-panel engine of
+ *                        BSM_P_TF32x3_PANEL wherever it applies (eager calls
+ *                        with the compensated sum, flush_every <= 0), the
+ *                        mma.sync kernel elsewhere -- for workloads where the
+ *                        tuner measured the engine faster
  * Values outside these ranges are BSM_ERR_ARG.
  */
 enum {
     BSM_TUNE_CTA_WARPS = 0, BSM_TUNE_CTAS_PER_SM = 1, BSM_TUNE_PASS_MT = 2, BSM_TUNE_PASS_NT = 3,
-    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_SCHED_TILE = 5, BSM_TUNE_COUNT = 6
+    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_SCHED_TILE = 5, BSM_TUNE_ENGINE = 6, BSM_TUNE_COUNT = 7
 };
 bsm_status bsm_set_tuning(int32_t prec, int32_t param, int32_t value);
 bsm_status bsm_get_tuning(int32_t prec, int32_t param, int32_t *value);

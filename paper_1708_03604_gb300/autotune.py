@@ -18,6 +18,8 @@ recorded by the library around the launch) on the caller's operands:
 * the order of the output blocks: by block row, or by 2-D tiles of ranked
   rows x ranked columns so that the blocks in flight share A's and B's
   blocks in L2;
+* for TF32x3, the engine: the per-C-block mma.sync kernel or the tcgen05
+  row-panel engine (where it applies);
 * for the split paths, the interval F of the FP64 running sum (FP32
   accumulation over at most F block products), the fastest F whose result is
   within ``err_target`` (relative Frobenius) of the FP64 path on the same
@@ -50,6 +52,8 @@ SEARCH = {
 for _p in SPLIT:
     SEARCH[_p] = [("cta_warps", [4, 2]), ("pass_mt", [2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 3, 4]),
                   TILES]
+# TF32x3 may also run on the tcgen05 row-panel engine where it applies
+SEARCH["tf32x3"] = SEARCH["tf32x3"] + [("engine", [0, 1])]
 FLUSH_CANDIDATES = [-1, 1, 2, 4, 8, 16]
 
 
@@ -59,11 +63,11 @@ def _shapes(A: bsm.Matrix, B: bsm.Matrix):
     return sorted(((m, n) for m in ms for n in ns), key=lambda t: (t[0] * t[1], t))
 
 
-def _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=0):
+def _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=0, phase="numeric"):
     t = []
     for _ in range(reps):
         bsm.multiply(1.0, A, B, 0.0, Cm, eps, prec=prec, build_stacks=False, flush_every=flush_every)
-        t.append(Cm.timings()["numeric"])
+        t.append(Cm.timings()[phase])
     return statistics.median(t)
 
 
@@ -110,6 +114,8 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
                 variants[f"{m}x{n}"] = 0
         params = {}
         for name, values in SEARCH.get(prec, []):
+            if name == "engine":
+                continue       # decided last, on the whole multiply's time
             chosen = values[0]
             bsm.bsm_set_tuning(prec, name, chosen)
             for v in values[1:]:
@@ -134,11 +140,27 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
             if fbest is not None:
                 flush = fbest[0]
                 best = min(best, fbest[1])
+        engine_trials = {}
+        if any(name == "engine" for name, _ in SEARCH.get(prec, [])):
+            # the engines differ in their preparation too: compare whole multiplies
+            bsm.bsm_set_tuning(prec, "engine", 0)
+            t0 = _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=flush or 0, phase="total")
+            bsm.bsm_set_tuning(prec, "engine", 1)
+            t1 = _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=0, phase="total")
+            panel_ran = Cm.engine() == "panel_tcgen05"
+            engine_trials = {"mma_sync_total_ms": t0, "panel_total_ms": t1 if panel_ran else None}
+            if panel_ran and t1 < t0 * (1.0 - gain):
+                params["engine"] = 1
+                flush = None       # the panel engine keeps its own compensated sum
+            else:
+                bsm.bsm_set_tuning(prec, "engine", 0)
+                params["engine"] = 0
         tuned_ms = _numeric_ms(A, B, eps, prec, reps, Cm, flush_every=flush or 0)
     finally:
         bsm.bsm_set_profiling(False)
     return {"prec": prec, "variants": variants, "params": params, "flush_every": flush,
-            "flush_trials": flush_trials, "numeric_ms": {"default": start, "tuned": tuned_ms},
+            "flush_trials": flush_trials, "engine_trials": engine_trials,
+            "numeric_ms": {"default": start, "tuned": tuned_ms},
             "workload": {"nbr": int(len(A.row_bs)), "block_sizes": sorted(set(int(x) for x in np.asarray(A.row_bs))),
                          "eps": eps}}
 

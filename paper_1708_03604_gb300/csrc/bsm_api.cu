@@ -2,6 +2,7 @@
 // validation and the orchestration of the symbolic, stack and numeric
 // kernels of the local block-sparse multiply (DBCSR, Bethune et al. 2017 §2).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -101,6 +102,9 @@ void tune_range(int prec, int param, int *lo, int *hi) {
         case BSM_TUNE_SCHED_TILE:
             if (prec != BSM_P_TF32x3_PANEL) { *lo = 0; *hi = 4096; }
             break;
+        case BSM_TUNE_ENGINE:
+            if (prec == BSM_P_TF32x3) { *lo = 0; *hi = 1; }
+            break;
     }
 }
 // the tuning of `prec` into the numeric launch arguments
@@ -153,18 +157,29 @@ size_t esize(int32_t dtype) { return dtype == BSM_FP64 ? 8 : 4; }
 
 bool same_vec(const std::vector<int32_t> &a, const std::vector<int32_t> &b) { return a == b; }
 
+// Phase marks of a multiply: CUDA events on the library stream when
+// profiling is on (bsm_get_timings), and NVTX ranges on the issuing host
+// thread always (no-ops unless a profiler is attached).
 struct Events {
     cudaEvent_t ev[BSM_T_COUNT + 1] = {};
     bool on = false;
+    bool range_open = false;
     void start() {
         on = g_prof;
         if (!on) return;
         for (auto &e : ev) cudaEventCreate(&e);
     }
     void mark(int idx) {
+        static const char *const names[BSM_T_COUNT + 1] = {"bsm norms",  "bsm symbolic count", "bsm fill",
+                                                           "bsm stacks", "bsm pack and order", "bsm numeric",
+                                                           "bsm post",   ""};
         if (on) cudaEventRecord(ev[idx], g_stream);
+        if (range_open) nvtxRangePop();
+        range_open = idx < BSM_T_COUNT;
+        if (range_open) nvtxRangePushA(names[idx]);
     }
     ~Events() {
+        if (range_open) nvtxRangePop();
         if (on)
             for (auto &e : ev) cudaEventDestroy(e);
     }
@@ -1265,8 +1280,13 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     const bool no_sync = opts.no_sync != 0;
     // BSM_P_TF32x3_PANEL: the tcgen05 row-panel engine where it applies, else
     // the mma.sync TF32x3 kernel (rprec: the precision of the mma.sync path)
-    const bool want_panel = opts.prec == BSM_P_TF32x3_PANEL;
-    if (want_panel && no_sync) return set_error(BSM_ERR_UNSUPPORTED, "BSM_P_TF32x3_PANEL does not run with no_sync");
+    // BSM_P_TF32x3 with the tuned engine 1 (and the compensated sum) also takes
+    // the row-panel engine where it applies
+    const bool tuned_panel = opts.prec == BSM_P_TF32x3 && !no_sync && opts.flush_every <= 0 &&
+                             tune_of(BSM_P_TF32x3)[BSM_TUNE_ENGINE] == 1;
+    const bool want_panel = opts.prec == BSM_P_TF32x3_PANEL || tuned_panel;
+    if (opts.prec == BSM_P_TF32x3_PANEL && no_sync)
+        return set_error(BSM_ERR_UNSUPPORTED, "BSM_P_TF32x3_PANEL does not run with no_sync");
     const int rprec = want_panel ? BSM_P_TF32x3 : opts.prec;
     const auto &pl = C->plan;
     if (no_sync) {
@@ -1391,7 +1411,9 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         }
         for (int64_t v : h_ccnt) max_ccnt = std::max(max_ccnt, v);
         if (nprod > INT32_MAX || nnzbC > INT32_MAX)
-            return set_error(BSM_ERR_UNSUPPORTED, "more than 2^31-1 products or C blocks");
+            return set_error(BSM_ERR_UNSUPPORTED, std::to_string(nprod) + " kept products and " +
+                                                      std::to_string(nnzbC) + " C blocks: more than 2^31-1 products "
+                                                      "or C blocks in one multiply");
         while (nchunk > 1 && symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 160 * 1024) nchunk >>= 1;
         if (symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 220 * 1024)
             return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");

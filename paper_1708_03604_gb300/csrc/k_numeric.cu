@@ -536,6 +536,19 @@ __device__ __forceinline__ void kahan_acc(float &hi, float &lo, float b) {
     hi = t;
 }
 
+// FP32 -> FP64 (exact).  Widening by integer bit operations instead of the
+// conversion instruction was measured no faster on GB300: the FP64 additions,
+// not the conversions, are what the FP64 running sum pays for.
+__device__ __forceinline__ double widen(float f) { return (double)f; }
+
+// The value of a compensated pair (hi, lo) plus a last partial sum b, in
+// FP64: b is first added into the pair in FP32 (one more compensated step),
+// then the pair is widened and added once.
+__device__ __forceinline__ double pair_total(float hi, float lo, float b) {
+    kahan_acc(hi, lo, b);
+    return widen(hi) + widen(lo);
+}
+
 // One pass over a super tile of MTC x NTC (at most 2 x 3) fragment tiles
 // starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
 // FF: cross-product sum as a compensated float pair (Kahan after every |F| block
@@ -683,7 +696,7 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
 #pragma unroll
                             for (int v = 0; v < 4; ++v) {
                                 if constexpr (FF) kahan_acc(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
-                                else s64[i][j][v] += (double)acc[i][j][v];
+                                else s64[i][j][v] += widen(acc[i][j][v]);
                                 acc[i][j][v] = 0.f;
                             }
                 }
@@ -706,9 +719,9 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                 const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
                 if (r < R && c < S) {
                     double sum;
-                    if constexpr (FF) sum = ((double)shi[i][j][v] + (double)slo[i][j][v]) + (double)acc[i][j][v];
-                    else sum = s64[i][j][v] + (double)acc[i][j][v];
-                    double val = a.alpha * sum;
+                    if constexpr (FF) sum = pair_total(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
+                    else sum = s64[i][j][v] + widen(acc[i][j][v]);
+                    double val = a.alpha == 1.0 ? sum : a.alpha * sum;
                     const int64_t e = (int64_t)r * S + c;
                     if (a.dtype == BSM_FP64) {
                         if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
@@ -817,7 +830,7 @@ __device__ __forceinline__ void cs_lane_item(const NumericArgs &a, int64_t q) {
 #pragma unroll
             for (int e = 0; e < L; ++e) {
                 if constexpr (FF) kahan_acc(shi[e], slo[e], acc[e]);
-                else s64[e] += (double)acc[e];
+                else s64[e] += widen(acc[e]);
                 acc[e] = 0.f;
             }
         }
@@ -826,9 +839,9 @@ __device__ __forceinline__ void cs_lane_item(const NumericArgs &a, int64_t q) {
     for (int e = 0; e < L; ++e) {
         if (e < RS) {
             double sum;
-            if constexpr (FF) sum = ((double)shi[e] + (double)slo[e]) + (double)acc[e];
-            else sum = s64[e] + (double)acc[e];
-            double val = a.alpha * sum;
+            if constexpr (FF) sum = pair_total(shi[e], slo[e], acc[e]);
+            else sum = s64[e] + widen(acc[e]);
+            double val = a.alpha == 1.0 ? sum : a.alpha * sum;
             if (a.dtype == BSM_FP64) {
                 if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
                 static_cast<double *>(a.out_data)[out_off + e] = val;
@@ -907,7 +920,7 @@ __device__ __forceinline__ void cs_lane_fixed(const NumericArgs &a, int64_t q) {
 #pragma unroll
                 for (int c = 0; c < S; ++c) {
                     if constexpr (FF) kahan_acc(shi[r][c], slo[r][c], acc[r][c]);
-                    else s64[r][c] += (double)acc[r][c];
+                    else s64[r][c] += widen(acc[r][c]);
                     acc[r][c] = 0.f;
                 }
         }
@@ -918,9 +931,9 @@ __device__ __forceinline__ void cs_lane_fixed(const NumericArgs &a, int64_t q) {
         for (int c = 0; c < S; ++c) {
             const int e = r * S + c;
             double sum;
-            if constexpr (FF) sum = ((double)shi[r][c] + (double)slo[r][c]) + (double)acc[r][c];
-            else sum = s64[r][c] + (double)acc[r][c];
-            double val = a.alpha * sum;
+            if constexpr (FF) sum = pair_total(shi[r][c], slo[r][c], acc[r][c]);
+            else sum = s64[r][c] + widen(acc[r][c]);
+            double val = a.alpha == 1.0 ? sum : a.alpha * sum;
             if (a.dtype == BSM_FP64) {
                 if (old >= 0) val = fma(a.beta, static_cast<const double *>(a.old_data)[old + e], val);
                 static_cast<double *>(a.out_data)[out_off + e] = val;

@@ -93,6 +93,31 @@ def test_schedule_tiles_permute_work_only(bsm, prec):
         autotune.reset(prec)
 
 
+def test_engine_knob_runs_the_panel_where_it_applies(bsm, oracle):
+    """BSM_TUNE_ENGINE = 1: BSM_P_TF32x3 runs on the tcgen05 row-panel engine
+    for uniform blocks with nothing filtered, on the mma.sync kernel where the
+    engine does not apply (mixed sizes) or when an FP64 running sum is asked
+    for; results within 1e-6 of the oracle either way."""
+    from paper_1708_03604_gb300 import autotune
+    u = I.large_banded_23(nb=60, occ=0.1, eps=1e-8)
+    A, B = bsm.Matrix.from_host(u["A"]), bsm.Matrix.from_host(u["B"])
+    ref = oracle.multiply(1.0, u["A"], u["B"], eps=u["eps"])
+    try:
+        bsm.bsm_set_tuning("tf32x3", "engine", 1)
+        Cp = bsm.multiply(1.0, A, B, eps=u["eps"], prec="tf32x3")
+        assert Cp.engine() == "panel_tcgen05" and Cp.launch_config()["kernel"] == "panel_tcgen05"
+        assert rel_fro(Cp.data_host(), ref.C.data) <= 1e-6
+        Cf = bsm.multiply(1.0, A, B, eps=u["eps"], prec="tf32x3", flush_every=4)
+        assert Cf.engine() == "split_mma"
+        assert rel_fro(Cf.data_host(), ref.C.data) <= 1e-6
+        w = I.mixed_banded(nb=120, occ=0.1, eps=1e-6)
+        Cm = bsm.multiply(1.0, bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"]), eps=w["eps"],
+                          prec="tf32x3")
+        assert Cm.engine() == "split_mma"
+    finally:
+        autotune.reset("tf32x3")
+
+
 def test_knob_ranges_are_checked(bsm):
     with pytest.raises(bsm.BsmError):
         bsm.bsm_set_tuning("fp64", "cta_warps", 2)        # the FP64 kernels run 4 warps per CTA
@@ -106,6 +131,8 @@ def test_knob_ranges_are_checked(bsm):
         bsm.bsm_set_tuning("tf32x3_panel", "ctas_per_sm", 1)
     with pytest.raises(bsm.BsmError):
         bsm.bsm_set_tuning("fp64", "sched_tile", 4)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("bf16x6", "engine", 1)
 
 
 def test_tuned_table_roundtrip(bsm, operands, tmp_path):
@@ -114,7 +141,7 @@ def test_tuned_table_roundtrip(bsm, operands, tmp_path):
     try:
         table = autotune.tune(A, B, 0.3, prec="tf32x3", reps=1)
         assert table["numeric_ms"]["tuned"] > 0
-        assert set(table["params"]) == {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm", "sched_tile"}
+        assert set(table["params"]) == {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm", "sched_tile", "engine"}
         # the flush interval the tuner chose keeps the error within its target
         if table["flush_every"] is not None:
             assert table["flush_trials"][str(table["flush_every"])]["rel_fro_err_vs_fp64_path"] <= 1e-6
