@@ -17,7 +17,9 @@ from types import SimpleNamespace
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libbsm.so")
+# BSM_DEBUG=1 in the environment loads the debug build (device-side bounds
+# checks in the numeric kernels; built with build.build(debug=True))
+LIB_PATH = os.path.join(_PKG, "libbsm_debug.so" if os.environ.get("BSM_DEBUG") == "1" else "libbsm.so")
 
 # bsm_status
 BSM_OK, BSM_ERR_ARG, BSM_ERR_BLOCKING, BSM_ERR_CAPACITY, BSM_ERR_ALLOC, BSM_ERR_CUDA, BSM_ERR_TIMEOUT, \

@@ -1609,8 +1609,19 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     }
     na.item_order = order;
     apply_tuning(rprec, na);
+    na.n_prod = nprod;
+    na.x_nnzb = A->nnzb; na.y_nnzb = B->nnzb;
+    na.x_len = A->data_len; na.y_len = B->data_len;
+    na.out_len = lenC; na.old_len = use_old ? C->data_len : 0;
+    na.x_pack_words = packA_words; na.y_pack_words = packB_words;
     ev.mark(5);
     if ((st = cuda_check(launch_numeric(na, g_stream, &nl), "numeric"))) return st;
+#ifdef BSM_DEBUG
+    if (!no_sync)
+        if (const uint32_t bits = numeric_debug_bits(g_stream))
+            return set_error(BSM_ERR_CUDA, "debug bounds check of the numeric kernel failed (bits " +
+                                               std::to_string(bits) + ")");
+#endif
     ev.mark(6);
     }
     if (no_sync) return BSM_OK;  // C's storage, counts and plan are unchanged
@@ -1775,12 +1786,15 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         const int xt = side == 0 ? 0 : 1, yt = side == 0 ? 1 : 0;
         Packed pkX, pkY;
         OzLines olX, olY;
+        int64_t wx_words = 0, wy_words = 0;
         if (tc && nprod > 0) {
             if ((st = pack_prepare(sc, X, 0, xt, kprec, pkX))) return st;
             if ((st = pack_prepare(sc, Y, 1, yt, kprec, pkY))) return st;
             const int64_t *src[2] = {pkX.off + X->nnzb, pkY.off + Y->nnzb};
             if ((st = read_words(src, 2))) return st;
             const int64_t wx = g_host[0], wy = g_host[1];
+            wx_words = wx;
+            wy_words = wy;
             if ((st = pack_fill(sc, X, 0, xt, kprec, pkX, wx, &olX))) return st;
             if ((st = pack_fill(sc, Y, 1, yt, kprec, pkY, wy, &olY))) return st;
         }
@@ -1825,7 +1839,17 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         }
         na.item_order = item_order;
         apply_tuning(opts.prec, na);
+        na.n_prod = nprod;
+        na.x_nnzb = X->nnzb; na.y_nnzb = Y->nnzb;
+        na.x_len = X->data_len; na.y_len = Y->data_len;
+        na.out_len = OUT->data_len; na.old_len = 0;
+        na.x_pack_words = pkX.words ? wx_words : 0; na.y_pack_words = pkY.words ? wy_words : 0;
         if ((st = cuda_check(launch_numeric(na, g_stream), "adjoint numeric"))) return st;
+#ifdef BSM_DEBUG
+        if (const uint32_t bits = numeric_debug_bits(g_stream))
+            return set_error(BSM_ERR_CUDA, "debug bounds check of the adjoint kernel failed (bits " +
+                                               std::to_string(bits) + ")");
+#endif
     }
     return BSM_OK;
 }

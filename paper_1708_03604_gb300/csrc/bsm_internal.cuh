@@ -279,7 +279,16 @@ struct NumericArgs {
     int32_t cta_warps;          // warps per CTA (4 or 8; mma.sync kernels)
     int32_t ctas_per_sm;        // persistent CTAs per SM (0: as many as fit)
     int32_t fp64_build;         // FP64 FMA kernel build: 0 by the largest block, 1 narrow, 2 wide
+    // sizes the debug build's bounds checks test every item against
+    int64_t n_prod;             // entries of px / py
+    int64_t x_nnzb, y_nnzb;     // operand blocks
+    int64_t x_len, y_len;       // operand elements
+    int64_t out_len, old_len;   // output elements, old output elements (beta != 0)
+    int64_t x_pack_words, y_pack_words;  // packed planes (0: none)
 };
+// Debug builds (BSM_DEBUG): bits of the bounds checks of the last numeric
+// launch (read and cleared; 0 in release builds).
+uint32_t numeric_debug_bits(cudaStream_t s);
 // What a numeric launch ran (bsm_get_launch_config).
 struct NumericLaunch {
     int32_t kernel;     // BSM_K_* of include/bsm.h

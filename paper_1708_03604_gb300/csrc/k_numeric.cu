@@ -28,6 +28,78 @@ namespace bsm {
 
 namespace {
 
+// ---------------------------------------------------------------------
+// Debug builds (-DBSM_DEBUG): before an item is computed, its output block
+// and every product's operand blocks are checked against the arrays' sizes;
+// a violation sets a bit in g_dbg_bits and the item is skipped (no access
+// outside the arrays, no trap).  Bits: 1 item or product range, 2 operand
+// block index, 4 operand block extent, 8 operand shapes that do not chain,
+// 16 packed-plane extent, 32 output block extent.
+// ---------------------------------------------------------------------
+#ifdef BSM_DEBUG
+__device__ unsigned int g_dbg_bits;
+
+__device__ uint32_t dbg_product_bits(const NumericArgs &a, int64_t p, int R, int S) {
+    const int32_t ix = a.px[p], iy = a.py[p];
+    if (ix < 0 || ix >= a.x_nnzb || iy < 0 || iy >= a.y_nnzb) return 2u;
+    const int32_t xrc = a.x_blk_rc[ix], yrc = a.y_blk_rc[iy];
+    const int64_t xo = a.x_blk_off[ix], yo = a.y_blk_off[iy];
+    uint32_t bits = 0;
+    if (xo < 0 || xo + (int64_t)rc_rows(xrc) * rc_cols(xrc) > a.x_len || yo < 0 ||
+        yo + (int64_t)rc_rows(yrc) * rc_cols(yrc) > a.y_len)
+        bits |= 4u;
+    const int xr = a.x_trans ? rc_cols(xrc) : rc_rows(xrc), xt = a.x_trans ? rc_rows(xrc) : rc_cols(xrc);
+    const int yt = a.y_trans ? rc_cols(yrc) : rc_rows(yrc), ys = a.y_trans ? rc_rows(yrc) : rc_cols(yrc);
+    if (xr != R || ys != S || xt != yt) bits |= 8u;
+    if (a.x_pack && (a.x_pack_off[ix] < 0 || a.x_pack_off[ix + 1] > a.x_pack_words)) bits |= 16u;
+    if (a.y_pack && (a.y_pack_off[iy] < 0 || a.y_pack_off[iy + 1] > a.y_pack_words)) bits |= 16u;
+    return bits;
+}
+
+__device__ uint32_t dbg_item_bits(const NumericArgs &a, int64_t q) {
+    if (q < 0 || q >= a.n_items) return 1u;
+    const int64_t p0 = a.seg_ptr[q], p1 = a.seg_ptr[q + 1];
+    if (p0 < 0 || p1 < p0 || p1 > a.n_prod) return 1u;
+    const int32_t orc = a.out_blk_rc[q];
+    const int64_t rs = (int64_t)rc_rows(orc) * rc_cols(orc);
+    uint32_t bits = 0;
+    if (a.out_blk_off[q] < 0 || a.out_blk_off[q] + rs > a.out_len) bits |= 32u;
+    if (a.beta != 0.0 && a.old_off && a.old_off[q] >= 0 && a.old_off[q] + rs > a.old_len) bits |= 32u;
+    return bits;
+}
+
+// all lanes of the warp: true when item q may be computed
+__device__ bool dbg_item_ok_warp(const NumericArgs &a, int64_t q, int lane) {
+    uint32_t bits = dbg_item_bits(a, q);
+    if (bits == 0) {
+        const int32_t orc = a.out_blk_rc[q];
+        for (int64_t p = a.seg_ptr[q] + lane; p < a.seg_ptr[q + 1]; p += 32)
+            bits |= dbg_product_bits(a, p, rc_rows(orc), rc_cols(orc));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+    if (bits && lane == 0) atomicOr(&g_dbg_bits, bits);
+    return bits == 0;
+}
+
+// one lane: true when item q may be computed
+__device__ bool dbg_item_ok_lane(const NumericArgs &a, int64_t q) {
+    uint32_t bits = dbg_item_bits(a, q);
+    if (bits == 0) {
+        const int32_t orc = a.out_blk_rc[q];
+        for (int64_t p = a.seg_ptr[q]; p < a.seg_ptr[q + 1]; ++p) bits |= dbg_product_bits(a, p, rc_rows(orc), rc_cols(orc));
+    }
+    if (bits) atomicOr(&g_dbg_bits, bits);
+    return bits == 0;
+}
+#define BSM_DBG_WARP_SKIP(a, q, lane) \
+    if (!dbg_item_ok_warp(a, q, lane)) continue;
+#define BSM_DBG_LANE_OK(a, q) dbg_item_ok_lane(a, q)
+#else
+#define BSM_DBG_WARP_SKIP(a, q, lane)
+#define BSM_DBG_LANE_OK(a, q) true
+#endif
+
 constexpr int kWarpsPerCta = 4;             // default warps per CTA
 constexpr int kThreadsNum = kWarpsPerCta * 32;
 
@@ -314,12 +386,13 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_cc(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            BSM_DBG_WARP_SKIP(a, q, lane)
             cc_dispatch<T, BUILD>(a, q, lane);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
             if (idx < a.n_items) {
                 const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                cc_lane_dispatch<T, BUILD>(a, q);
+                if (BSM_DBG_LANE_OK(a, q)) cc_lane_dispatch<T, BUILD>(a, q);
             }
         }
     }
@@ -447,6 +520,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_dmma(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            BSM_DBG_WARP_SKIP(a, q, lane)
             const int32_t orc = a.out_blk_rc[q];
             if (rc_rows(orc) >= 8 && rc_cols(orc) >= 8) dmma_item(a, q, lane);
             else cc_dispatch<double, kCcNarrow>(a, q, lane);
@@ -454,7 +528,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_dmma(NumericArgs a) {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
             if (idx < a.n_items) {
                 const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                cc_lane_dispatch<double, kCcNarrow>(a, q);
+                if (BSM_DBG_LANE_OK(a, q)) cc_lane_dispatch<double, kCcNarrow>(a, q);
             }
         }
     }
@@ -978,10 +1052,14 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            BSM_DBG_WARP_SKIP(a, q, lane)
             tc_item<PREC, FF>(a, q, lane, ring);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
-            if (idx < a.n_items) cs_lane_dispatch<PREC, FF>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
+            if (idx < a.n_items) {
+                const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
+                if (BSM_DBG_LANE_OK(a, q)) cs_lane_dispatch<PREC, FF>(a, q);
+            }
         }
     }
 }
@@ -1272,10 +1350,14 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
         if (t < n0) {
             int64_t q = t;
             if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+            BSM_DBG_WARP_SKIP(a, q, lane)
             oz_item<MAXN>(a, q, lane, ring);
         } else {
             const int64_t idx = n0 + (t - n0) * 32 + lane;
-            if (idx < a.n_items) cc_lane_dispatch<double>(a, (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu));
+            if (idx < a.n_items) {
+                const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
+                if (BSM_DBG_LANE_OK(a, q)) cc_lane_dispatch<double>(a, q);
+            }
         }
     }
 }
@@ -1677,6 +1759,23 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     if (info) *info = li;
     count_launch(1);
     return cudaGetLastError();
+}
+
+uint32_t numeric_debug_bits(cudaStream_t s) {
+#ifdef BSM_DEBUG
+    uint32_t bits = 0;
+    const uint32_t zero = 0;
+    if (cudaMemcpyFromSymbolAsync(&bits, g_dbg_bits, sizeof(bits), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyToSymbolAsync(g_dbg_bits, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return 0x80000000u;
+    }
+    return bits;
+#else
+    (void)s;
+    return 0;
+#endif
 }
 
 cudaError_t launch_split_plain(const bsm_mat *M, int prec, float *out, cudaStream_t s) {

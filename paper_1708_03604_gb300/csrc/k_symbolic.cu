@@ -655,6 +655,32 @@ __global__ void k_stack_triples(int64_t nprod, const int32_t *order, const int32
     }
 }
 
+// One block shape: the stack is the product list itself, in order.  Each
+// thread writes the triples of two consecutive products as three 16-byte
+// stores (48 contiguous bytes, 16-byte aligned).
+__global__ void k_stack_single(int64_t nprod, const int32_t *pa, const int32_t *pb, const int32_t *pc,
+                               const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
+                               int64_t *triples, int64_t *counts) {
+    const int64_t npair = (nprod + 1) / 2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[0] = nprod;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npair;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = 2 * t;
+        const int64_t a0 = a_off[pa[p]], b0 = b_off[pb[p]], c0 = c_off[pc[p]];
+        if (p + 1 < nprod) {
+            const int64_t a1 = a_off[pa[p + 1]], b1 = b_off[pb[p + 1]], c1 = c_off[pc[p + 1]];
+            longlong2 *dst = reinterpret_cast<longlong2 *>(triples + 3 * p);
+            dst[0] = make_longlong2(a0, b0);
+            dst[1] = make_longlong2(c0, a1);
+            dst[2] = make_longlong2(b1, c1);
+        } else {
+            triples[3 * p + 0] = a0;
+            triples[3 * p + 1] = b0;
+            triples[3 * p + 2] = c0;
+        }
+    }
+}
+
 // Counts of keys < nbins.  Few bins (shape ids): a per-CTA shared-memory
 // histogram merged with one global atomic per bin and CTA; many bins (block
 // indices): global atomics, which then rarely collide.
@@ -890,6 +916,12 @@ cudaError_t launch_stacks_direct(int64_t nprod, const int32_t *pa, const int32_t
                                  int32_t nbins, const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
                                  int64_t *triples, int64_t *counts, int64_t *tmp, cudaStream_t s) {
     if (nprod == 0 || nbins > kStackBins) return nprod == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    if (nbins == 1) {  // every product has the one shape: no counting, no scatter
+        k_stack_single<<<grid_for((nprod + 1) / 2), kThreads, 0, s>>>(nprod, pa, pb, pc, a_off, b_off, c_off, triples,
+                                                                       counts);
+        count_launch(1);
+        return cudaGetLastError();
+    }
     const int64_t nt = (nprod + kRadixTile - 1) / kRadixTile;
     const int64_t h = (int64_t)nbins * nt;
     int64_t *hist = tmp, *offs = tmp + h, *stmp = tmp + 2 * h + 1;  // offs holds h+1 entries

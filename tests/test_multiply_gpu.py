@@ -190,6 +190,19 @@ def test_autotune_table_roundtrip(bsm, oracle, tmp_path):
         autotune.reset("fp64", sizes)
 
 
+@pytest.mark.parametrize("nb", [29, 40])
+def test_single_shape_stacks(bsm, oracle, nb):
+    """One block shape: the stack is the product list in order (the direct
+    path), for an odd and an even product count."""
+    w = I.uniform_23(nb=nb, occ=0.2)
+    Cg, ref, _, _ = _run(bsm, oracle, w["A"], w["B"], 0.0)
+    shapes, ptr, trip = Cg.stacks()
+    s_ref, p_ref, t_ref = oracle.stacks(w["A"], w["B"], ref.C, ref.prods)
+    np.testing.assert_array_equal(shapes, s_ref)
+    np.testing.assert_array_equal(ptr, p_ref)
+    np.testing.assert_array_equal(trip, t_ref)
+
+
 def test_ragged_sizes_and_large_blocks(bsm, oracle):
     # block sizes 1..40 (several fragment tiles and element passes per block)
     rng = np.random.default_rng(5)

@@ -87,6 +87,7 @@ def test_uniform_23_full(env, oracle):
     shapes, ptr, trip = Cm.stacks()
     s_ref, p_ref, t_ref = oracle.stacks(w["A"], w["B"], ref.C, ref.prods)
     np.testing.assert_array_equal(shapes, s_ref)
+    np.testing.assert_array_equal(ptr, p_ref)
     np.testing.assert_array_equal(trip, t_ref)
 
 
