@@ -162,6 +162,22 @@ bsm_status bsm_set_allocator(bsm_alloc_fn alloc, bsm_free_fn free_fn, void *ctx)
  * complete at once); process-wide. */
 bsm_status bsm_set_wait_limit(double seconds);
 
+/* Most kept products one pass of bsm_multiply holds, in [1, 2^31 - 1]
+ * (default 2^31 - 1, the limit of the 32-bit product indices; process-wide).
+ * A multiply whose kept products exceed it runs its fill and numeric phases
+ * row panel by row panel of C, each panel a run of whole C block rows with at
+ * most this many products, so that the product list held at once stays
+ * within the limit (the row-panel chunking of the local multiply, Section
+ * 2).  The result is bit for bit that of one pass (every C block is computed
+ * by the same kernel from the same products in the same order).  Such a C
+ * keeps its pattern, data, counts and timings but no product list: no
+ * stacks, no bsm_get_products list, no bsm_multiply_backward and no no_sync
+ * replay; the tcgen05 row-panel engine does not take it (the mma.sync TF32x3
+ * kernel runs instead).  A single C block row with more kept products than
+ * the limit gives BSM_ERR_CAPACITY.  Exists for products beyond 2^31 and so
+ * that tests can force the panels with a small limit. */
+bsm_status bsm_set_product_limit(int64_t max_products);
+
 /* Arithmetic units bsm_measure_peak can time. */
 enum {
     BSM_U_FP64_FMA = 0,   /* FP64 fused multiply-add on the CUDA cores (DFMA)        */

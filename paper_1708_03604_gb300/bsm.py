@@ -43,7 +43,8 @@ EXPORTS = ["bsm_last_error", "bsm_set_stream", "bsm_set_profiling", "bsm_get_lau
            "bsm_get_stacks", "bsm_add", "bsm_count_products_static", "bsm_borrow_data", "bsm_add_backward",
            "bsm_get_status", "bsm_set_variant", "bsm_get_variant", "bsm_get_engine", "bsm_set_allocator",
            "bsm_get_allocator_stats", "bsm_measure_peak",
-           "bsm_set_wait_limit", "bsm_set_tuning", "bsm_get_tuning", "bsm_get_launch_config"]
+           "bsm_set_wait_limit", "bsm_set_tuning", "bsm_get_tuning", "bsm_get_launch_config",
+           "bsm_set_product_limit"]
 
 
 class BsmError(RuntimeError):
@@ -112,6 +113,7 @@ def lib() -> C.CDLL:
         "bsm_get_allocator_stats": ([_P(_i64)], _i32),
         "bsm_measure_peak": ([_i32, _i32, _P(_f64)], _i32),
         "bsm_set_wait_limit": ([_f64], _i32),
+        "bsm_set_product_limit": ([_i64], _i32),
         "bsm_set_tuning": ([_i32, _i32, _i32], _i32),
         "bsm_get_tuning": ([_i32, _i32, _P(_i32)], _i32),
         "bsm_get_launch_config": ([_vp, _P(_i32)], _i32),
@@ -198,6 +200,12 @@ def measure_peak(unit: str, reps: int = 5) -> float:
     v = _f64()
     _check(lib().bsm_measure_peak(PEAK_UNITS[unit], int(reps), C.byref(v)))
     return v.value
+
+
+def set_product_limit(max_products: int = 2**31 - 1):
+    """Most kept products one pass of a multiply holds; above it the multiply
+    runs row panel by row panel of C (no product list is kept)."""
+    _check(lib().bsm_set_product_limit(int(max_products)))
 
 
 def _check(st: int):

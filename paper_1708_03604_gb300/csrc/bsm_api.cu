@@ -25,6 +25,8 @@ bool g_prof = false;
 bool g_pool_configured = false;
 // limit of the panel kernel's main-loop waits (bsm_set_wait_limit)
 std::atomic<unsigned long long> g_wait_ns{2000000000ull};
+// kept products one pass of a multiply holds (bsm_set_product_limit)
+std::atomic<int64_t> g_product_limit{INT32_MAX};
 int64_t *g_host = nullptr;  // pinned host words for small device->host reads
 // numeric variant per (precision, rows, cols) of the output block; -1 = the
 // library default (see variant_of)
@@ -447,6 +449,7 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
                        const int32_t *col_rank = nullptr, int32_t ncols = 0, int32_t tile = 0) {
     if (uses_cores) *uses_cores = false;
     *order = nullptr;
+    if (n_marked) *n_marked = nullptr;
     if (n <= 1) return BSM_OK;
     std::vector<int32_t> sizes(rsz);
     sizes.insert(sizes.end(), csz.begin(), csz.end());
@@ -455,7 +458,6 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     const int32_t ns = (int32_t)sizes.size();
     if ((int64_t)ns * ns > (1 << 16)) return BSM_OK;  // too many shapes: natural order
     std::vector<int32_t> sidx(kMaxBlockDim + 1, 0), table((size_t)ns * ns);
-    if (n_marked) *n_marked = nullptr;
     for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
     std::vector<std::pair<int64_t, int32_t>> cls;
     for (int32_t r = 0; r < ns; ++r)
@@ -976,6 +978,13 @@ bsm_status bsm_set_wait_limit(double seconds) {
     return BSM_OK;
 }
 
+bsm_status bsm_set_product_limit(int64_t max_products) {
+    if (max_products < 1 || max_products > INT32_MAX)
+        return set_error(BSM_ERR_ARG, "product limit outside [1, 2^31-1]");
+    g_product_limit.store(max_products, std::memory_order_relaxed);
+    return BSM_OK;
+}
+
 bsm_status bsm_get_allocator_stats(int64_t *outstanding) {
     if (!outstanding) return set_error(BSM_ERR_ARG, "outstanding is NULL");
     *outstanding = hook_blocks_outstanding();
@@ -1378,6 +1387,10 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     }
     int64_t nprod, nnzbC, lenC, nfilt, mnk, packA_words = 0, packB_words = 0, max_ccnt = 0;
     int nchunk = 8;
+    // row panels of a multiply above the product limit (empty: one pass)
+    std::vector<int32_t> panel_rows;
+    std::vector<int64_t> h_pp, h_cp;
+    int64_t panel_max = 0;
     if (no_sync) {
         // sizes of the eager call; the device checks that they hold
         nprod = pl.nprod; nnzbC = pl.nnzb; lenC = pl.len; nfilt = pl.nfilt; mnk = pl.mnk;
@@ -1410,16 +1423,38 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             packB_words = g_host[6];
         }
         for (int64_t v : h_ccnt) max_ccnt = std::max(max_ccnt, v);
-        if (nprod > INT32_MAX || nnzbC > INT32_MAX)
-            return set_error(BSM_ERR_UNSUPPORTED, std::to_string(nprod) + " kept products and " +
-                                                      std::to_string(nnzbC) + " C blocks: more than 2^31-1 products "
-                                                      "or C blocks in one multiply");
+        if (nnzbC > INT32_MAX)
+            return set_error(BSM_ERR_UNSUPPORTED, std::to_string(nnzbC) + " C blocks: more than 2^31-1 in one multiply");
+        // more kept products than one pass holds: row panels of C, each within the limit
+        const int64_t plimit = g_product_limit.load(std::memory_order_relaxed);
+        if (nprod > plimit) {
+            h_pp.resize((size_t)nbr + 1);
+            h_cp.resize((size_t)nbr + 1);
+            e = cudaMemcpyAsync(h_pp.data(), prod_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyDeviceToHost, g_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_cp.data(), crow_ptr, sizeof(int64_t) * (nbr + 1), cudaMemcpyDeviceToHost, g_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+            if ((st = cuda_check(e, "read row pointers"))) return st;
+            panel_rows.push_back(0);
+            for (int32_t r = 0; r < nbr;) {
+                if (h_pp[r + 1] - h_pp[r] > plimit)
+                    return set_error(BSM_ERR_CAPACITY, "C block row " + std::to_string(r) + " has " +
+                                                           std::to_string(h_pp[r + 1] - h_pp[r]) +
+                                                           " kept products, above the product limit of one pass");
+                int32_t r1 = r + 1;
+                while (r1 < nbr && h_pp[r1 + 1] - h_pp[r] <= plimit) ++r1;
+                panel_max = std::max(panel_max, h_pp[r1] - h_pp[r]);
+                panel_rows.push_back(r1);
+                r = r1;
+            }
+        }
         while (nchunk > 1 && symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 160 * 1024) nchunk >>= 1;
         if (symbolic_fill_smem_bytes(nwords, (int32_t)max_ccnt, nchunk) > 220 * 1024)
             return set_error(BSM_ERR_UNSUPPORTED, "a C block row has too many blocks for the fill phase");
     }
+    const bool chunked = !panel_rows.empty();
     int32_t panel_s = 0;
-    const bool use_panel = want_panel && A->dtype == BSM_FP64 && nfilt == 0 && panel_blocking(A, B, &panel_s) &&
+    const bool use_panel = want_panel && !chunked && A->dtype == BSM_FP64 && nfilt == 0 && panel_blocking(A, B, &panel_s) &&
                            panel_tile_smem((B->nbc + panel_tile_cols() - 1) / panel_tile_cols()) <= 200 * 1024;
     ev.mark(2);
 
@@ -1431,9 +1466,10 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         c_col = C->col_idx; c_off = C->blk_off; c_rc = C->blk_rc; cptr = C->cptr;
         pa = C->pa; pb = C->pb; pc = C->pc; c_data = C->data;
     } else {
+        const int64_t nprod_alloc = chunked ? panel_max : nprod;  // products held at once
         if ((st = sc.get(&c_col, nnzbC)) || (st = sc.get(&c_off, nnzbC)) || (st = sc.get(&c_rc, nnzbC)) ||
-            (st = sc.get(&cptr, (size_t)nnzbC + 1)) || (st = sc.get(&pa, nprod)) || (st = sc.get(&pb, nprod)) ||
-            (st = sc.get(&pc, nprod)))
+            (st = sc.get(&cptr, (size_t)nnzbC + 1)) || (st = sc.get(&pa, nprod_alloc)) ||
+            (st = sc.get(&pb, nprod_alloc)) || (st = sc.get(&pc, nprod_alloc)))
             return st;
         if (use_old && (st = sc.get(&old_off, nnzbC))) return st;
         if ((st = dalloc(&c_data, (size_t)lenC * esize(C->dtype)))) return st;
@@ -1445,21 +1481,29 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (by_cols) {
         if (no_sync && !B->t_ptr) return set_error(BSM_ERR_ARG, "no_sync: B's column copy is missing");
         if ((st = ensure_transpose(B))) return st;
-        e = launch_symbolic_fill_cols(sa, bitmaps, fo, B->t_ptr, B->t_row, B->t_blk, g_stream);
-    } else {
-        e = launch_symbolic_fill(sa, bitmaps, fo, g_stream);
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(cptr + nnzbC, prod_ptr + nbr, sizeof(int64_t), cudaMemcpyDeviceToDevice, g_stream);
-    if (e == cudaSuccess && no_sync) e = launch_copy_i64_if_ok(nbr + 1, crow_ptr, C->row_ptr, C->status, g_stream);
-    if ((st = cuda_check(e, "symbolic fill"))) return st;
+    // rows [r0, r1) of C's pattern and of the product list (offsets relative to prod_ptr[r0])
+    auto fill_rows = [&](int32_t r0, int32_t r1, int64_t prod_base) -> cudaError_t {
+        FillOut f = fo;
+        f.row0 = r0;
+        f.prod_base = prod_base;
+        return by_cols ? launch_symbolic_fill_cols(sa, bitmaps, f, B->t_ptr, B->t_row, B->t_blk, g_stream, r1 - r0)
+                       : launch_symbolic_fill(sa, bitmaps, f, g_stream, r1 - r0);
+    };
+    if (!chunked) {  // a chunked multiply fills each row panel right before its numeric pass
+        e = fill_rows(0, nbr, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cptr + nnzbC, prod_ptr + nbr, sizeof(int64_t), cudaMemcpyDeviceToDevice, g_stream);
+        if (e == cudaSuccess && no_sync) e = launch_copy_i64_if_ok(nbr + 1, crow_ptr, C->row_ptr, C->status, g_stream);
+        if ((st = cuda_check(e, "symbolic fill"))) return st;
+    }
     ev.mark(3);
 
     // ---- a4: stacks by shape (m, n, k)
     int32_t nshapes = 0;
     std::vector<int32_t> h_shapes;
     int64_t *stack_ptr = nullptr, *triples = nullptr;
-    if (!no_sync && opts.build_stacks && nprod > 0) {
+    if (!no_sync && !chunked && opts.build_stacks && nprod > 0) {
         std::vector<int32_t> sizes;
         for (auto *v : {&A->h_row_bs, &A->h_col_bs, &B->h_col_bs}) sizes.insert(sizes.end(), v->begin(), v->end());
         std::sort(sizes.begin(), sizes.end());
@@ -1553,75 +1597,103 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
                             olB.line0, olB.exps);
         if ((st = cuda_check(e, "pack"))) return st;
     }
-    NumericArgs na{};
-    na.n_items = nnzbC;
-    na.seg_ptr = cptr;
-    na.px = pa;
-    na.py = pb;
-    na.out_data = c_data;
-    na.out_blk_off = c_off;
-    na.out_blk_rc = c_rc;
-    na.x_data = A->data; na.x_blk_off = A->blk_off; na.x_blk_rc = A->blk_rc; na.x_trans = 0;
-    na.y_data = B->data; na.y_blk_off = B->blk_off; na.y_blk_rc = B->blk_rc; na.y_trans = 0;
-    na.alpha = alpha;
-    na.beta = use_old ? beta : 0.0;
-    na.old_data = use_old ? C->data : nullptr;
-    na.old_off = old_off;
-    na.dtype = C->dtype;
-    na.prec = kprec;
-    na.flush_every = opts.flush_every;
-    na.max_out_rows = A->max_bs_row; na.max_out_cols = B->max_bs_col;
-    na.x_pack = pkA.words; na.x_pack_off = pkA.off;
-    na.y_pack = pkB.words; na.y_pack_off = pkB.off;
-    na.x_exp = olA.exps; na.x_line0 = olA.line0;
-    na.y_exp = olB.exps; na.y_line0 = olB.line0;
-    na.status = no_sync ? C->status : nullptr;
-    if ((st = sc.get(&na.work_counter, 2))) return st;
-    if (no_sync) {
-        order = C->item_order;
-        n_marked = C->n_marked;
-        uses_cores = pl.uses_cores;
-    } else {
-        if ((st = ensure_row_rank(A))) return st;
-        const int32_t tile = tune_of(rprec)[BSM_TUNE_SCHED_TILE];
-        if (tile > 0 && (st = ensure_col_rank(B))) return st;
-        bsm_mat rows_view;
-        rows_view.nbr = nbr;
-        rows_view.row_ptr = crow_ptr;
-        if ((st = shape_order(sc, nnzbC, c_rc, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
-                              rprec, &uses_cores, &n_marked, c_col, tile > 0 ? B->col_rank : nullptr, nbc,
-                              tile > 0 ? tile : 0)))
-            return st;
-    }
-    na.n_lane_items = n_marked;
-    if (needs_plain(kprec) && uses_cores) {  // unpacked pieces for the CUDA-core split variant
-        const int np = split_pieces(rprec);
-        float *xp = nullptr, *yp = nullptr;
-        if ((st = sc.get(&xp, (size_t)A->data_len * np))) return st;
-        e = launch_split_plain(A, rprec, xp, g_stream);
-        if (e == cudaSuccess && B != A) {
-            if ((st = sc.get(&yp, (size_t)B->data_len * np))) return st;
-            e = launch_split_plain(B, rprec, yp, g_stream);
+    // one numeric pass over the output blocks [cb0, cb0 + nitems) holding nprod_pass
+    // products (the whole C, or one row panel of a chunked multiply)
+    float *plain_x = nullptr, *plain_y = nullptr;
+    auto numeric_pass = [&](int64_t cb0, int64_t nitems, int64_t nprod_pass, bool whole) -> bsm_status {
+        NumericArgs na{};
+        na.n_items = nitems;
+        na.seg_ptr = cptr + cb0;
+        na.px = pa;
+        na.py = pb;
+        na.out_data = c_data;
+        na.out_blk_off = c_off + cb0;
+        na.out_blk_rc = c_rc + cb0;
+        na.x_data = A->data; na.x_blk_off = A->blk_off; na.x_blk_rc = A->blk_rc; na.x_trans = 0;
+        na.y_data = B->data; na.y_blk_off = B->blk_off; na.y_blk_rc = B->blk_rc; na.y_trans = 0;
+        na.alpha = alpha;
+        na.beta = use_old ? beta : 0.0;
+        na.old_data = use_old ? C->data : nullptr;
+        na.old_off = old_off ? old_off + cb0 : nullptr;
+        na.dtype = C->dtype;
+        na.prec = kprec;
+        na.flush_every = opts.flush_every;
+        na.max_out_rows = A->max_bs_row; na.max_out_cols = B->max_bs_col;
+        na.x_pack = pkA.words; na.x_pack_off = pkA.off;
+        na.y_pack = pkB.words; na.y_pack_off = pkB.off;
+        na.x_exp = olA.exps; na.x_line0 = olA.line0;
+        na.y_exp = olB.exps; na.y_line0 = olB.line0;
+        na.status = no_sync ? C->status : nullptr;
+        bsm_status sst;
+        if ((sst = sc.get(&na.work_counter, 2))) return sst;
+        if (no_sync) {
+            order = C->item_order;
+            n_marked = C->n_marked;
+            uses_cores = pl.uses_cores;
+        } else if (whole) {
+            if ((sst = ensure_row_rank(A))) return sst;
+            const int32_t tile = tune_of(rprec)[BSM_TUNE_SCHED_TILE];
+            if (tile > 0 && (sst = ensure_col_rank(B))) return sst;
+            bsm_mat rows_view;
+            rows_view.nbr = nbr;
+            rows_view.row_ptr = crow_ptr;
+            if ((sst = shape_order(sc, nitems, c_rc + cb0, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
+                                   rprec, &uses_cores, &n_marked, c_col + cb0, tile > 0 ? B->col_rank : nullptr, nbc,
+                                   tile > 0 ? tile : 0)))
+                return sst;
+        } else {  // a row panel: block-shape classes and variants only
+            if ((sst = shape_order(sc, nitems, c_rc + cb0, A->h_row_bs, B->h_col_bs, &order, nullptr, nullptr, rprec,
+                                   &uses_cores, &n_marked)))
+                return sst;
         }
-        if ((st = cuda_check(e, "split pieces"))) return st;
-        na.x_plain = xp;
-        na.y_plain = B == A ? xp : yp;
-    }
-    na.item_order = order;
-    apply_tuning(rprec, na);
-    na.n_prod = nprod;
-    na.x_nnzb = A->nnzb; na.y_nnzb = B->nnzb;
-    na.x_len = A->data_len; na.y_len = B->data_len;
-    na.out_len = lenC; na.old_len = use_old ? C->data_len : 0;
-    na.x_pack_words = packA_words; na.y_pack_words = packB_words;
-    ev.mark(5);
-    if ((st = cuda_check(launch_numeric(na, g_stream, &nl), "numeric"))) return st;
+        na.n_lane_items = n_marked;
+        if (needs_plain(kprec) && uses_cores && !plain_x) {  // unpacked pieces for the CUDA-core split variant
+            const int np = split_pieces(rprec);
+            if ((sst = sc.get(&plain_x, (size_t)A->data_len * np))) return sst;
+            cudaError_t pe = launch_split_plain(A, rprec, plain_x, g_stream);
+            if (pe == cudaSuccess && B != A) {
+                if ((sst = sc.get(&plain_y, (size_t)B->data_len * np))) return sst;
+                pe = launch_split_plain(B, rprec, plain_y, g_stream);
+            }
+            if ((sst = cuda_check(pe, "split pieces"))) return sst;
+        }
+        na.x_plain = plain_x;
+        na.y_plain = B == A ? plain_x : plain_y;
+        na.item_order = order;
+        apply_tuning(rprec, na);
+        na.n_prod = nprod_pass;
+        na.x_nnzb = A->nnzb; na.y_nnzb = B->nnzb;
+        na.x_len = A->data_len; na.y_len = B->data_len;
+        na.out_len = lenC; na.old_len = use_old ? C->data_len : 0;
+        na.x_pack_words = packA_words; na.y_pack_words = packB_words;
+        if (whole) ev.mark(5);
+        if ((sst = cuda_check(launch_numeric(na, g_stream, &nl), "numeric"))) return sst;
 #ifdef BSM_DEBUG
-    if (!no_sync)
-        if (const uint32_t bits = numeric_debug_bits(g_stream))
-            return set_error(BSM_ERR_CUDA, "debug bounds check of the numeric kernel failed (bits " +
-                                               std::to_string(bits) + ")");
+        if (!no_sync)
+            if (const uint32_t bits = numeric_debug_bits(g_stream))
+                return set_error(BSM_ERR_CUDA, "debug bounds check of the numeric kernel failed (bits " +
+                                                   std::to_string(bits) + ")");
 #endif
+        return BSM_OK;
+    };
+    if (!chunked) {
+        if ((st = numeric_pass(0, nnzbC, nprod, true))) return st;
+    } else {
+        ev.mark(5);  // the row panels' fill and numeric passes, timed together
+        // row panels: fill the panel's pattern and products, then its numeric pass
+        for (size_t q = 0; q + 1 < panel_rows.size(); ++q) {
+            const int32_t r0 = panel_rows[q], r1 = panel_rows[q + 1];
+            const int64_t cb0 = h_cp[r0], cb1 = h_cp[r1], np = h_pp[r1] - h_pp[r0];
+            e = fill_rows(r0, r1, h_pp[r0]);
+            // the panel's end of products (a pageable source: staged before the call returns)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(cptr + cb1, &np, sizeof(int64_t), cudaMemcpyHostToDevice, g_stream);
+            if ((st = cuda_check(e, "symbolic fill of a row panel"))) return st;
+            if (cb1 > cb0 && (st = numeric_pass(cb0, cb1 - cb0, np, false))) return st;
+        }
+        order = nullptr;  // the panels' orders are scratch
+        n_marked = nullptr;
+    }
     ev.mark(6);
     }
     if (no_sync) return BSM_OK;  // C's storage, counts and plan are unchanged
@@ -1639,6 +1711,10 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     C->own_data = true;
     C->nnzb = nnzbC;
     C->data_len = lenC;
+    if (chunked) {  // no product list of the whole C is kept: it goes back with the scratch
+        cptr = nullptr;
+        pa = pb = pc = nullptr;
+    }
     C->cptr = cptr;
     C->pa = pa; C->pb = pb; C->pc = pc;
     C->nprod = nprod;
@@ -1648,7 +1724,8 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     C->h_shapes = h_shapes;
     C->stack_ptr = stack_ptr;
     C->triples = triples;
-    C->prod_A = A; C->prod_B = B;
+    C->prod_A = chunked ? nullptr : A;
+    C->prod_B = chunked ? nullptr : B;
     C->prod_A_nnzb = A->nnzb; C->prod_B_nnzb = B->nnzb;
     C->launch_cfg[0] = nl.kernel; C->launch_cfg[1] = nl.build; C->launch_cfg[2] = nl.cta_threads;
     C->launch_cfg[3] = nl.grid; C->launch_cfg[4] = nl.pass_mt; C->launch_cfg[5] = nl.pass_nt;
@@ -1661,7 +1738,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
                     (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order, (void *)n_marked})
         sc.release(p);
     C->plan = bsm_mat::Plan{};
-    if (!use_old && !opts.post_filter) {
+    if (!use_old && !opts.post_filter && !chunked) {
         auto &P = C->plan;
         P.kind = 1; P.A = A; P.B = B; P.A_nnzb = A->nnzb; P.B_nnzb = B->nnzb; P.eps = filter_eps;
         P.prec = opts.prec; P.kprec = kprec; P.nprod = nprod; P.nnzb = nnzbC; P.len = lenC; P.max_ccnt = max_ccnt;

@@ -187,15 +187,18 @@ struct FillOut {
     int64_t *old_off;    // [nnzbC] or nullptr
     int32_t max_ccnt;
     int32_t nchunk;      // A-block chunks per row (1..8, one warp each)
+    int32_t row0;        // first block row of this launch (row panels; 0 otherwise)
+    int64_t prod_base;   // prod_ptr[row0]: product offsets are written relative to it
 };
+// Fill block rows [o.row0, o.row0 + nrows) (nrows < 0: all rows).
 cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int32_t nrows = -1);
 int64_t symbolic_fill_smem_bytes(int32_t nwords, int32_t max_ccnt, int nchunk);
 // Fill through B's columns (B transposed: bt_ptr[nbc+1], bt_k / bt_b = block row
 // and block index of every B block, column-major, ascending k inside a column).
 cudaError_t launch_symbolic_fill_cols(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
                                       const int64_t *bt_ptr, const int32_t *bt_k, const int32_t *bt_b,
-                                      cudaStream_t s);
+                                      cudaStream_t s, int32_t nrows = -1);
 int64_t symbolic_fill_cols_smem_bytes(int32_t nwords, int32_t max_ccnt, int32_t nbk);
 cudaError_t launch_blk_rows(const bsm_mat *X, int32_t *rows, cudaStream_t s);
 

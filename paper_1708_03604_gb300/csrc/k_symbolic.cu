@@ -269,11 +269,11 @@ __global__ void __launch_bounds__(kThreads) k_sym_fill(SymbolicArgs a, const uin
     uint32_t *bm = smem;
     int32_t *wpre = reinterpret_cast<int32_t *>(smem + nw);
     int32_t *cnt = wpre + nw;
-    const int i = blockIdx.x;
+    const int i = o.row0 + blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t crow = o.crow_ptr[i];
     const int32_t ccnt = (int32_t)(o.crow_ptr[i + 1] - crow);
-    const int64_t prow = o.prod_ptr[i];
+    const int64_t prow = o.prod_ptr[i] - o.prod_base;
     const int32_t m = a.a_row_bs[i];
 
     for (int w = tid; w < nw; w += blockDim.x) {
@@ -393,11 +393,11 @@ __global__ void __launch_bounds__(kThreads) k_sym_fill_cols(SymbolicArgs a, cons
     int32_t *wpre = reinterpret_cast<int32_t *>(smem + nw);
     int32_t *cnt = wpre + nw;
     int32_t *amap = cnt + o.max_ccnt;  // [nbk]: A block of row i in column k, or -1
-    const int i = blockIdx.x;
+    const int i = o.row0 + blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int64_t crow = o.crow_ptr[i];
     const int32_t ccnt = (int32_t)(o.crow_ptr[i + 1] - crow);
-    const int64_t prow = o.prod_ptr[i];
+    const int64_t prow = o.prod_ptr[i] - o.prod_base;
     const int32_t m = a.a_row_bs[i];
 
     for (int w = tid; w < nw; w += blockDim.x) {
@@ -825,14 +825,15 @@ int64_t symbolic_fill_cols_smem_bytes(int32_t nwords, int32_t max_ccnt, int32_t 
 
 cudaError_t launch_symbolic_fill_cols(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
                                       const int64_t *bt_ptr, const int32_t *bt_k, const int32_t *bt_b,
-                                      cudaStream_t s) {
-    if (a.nbr == 0) return cudaSuccess;
+                                      cudaStream_t s, int32_t nrows) {
+    if (nrows < 0) nrows = a.nbr - o.row0;
+    if (nrows <= 0) return cudaSuccess;
     const int smem = (int)symbolic_fill_cols_smem_bytes(a.nwords, o.max_ccnt, a.nbk);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_sym_fill_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    k_sym_fill_cols<<<a.nbr, kThreads, smem, s>>>(a, bitmaps, o, bt_ptr, bt_k, bt_b);
+    k_sym_fill_cols<<<nrows, kThreads, smem, s>>>(a, bitmaps, o, bt_ptr, bt_k, bt_b);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -845,14 +846,15 @@ cudaError_t launch_blk_rows(const bsm_mat *X, int32_t *rows, cudaStream_t s) {
 }
 
 cudaError_t launch_symbolic_fill(const SymbolicArgs &a, const uint32_t *bitmaps, const FillOut &o,
-                                 cudaStream_t s) {
-    if (a.nbr == 0) return cudaSuccess;
+                                 cudaStream_t s, int32_t nrows) {
+    if (nrows < 0) nrows = a.nbr - o.row0;
+    if (nrows <= 0) return cudaSuccess;
     const int smem = (int)symbolic_fill_smem_bytes(a.nwords, o.max_ccnt, o.nchunk);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_sym_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    k_sym_fill<<<a.nbr, kThreads, smem, s>>>(a, bitmaps, o);
+    k_sym_fill<<<nrows, kThreads, smem, s>>>(a, bitmaps, o);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -108,3 +108,13 @@ def test_allocator_wait_limit_and_probe_arguments_on_host(libbsm):
     assert L.bsm_measure_peak(0, 1, None) == bsm.BSM_ERR_ARG
     # the binding's hooks are back in place
     bsm.use_torch_allocator()
+
+
+def test_product_limit_range():
+    """The product limit is host state: its range check runs without a GPU."""
+    from paper_1708_03604_gb300 import bsm
+    L = bsm.lib()
+    assert L.bsm_set_product_limit(0) == bsm.BSM_ERR_ARG
+    assert L.bsm_set_product_limit(2**31) == bsm.BSM_ERR_ARG
+    assert L.bsm_set_product_limit(1000) == bsm.BSM_OK
+    assert L.bsm_set_product_limit(2**31 - 1) == bsm.BSM_OK
