@@ -237,8 +237,13 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  *   BSM_TUNE_CTAS_PER_SM persistent CTAs per SM, 1..16, capped by what fits;
  *                        0 = as many as fit (default)
  *   BSM_TUNE_PASS_MT     fragment tiles along the output rows per pass over
- *                        a block's products: split paths 1..2 (default 2,
- *                        16-row tiles), FP64_DMMA 1..3 (default 3, 8-row tiles)
+ *                        a block's products: split paths 1..2 (16-row tiles;
+ *                        default: output blocks of one tile row run in a
+ *                        kernel instance compiled for 1-row passes -- fewer
+ *                        registers, more warps per SM -- and the others in a
+ *                        2-row instance, two launches; 1 or 2 runs every block
+ *                        in that one instance), FP64_DMMA 1..3 (default 3,
+ *                        8-row tiles)
  *   BSM_TUNE_PASS_NT     along the columns: split paths 1..3 (default 3,
  *                        8-column tiles), OZAKI 1..3 (default 2; 3 runs a
  *                        kernel instance with a larger staging ring), FP64_DMMA
@@ -279,7 +284,9 @@ enum {
 /* What the last numeric launch into C ran: cfg[0] kernel (BSM_K_*),
  * cfg[1] FP64 kernel build (0 small, 1 narrow, 2 wide; -1 for the others),
  * cfg[2] threads per CTA, cfg[3] CTAs, cfg[4] / cfg[5] fragment tiles per pass
- * along rows / columns (0 where the kernel has no passes). */
+ * along rows / columns (0 where the kernel has no passes; cfg[4] = 0 on the
+ * split paths when one-tile-row blocks ran in their own instance, cfg[3] then
+ * the CTAs of the 2-row instance). */
 bsm_status bsm_get_launch_config(bsm_t C, int32_t *cfg);
 
 /* Fills `opts` with the defaults (FP64, no post filter, stacks built). */

@@ -14,7 +14,9 @@ recorded by the library around the launch) on the caller's operands:
 * warps per CTA (4 or 2) of the persistent mma.sync kernels;
 * persistent CTAs per SM;
 * the fragment-tile pass shape (tiles along rows and columns that one pass
-  over a block's products covers) of the split, Ozaki and FP64-MMA kernels;
+  over a block's products covers) of the split, Ozaki and FP64-MMA kernels
+  (on the split paths also the default split: blocks of one tile row in a
+  kernel instance of their own, compiled for 1-row passes);
 * the order of the output blocks: by block row, or by 2-D tiles of ranked
   rows x ranked columns so that the blocks in flight share A's and B's
   blocks in L2;
@@ -50,8 +52,9 @@ SEARCH = {
     "ozaki": [("cta_warps", [4, 2]), ("pass_nt", [2, 1, 3]), ("ctas_per_sm", [0, 1, 2, 3]), TILES],
 }
 for _p in SPLIT:
-    SEARCH[_p] = [("cta_warps", [4, 2]), ("pass_mt", [2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 3, 4]),
-                  TILES]
+    # pass_mt -1: blocks of one tile row in a 1-row kernel instance, the rest in a 2-row one
+    SEARCH[_p] = [("cta_warps", [4, 2]), ("pass_mt", [-1, 2, 1]), ("pass_nt", [3, 2, 1]),
+                  ("ctas_per_sm", [0, 1, 2, 3, 4]), TILES]
 # TF32x3 may also run on the tcgen05 row-panel engine where it applies
 SEARCH["tf32x3"] = SEARCH["tf32x3"] + [("engine", [0, 1])]
 FLUSH_CANDIDATES = [-1, 1, 2, 4, 8, 16]

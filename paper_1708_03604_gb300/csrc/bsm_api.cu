@@ -218,6 +218,7 @@ void free_pattern(bsm_mat *X) {
     X->norms_valid = false;
     dfree(X->item_order); X->item_order = nullptr;
     dfree(X->n_marked); X->n_marked = nullptr;
+    dfree(X->item_groups); X->item_groups = nullptr;
     dfree(X->row_rank); X->row_rank = nullptr;
     dfree(X->col_rank); X->col_rank = nullptr;
     dfree(X->panel_ord_r); X->panel_ord_r = nullptr;
@@ -446,10 +447,12 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
                        const std::vector<int32_t> &csz, int32_t **order, const bsm_mat *rows_of = nullptr,
                        const int32_t *row_rank = nullptr, int prec = -1, bool *uses_cores = nullptr,
                        int64_t **n_marked = nullptr, const int32_t *blk_col = nullptr,
-                       const int32_t *col_rank = nullptr, int32_t ncols = 0, int32_t tile = 0) {
+                       const int32_t *col_rank = nullptr, int32_t ncols = 0, int32_t tile = 0,
+                       int64_t **groups = nullptr) {
     if (uses_cores) *uses_cores = false;
     *order = nullptr;
     if (n_marked) *n_marked = nullptr;
+    if (groups) *groups = nullptr;
     if (n <= 1) return BSM_OK;
     std::vector<int32_t> sizes(rsz);
     sizes.insert(sizes.end(), csz.begin(), csz.end());
@@ -459,9 +462,14 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     if ((int64_t)ns * ns > (1 << 16)) return BSM_OK;  // too many shapes: natural order
     std::vector<int32_t> sidx(kMaxBlockDim + 1, 0), table((size_t)ns * ns);
     for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
+    // split paths with groups: blocks of one tile row (at most 16 rows) after
+    // the others, each group for a kernel instance of its own
+    const bool grouped = groups && (prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6);
+    auto group_of = [&](int32_t m) -> int64_t { return (grouped && m <= 16) ? 1 : 0; };
     std::vector<std::pair<int64_t, int32_t>> cls;
     for (int32_t r = 0; r < ns; ++r)
-        for (int32_t c = 0; c < ns; ++c) cls.emplace_back(-(int64_t)sizes[r] * sizes[c], r * ns + c);
+        for (int32_t c = 0; c < ns; ++c)
+            cls.emplace_back(group_of(sizes[r]) * (int64_t(1) << 40) - (int64_t)sizes[r] * sizes[c], r * ns + c);
     std::sort(cls.begin(), cls.end());
     // per-class variant; second-variant classes sort after all others
     std::vector<int8_t> var((size_t)ns * ns, 0);
@@ -506,6 +514,20 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     if (e == cudaSuccess)
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
+    if (grouped) {
+        // positions in the sorted order where the one-tile-row blocks and the lane items start
+        const int64_t mult = use_tiles ? nrt * nct : (row_rank ? std::max(nbr, 1) : 1);
+        const int32_t ncls = (int32_t)cls.size();
+        int32_t q1 = 0;
+        while (q1 < ncls && group_of(sizes[cls[q1].second / ns]) == 0) ++q1;
+        int64_t *gb;
+        if ((st = sc.get(&gb, 2))) return st;
+        if ((st = cuda_check(launch_group_bounds(keys_sorted, n, (uint32_t)(q1 * mult), (uint32_t)(ncls * mult), gb,
+                                                 g_stream),
+                             "tile-row groups")))
+            return st;
+        *groups = gb;
+    }
     if (any_var) {
         int8_t *d_var;
         int64_t *cnt;
@@ -1573,7 +1595,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     NumericLaunch nl{use_panel ? BSM_K_PANEL_TCGEN05 : BSM_K_NONE, -1, 0, 0, 0, 0};
     OzLines olA, olB;
     int32_t *order = nullptr;
-    int64_t *n_marked = nullptr;
+    int64_t *n_marked = nullptr, *groups = nullptr;
     bool uses_cores = false;
     if (use_panel) {
         PanelOut po{nnzbC, crow_ptr, c_col, c_off, static_cast<double *>(c_data), old_off,
@@ -1600,6 +1622,9 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     // one numeric pass over the output blocks [cb0, cb0 + nitems) holding nprod_pass
     // products (the whole C, or one row panel of a chunked multiply)
     float *plain_x = nullptr, *plain_y = nullptr;
+    // split paths: blocks of one tile row in their own kernel instance, unless
+    // the tuning fixes the pass rows
+    const bool want_groups = tune_of(rprec)[BSM_TUNE_PASS_MT] <= 0;
     auto numeric_pass = [&](int64_t cb0, int64_t nitems, int64_t nprod_pass, bool whole) -> bsm_status {
         NumericArgs na{};
         na.n_items = nitems;
@@ -1625,10 +1650,11 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         na.y_exp = olB.exps; na.y_line0 = olB.line0;
         na.status = no_sync ? C->status : nullptr;
         bsm_status sst;
-        if ((sst = sc.get(&na.work_counter, 2))) return sst;
+        if ((sst = sc.get(&na.work_counter, 4))) return sst;
         if (no_sync) {
             order = C->item_order;
             n_marked = C->n_marked;
+            groups = C->item_groups;
             uses_cores = pl.uses_cores;
         } else if (whole) {
             if ((sst = ensure_row_rank(A))) return sst;
@@ -1639,13 +1665,14 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             rows_view.row_ptr = crow_ptr;
             if ((sst = shape_order(sc, nitems, c_rc + cb0, A->h_row_bs, B->h_col_bs, &order, &rows_view, A->row_rank,
                                    rprec, &uses_cores, &n_marked, c_col + cb0, tile > 0 ? B->col_rank : nullptr, nbc,
-                                   tile > 0 ? tile : 0)))
+                                   tile > 0 ? tile : 0, want_groups ? &groups : nullptr)))
                 return sst;
         } else {  // a row panel: block-shape classes and variants only
             if ((sst = shape_order(sc, nitems, c_rc + cb0, A->h_row_bs, B->h_col_bs, &order, nullptr, nullptr, rprec,
-                                   &uses_cores, &n_marked)))
+                                   &uses_cores, &n_marked, nullptr, nullptr, 0, 0, want_groups ? &groups : nullptr)))
                 return sst;
         }
+        na.item_groups = groups;
         na.n_lane_items = n_marked;
         if (needs_plain(kprec) && uses_cores && !plain_x) {  // unpacked pieces for the CUDA-core split variant
             const int np = split_pieces(rprec);
@@ -1693,6 +1720,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
         }
         order = nullptr;  // the panels' orders are scratch
         n_marked = nullptr;
+        groups = nullptr;
     }
     ev.mark(6);
     }
@@ -1703,6 +1731,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     free_pattern(C);
     C->item_order = order;
     C->n_marked = n_marked;
+    C->item_groups = groups;
     C->row_ptr = crow_ptr;
     C->col_idx = c_col;
     C->blk_off = c_off;
@@ -1735,7 +1764,8 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
                 : is_tc(kprec) ? BSM_E_SPLIT_MMA
                                : BSM_E_FP64_CORES;
     for (void *p : {(void *)crow_ptr, (void *)c_col, (void *)c_off, (void *)c_rc, c_data, (void *)cptr, (void *)pa,
-                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order, (void *)n_marked})
+                    (void *)pb, (void *)pc, (void *)stack_ptr, (void *)triples, (void *)order, (void *)n_marked,
+                    (void *)groups})
         sc.release(p);
     C->plan = bsm_mat::Plan{};
     if (!use_old && !opts.post_filter && !chunked) {
@@ -1760,6 +1790,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
             dfree(C->triples); C->triples = nullptr;
             dfree(C->item_order); C->item_order = nullptr;
             dfree(C->n_marked); C->n_marked = nullptr;
+            dfree(C->item_groups); C->item_groups = nullptr;
             C->nshapes = 0;
             C->h_shapes.clear();
             C->prod_A = C->prod_B = nullptr;
@@ -1895,7 +1926,7 @@ bsm_status bsm_multiply_backward(double alpha, bsm_t C, const void *dC_data, bsm
         na.y_pack = pkY.words; na.y_pack_off = pkY.off;
         na.x_exp = olX.exps; na.x_line0 = olX.line0;
         na.y_exp = olY.exps; na.y_line0 = olY.line0;
-        if ((st = sc.get(&na.work_counter, 2))) return st;
+        if ((st = sc.get(&na.work_counter, 4))) return st;
         int32_t *item_order = nullptr;
         int64_t *n_marked = nullptr;
         bool uses_cores = false;

@@ -91,6 +91,7 @@ struct bsm_mat {
     } plan;
     int32_t *item_order = nullptr;      // numeric processing order of the last eager multiply
     int64_t *n_marked = nullptr;        // device count of its second-variant items (or null)
+    int64_t *item_groups = nullptr;     // device bounds of its tile-row groups (or null)
     // rank of every block row in a breadth-first order through shared block
     // columns (built on demand, dropped with the pattern); schedules numeric work
     int32_t *row_rank = nullptr;        // [nbr]
@@ -272,8 +273,13 @@ struct NumericArgs {
                                 // bit 31 marks the second variant of the item's shape
     const int64_t *n_lane_items;  // nullable (CUDA-core FP64 path): the last *n_lane_items items of
                                   // item_order are tiny blocks computed one per lane
+    // nullable (split paths): item_order positions [0] end of the blocks of two
+    // tile rows and more, [1] end of the blocks of one tile row (start of the
+    // lane items); each group runs in its own kernel instance
+    const int64_t *item_groups;
+    int32_t group;              // set by the launcher: the group one launch covers
     const int32_t *status;      // nullable: the kernel does nothing when *status != 0
-    unsigned long long *work_counter;  // 8 bytes of device memory, zeroed by the launcher
+    unsigned long long *work_counter;  // 4 x 8 bytes of device memory, zeroed by the launcher
     // Ozaki path: biased FP64 exponent field of the largest |x| of every global
     // line (logical rows of X, logical columns of Y) and the first line of every block
     const int32_t *x_exp, *x_line0, *y_exp, *y_line0;
@@ -299,6 +305,9 @@ struct NumericLaunch {
     int32_t cta_threads, grid, pass_mt, pass_nt;
 };
 cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *info = nullptr);
+// out[g] = number of keys below thr[g] in the ascending keys[0..n) (g < 2)
+cudaError_t launch_group_bounds(const uint32_t *keys, int64_t n, uint32_t thr0, uint32_t thr1, int64_t *out,
+                                cudaStream_t s);
 
 // Ozaki path: line0[b] = first global line of block b, lines being the stored
 // rows (by_rows) or the stored columns of M's blocks; exps[line] = max biased

@@ -580,13 +580,18 @@ __device__ __forceinline__ void mma_piece(float (&d)[4], const uint32_t (&a)[4],
 // needs no warp barrier -- only each lane's own cp.async.wait_group.  A stage
 // is chunk-major like the packs (chunk c of lane L at word c * 128 + 4 * L):
 // every 16-byte copy and read of the warp covers 512 contiguous bytes.
-template <int PREC> struct RingTraits;
-template <> struct RingTraits<BSM_P_TF32x3> { static constexpr int STAGES = 4, SW = 2 * 8 + 3 * 4; };
-template <> struct RingTraits<BSM_P_BF16x3> { static constexpr int STAGES = 4, SW = 2 * 8 + 3 * 4; };
-template <> struct RingTraits<BSM_P_BF16x6> { static constexpr int STAGES = 3, SW = 2 * 12 + 3 * 8; };
+// Stages, and words per lane of a stage for passes of at most PM x PN tiles.
+// A kernel instance compiled for smaller passes holds fewer accumulators and
+// a smaller ring, so more warps fit on an SM.
+template <int PREC, int PM = 2, int PN = 3> struct RingTraits {
+    static constexpr int STAGES = PREC == BSM_P_BF16x6 ? 3 : 4;
+    static constexpr int SW = PM * PrecTraits<PREC>::XW + PN * PrecTraits<PREC>::YW;
+};
 
-template <int PREC>
-__host__ __device__ constexpr int ring_words_per_warp() { return RingTraits<PREC>::STAGES * 32 * RingTraits<PREC>::SW; }
+template <int PREC, int PM = 2, int PN = 3>
+__host__ __device__ constexpr int ring_words_per_warp() {
+    return RingTraits<PREC, PM, PN>::STAGES * 32 * RingTraits<PREC, PM, PN>::SW;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -627,11 +632,11 @@ __device__ __forceinline__ double pair_total(float hi, float lo, float b) {
 // starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
 // FF: cross-product sum as a compensated float pair (Kahan after every |F| block
 // products); otherwise an FP64 sum refreshed every F products.
-template <int PREC, int MTC, int NTC, bool FF>
+template <int PREC, int MTC, int NTC, bool FF, int PM, int PN>
 __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
                                         uint32_t *ring) {
     using PT = PrecTraits<PREC>;
-    using RT = RingTraits<PREC>;
+    using RT = RingTraits<PREC, PM, PN>;
     constexpr int ST = RT::STAGES, SW = RT::SW;
     const int32_t orc = a.out_blk_rc[q];
     const int R = rc_rows(orc), S = rc_cols(orc);
@@ -808,26 +813,26 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
             }
 }
 
-template <int PREC, bool FF>
+template <int PREC, bool FF, int PM, int PN>
 __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
-    const int pm = a.pass_mt > 0 ? a.pass_mt : 2, pn = a.pass_nt > 0 ? a.pass_nt : 3;
+    const int pm = min(PM, a.pass_mt > 0 ? a.pass_mt : PM), pn = min(PN, a.pass_nt > 0 ? a.pass_nt : PN);
     for (int mt0 = 0; mt0 < MT; mt0 += pm) {
         const int mtc = min(pm, MT - mt0);
         for (int nt0 = 0; nt0 < NT; nt0 += pn) {
             const int ntc = min(pn, NT - nt0);
-            if (mtc == 1) {
-                switch (ntc) {
-                    case 1: tc_pass<PREC, 1, 1, FF>(a, q, lane, mt0, nt0, ring); break;
-                    case 2: tc_pass<PREC, 1, 2, FF>(a, q, lane, mt0, nt0, ring); break;
-                    default: tc_pass<PREC, 1, 3, FF>(a, q, lane, mt0, nt0, ring); break;
+            if (PM == 1 || mtc == 1) {
+                if (PN == 1 || ntc == 1) tc_pass<PREC, 1, 1, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                else if constexpr (PN >= 2) {
+                    if (PN == 2 || ntc == 2) tc_pass<PREC, 1, 2, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                    else if constexpr (PN >= 3) tc_pass<PREC, 1, 3, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
                 }
-            } else {
-                switch (ntc) {
-                    case 1: tc_pass<PREC, 2, 1, FF>(a, q, lane, mt0, nt0, ring); break;
-                    case 2: tc_pass<PREC, 2, 2, FF>(a, q, lane, mt0, nt0, ring); break;
-                    default: tc_pass<PREC, 2, 3, FF>(a, q, lane, mt0, nt0, ring); break;
+            } else if constexpr (PM >= 2) {
+                if (PN == 1 || ntc == 1) tc_pass<PREC, 2, 1, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                else if constexpr (PN >= 2) {
+                    if (PN == 2 || ntc == 2) tc_pass<PREC, 2, 2, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                    else if constexpr (PN >= 3) tc_pass<PREC, 2, 3, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
                 }
             }
         }
@@ -1032,34 +1037,52 @@ __device__ __forceinline__ void cs_lane_dispatch(const NumericArgs &a, int64_t q
     }
 }
 
-template <int PREC, bool FF>
+// PM x PN: the largest pass this instance runs.  Items [i0, i1) of the
+// order, a warp each on the tensor cores: every item before the lane items
+// (a.group < 0), or one group of a multiply whose blocks of one tile row run
+// in a 1 x PN instance (group 1) and the rest in a 2 x PN instance (group 0).
+template <int PREC, bool FF, int PM, int PN>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t tc_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC>();
-    unsigned long long *ctr = a.work_counter;
+    uint32_t *ring = tc_smem + warp * ring_words_per_warp<PREC, PM, PN>();
     if (a.status && *a.status != 0) return;
-    // items [0, n0): a warp each on the tensor cores; items [n0, n_items):
-    // tiny blocks marked for the CUDA-core variant, 32 per ticket
     const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
-    const int64_t n0 = a.n_items - n_lane;
-    const int64_t tickets = n0 + (n_lane + 31) / 32;
+    int64_t i0 = 0, i1 = a.n_items - n_lane;
+    if (a.group == 0) i1 = a.item_groups[0];
+    if (a.group == 1) i0 = a.item_groups[0];
+    unsigned long long *ctr = a.work_counter + (a.group > 0 ? a.group : 0);
+    while (true) {
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0) + i0;
+        if (t >= i1) break;
+        int64_t q = t;
+        if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+        BSM_DBG_WARP_SKIP(a, q, lane)
+        tc_item<PREC, FF, PM, PN>(a, q, lane, ring);
+    }
+}
+
+// The last *n_lane_items items of the order: tiny blocks marked for the
+// CUDA-core variant, 32 per ticket (a kernel of their own, so that the
+// tensor-core instances do not carry its registers).
+template <int PREC, bool FF>
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_tc_lane(NumericArgs a) {
+    const int lane = threadIdx.x & 31;
+    if (a.status && *a.status != 0) return;
+    const int64_t n_lane = *a.n_lane_items;
+    const int64_t lane0 = a.n_items - n_lane;
+    unsigned long long *ctr = a.work_counter + 2;
     while (true) {
         int64_t t = 0;
         if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= tickets) break;
-        if (t < n0) {
-            int64_t q = t;
-            if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
-            BSM_DBG_WARP_SKIP(a, q, lane)
-            tc_item<PREC, FF>(a, q, lane, ring);
-        } else {
-            const int64_t idx = n0 + (t - n0) * 32 + lane;
-            if (idx < a.n_items) {
-                const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                if (BSM_DBG_LANE_OK(a, q)) cs_lane_dispatch<PREC, FF>(a, q);
-            }
+        if (t * 32 >= n_lane) break;
+        const int64_t idx = lane0 + t * 32 + lane;
+        if (idx < a.n_items) {
+            const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
+            if (BSM_DBG_LANE_OK(a, q)) cs_lane_dispatch<PREC, FF>(a, q);
         }
     }
 }
@@ -1675,14 +1698,56 @@ int launch_cc(const NumericArgs &a, cudaStream_t s) {
     return g;
 }
 
+template <int PREC, bool FF, int PM, int PN>
+cudaError_t launch_tc_pass(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
+    const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC, PM, PN>() * (threads / 32);
+    cudaError_t e = cudaFuncSetAttribute(k_numeric_tc<PREC, FF, PM, PN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    *grid = persistent_grid(k_numeric_tc<PREC, FF, PM, PN>, a.n_items, smem, threads, a.ctas_per_sm);
+    k_numeric_tc<PREC, FF, PM, PN><<<*grid, threads, smem, s>>>(a);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+template <int PREC, bool FF, int PM>
+cudaError_t launch_tc_pm(const NumericArgs &a, cudaStream_t s, int threads, int *grid, int pn) {
+    if (pn >= 3) return launch_tc_pass<PREC, FF, PM, 3>(a, s, threads, grid);
+    if (pn == 2) return launch_tc_pass<PREC, FF, PM, 2>(a, s, threads, grid);
+    return launch_tc_pass<PREC, FF, PM, 1>(a, s, threads, grid);
+}
+
+// The instance by the largest pass asked for (pass_mt 1 or 2, pass_nt 1..3;
+// default 2 x 3), or -- with item groups, the default -- the blocks of two
+// tile rows and more in a 2 x PN instance and those of one tile row in a
+// 1 x PN instance (fewer registers and a smaller ring: more warps per SM);
+// then the lane items.
 template <int PREC, bool FF>
 cudaError_t launch_tc_ff(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
-    const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC>() * (threads / 32);
-    cudaError_t e = cudaFuncSetAttribute(k_numeric_tc<PREC, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    *grid = persistent_grid(k_numeric_tc<PREC, FF>, a.n_items, smem, threads, a.ctas_per_sm);
-    k_numeric_tc<PREC, FF><<<*grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
+    const int pm = a.pass_mt > 0 ? a.pass_mt : 2, pn = a.pass_nt > 0 ? a.pass_nt : 3;
+    cudaError_t e;
+    if (a.item_groups) {
+        NumericArgs b = a;
+        b.group = 0;
+        e = launch_tc_pm<PREC, FF, 2>(b, s, threads, grid, pn);
+        if (e == cudaSuccess) {
+            int g1 = 0;
+            b.group = 1;
+            e = launch_tc_pm<PREC, FF, 1>(b, s, threads, &g1, pn);
+        }
+    } else {
+        NumericArgs b = a;
+        b.group = -1;
+        e = pm >= 2 ? launch_tc_pm<PREC, FF, 2>(b, s, threads, grid, pn)
+                    : launch_tc_pm<PREC, FF, 1>(b, s, threads, grid, pn);
+    }
+    if (e == cudaSuccess && a.n_lane_items) {
+        const int g = persistent_grid(k_numeric_tc_lane<PREC, FF>, a.n_items / 32 + 1, 0, kThreadsNum, a.ctas_per_sm);
+        k_numeric_tc_lane<PREC, FF><<<g, kThreadsNum, 0, s>>>(a);
+        count_launch(1);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 template <int PREC>
@@ -1697,7 +1762,7 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     NumericLaunch li{BSM_K_NONE, -1, 0, 0, 0, 0};
     if (info) *info = li;
     if (a.n_items == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(a.work_counter, 0, 4 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const bool tc = a.prec == BSM_P_TF32x3 || a.prec == BSM_P_BF16x3 || a.prec == BSM_P_BF16x6;
     // the mma.sync kernels run 2 or 4 warps per CTA (compiled for at most 4,
@@ -1752,12 +1817,12 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
         if (a.prec == BSM_P_TF32x3) e = launch_tc<BSM_P_TF32x3>(a, s, tc_threads, &grid);
         else if (a.prec == BSM_P_BF16x3) e = launch_tc<BSM_P_BF16x3>(a, s, tc_threads, &grid);
         else e = launch_tc<BSM_P_BF16x6>(a, s, tc_threads, &grid);
-        li = NumericLaunch{BSM_K_SPLIT_MMA, -1, tc_threads, grid, a.pass_mt > 0 ? a.pass_mt : 2,
-                           a.pass_nt > 0 ? a.pass_nt : 3};
+        li = NumericLaunch{BSM_K_SPLIT_MMA, -1, tc_threads, grid,
+                           a.item_groups ? 0 : (a.pass_mt > 0 ? a.pass_mt : 2), a.pass_nt > 0 ? a.pass_nt : 3};
     }
     if (e != cudaSuccess) return e;
     if (info) *info = li;
-    count_launch(1);
+    if (!tc) count_launch(1);  // the split paths count their launches themselves
     return cudaGetLastError();
 }
 

@@ -756,6 +756,20 @@ __global__ void k_class_keys(int64_t n, const int32_t *blk_rc, const int32_t *si
     }
 }
 
+// lower bounds of two thresholds in sorted keys (one thread each)
+__global__ void k_group_bounds(const uint32_t *keys, int64_t n, uint32_t thr0, uint32_t thr1, int64_t *out) {
+    const int g = threadIdx.x;
+    if (g >= 2) return;
+    const uint32_t thr = g == 0 ? thr0 : thr1;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < thr) lo = mid + 1;
+        else hi = mid;
+    }
+    out[g] = lo;
+}
+
 inline int grid_for(int64_t n, int threads = kThreads) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -766,6 +780,13 @@ inline int grid_for(int64_t n, int threads = kThreads) {
 }  // namespace
 
 // =================================================================== launchers
+cudaError_t launch_group_bounds(const uint32_t *keys, int64_t n, uint32_t thr0, uint32_t thr1, int64_t *out,
+                                cudaStream_t s) {
+    k_group_bounds<<<1, 32, 0, s>>>(keys, n, thr0, thr1, out);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_blk_rc(const bsm_mat *X, int32_t *out_rc, cudaStream_t s) {
     if (X->nnzb == 0) return cudaSuccess;
     const int64_t warps = X->nbr;
