@@ -462,14 +462,20 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
     if ((int64_t)ns * ns > (1 << 16)) return BSM_OK;  // too many shapes: natural order
     std::vector<int32_t> sidx(kMaxBlockDim + 1, 0), table((size_t)ns * ns);
     for (int32_t q = 0; q < ns; ++q) sidx[sizes[q]] = q;
-    // split paths with groups: blocks of one tile row (at most 16 rows) after
-    // the others, each group for a kernel instance of its own
-    const bool grouped = groups && (prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6);
-    auto group_of = [&](int32_t m) -> int64_t { return (grouped && m <= 16) ? 1 : 0; };
+    // with groups, the blocks a smaller kernel instance takes come after the
+    // others: split paths, one tile row (at most 16 rows); Ozaki path, one tile
+    // column (at most 8 columns)
+    const bool split = prec == BSM_P_TF32x3 || prec == BSM_P_BF16x3 || prec == BSM_P_BF16x6;
+    const bool grouped = groups && (split || prec == BSM_P_OZAKI);
+    auto group_of = [&](int32_t m, int32_t nn) -> int64_t {
+        if (!grouped) return 0;
+        return (split ? m <= 16 : nn <= 8) ? 1 : 0;
+    };
     std::vector<std::pair<int64_t, int32_t>> cls;
     for (int32_t r = 0; r < ns; ++r)
         for (int32_t c = 0; c < ns; ++c)
-            cls.emplace_back(group_of(sizes[r]) * (int64_t(1) << 40) - (int64_t)sizes[r] * sizes[c], r * ns + c);
+            cls.emplace_back(group_of(sizes[r], sizes[c]) * (int64_t(1) << 40) - (int64_t)sizes[r] * sizes[c],
+                             r * ns + c);
     std::sort(cls.begin(), cls.end());
     // per-class variant; second-variant classes sort after all others
     std::vector<int8_t> var((size_t)ns * ns, 0);
@@ -515,11 +521,11 @@ bsm_status shape_order(Scratch &sc, int64_t n, const int32_t *blk_rc, const std:
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, out, n, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "shape order"))) return st;
     if (grouped) {
-        // positions in the sorted order where the one-tile-row blocks and the lane items start
+        // positions in the sorted order where group 1 and the lane items start
         const int64_t mult = use_tiles ? nrt * nct : (row_rank ? std::max(nbr, 1) : 1);
         const int32_t ncls = (int32_t)cls.size();
         int32_t q1 = 0;
-        while (q1 < ncls && group_of(sizes[cls[q1].second / ns]) == 0) ++q1;
+        while (q1 < ncls && group_of(sizes[cls[q1].second / ns], sizes[cls[q1].second % ns]) == 0) ++q1;
         int64_t *gb;
         if ((st = sc.get(&gb, 2))) return st;
         if ((st = cuda_check(launch_group_bounds(keys_sorted, n, (uint32_t)(q1 * mult), (uint32_t)(ncls * mult), gb,
@@ -1623,8 +1629,8 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     // products (the whole C, or one row panel of a chunked multiply)
     float *plain_x = nullptr, *plain_y = nullptr;
     // split paths: blocks of one tile row in their own kernel instance, unless
-    // the tuning fixes the pass rows
-    const bool want_groups = tune_of(rprec)[BSM_TUNE_PASS_MT] <= 0;
+    // the tuning fixes the pass rows; Ozaki path: blocks of one tile column
+    const bool want_groups = rprec == BSM_P_OZAKI || tune_of(rprec)[BSM_TUNE_PASS_MT] <= 0;
     auto numeric_pass = [&](int64_t cb0, int64_t nitems, int64_t nprod_pass, bool whole) -> bsm_status {
         NumericArgs na{};
         na.n_items = nitems;

@@ -1338,7 +1338,7 @@ template <int MAXN>
 __device__ __forceinline__ void oz_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
-    const int pn = MAXN == 3 ? 3 : (a.pass_nt == 1 ? 1 : 2);
+    const int pn = MAXN == 3 ? 3 : MAXN == 1 ? 1 : (a.pass_nt == 1 ? 1 : 2);
     for (int mt0 = 0; mt0 < MT; ++mt0)
         for (int nt0 = 0; nt0 < NT; nt0 += pn) {
             const int left = NT - nt0;
@@ -1346,9 +1346,11 @@ __device__ __forceinline__ void oz_item(const NumericArgs &a, int64_t q, int lan
                 if (left >= 3) oz_pass<3, MAXN>(a, q, lane, mt0, nt0, ring);
                 else if (left == 2) oz_pass<2, MAXN>(a, q, lane, mt0, nt0, ring);
                 else oz_pass<1, MAXN>(a, q, lane, mt0, nt0, ring);
-            } else {
+            } else if constexpr (MAXN == 2) {
                 if (pn == 2 && left >= 2) oz_pass<2, MAXN>(a, q, lane, mt0, nt0, ring);
                 else oz_pass<1, MAXN>(a, q, lane, mt0, nt0, ring);
+            } else {
+                oz_pass<1, MAXN>(a, q, lane, mt0, nt0, ring);
             }
         }
 }
@@ -1360,27 +1362,42 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_oz(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t oz_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *ring = oz_smem + warp * oz_ring_words_per_warp<MAXN>();
-    unsigned long long *ctr = a.work_counter;
     if (a.status && *a.status != 0) return;
+    // items [i0, i1): every item before the lane items (a.group < 0), or one
+    // group: blocks of two tile columns and more (0), of one tile column (1)
     const int64_t n_lane = a.n_lane_items ? *a.n_lane_items : 0;
-    const int64_t n0 = a.n_items - n_lane;
-    const int64_t tickets = n0 + (n_lane + 31) / 32;
+    int64_t i0 = 0, i1 = a.n_items - n_lane;
+    if (a.group == 0) i1 = a.item_groups[0];
+    if (a.group == 1) i0 = a.item_groups[0];
+    unsigned long long *ctr = a.work_counter + (a.group > 0 ? a.group : 0);
+    while (true) {
+        int64_t t = 0;
+        if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0) + i0;
+        if (t >= i1) break;
+        int64_t q = t;
+        if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
+        BSM_DBG_WARP_SKIP(a, q, lane)
+        oz_item<MAXN>(a, q, lane, ring);
+    }
+}
+
+// The lane items of the Ozaki path: plain FP64 FMA, one lane per block.
+__global__ void __launch_bounds__(kThreadsNum) k_numeric_oz_lane(NumericArgs a) {
+    const int lane = threadIdx.x & 31;
+    if (a.status && *a.status != 0) return;
+    const int64_t n_lane = *a.n_lane_items;
+    const int64_t lane0 = a.n_items - n_lane;
+    unsigned long long *ctr = a.work_counter + 2;
     while (true) {
         int64_t t = 0;
         if (lane == 0) t = (int64_t)atomicAdd(ctr, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= tickets) break;
-        if (t < n0) {
-            int64_t q = t;
-            if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
-            BSM_DBG_WARP_SKIP(a, q, lane)
-            oz_item<MAXN>(a, q, lane, ring);
-        } else {
-            const int64_t idx = n0 + (t - n0) * 32 + lane;
-            if (idx < a.n_items) {
-                const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
-                if (BSM_DBG_LANE_OK(a, q)) cc_lane_dispatch<double>(a, q);
-            }
+        if (t * 32 >= n_lane) break;
+        const int64_t idx = lane0 + t * 32 + lane;
+        if (idx < a.n_items) {
+            const int64_t q = (int64_t)((uint32_t)a.item_order[idx] & 0x7fffffffu);
+            if (BSM_DBG_LANE_OK(a, q)) cc_lane_dispatch<double>(a, q);
         }
     }
 }
@@ -1698,6 +1715,17 @@ int launch_cc(const NumericArgs &a, cudaStream_t s) {
     return g;
 }
 
+template <int MAXN>
+cudaError_t launch_oz(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
+    const size_t smem = sizeof(uint32_t) * (size_t)oz_ring_words_per_warp<MAXN>() * (threads / 32);
+    cudaError_t e = cudaFuncSetAttribute(k_numeric_oz<MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    *grid = persistent_grid(k_numeric_oz<MAXN>, a.n_items, smem, threads, a.ctas_per_sm);
+    k_numeric_oz<MAXN><<<*grid, threads, smem, s>>>(a);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 template <int PREC, bool FF, int PM, int PN>
 cudaError_t launch_tc_pass(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
     const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC, PM, PN>() * (threads / 32);
@@ -1770,22 +1798,22 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     const int tc_threads = (a.cta_warps == 2 ? 2 : 4) * 32;
     int grid = 0;
     if (a.prec == BSM_P_OZAKI) {
-        // passes of up to 3 tiles take the instance with the wider ring
+        // passes of up to 3 tiles take the instance with the wider ring; with
+        // item groups the blocks of one tile column run in the 1-tile instance
         const bool wide = a.pass_nt == 3;
-        const size_t smem = sizeof(uint32_t) * (size_t)(wide ? oz_ring_words_per_warp<3>() : oz_ring_words_per_warp<2>()) *
-                            (tc_threads / 32);
-        if (wide) {
-            e = cudaFuncSetAttribute(k_numeric_oz<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) {
-                grid = persistent_grid(k_numeric_oz<3>, a.n_items, smem, tc_threads, a.ctas_per_sm);
-                k_numeric_oz<3><<<grid, tc_threads, smem, s>>>(a);
-            }
-        } else {
-            e = cudaFuncSetAttribute(k_numeric_oz<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess) {
-                grid = persistent_grid(k_numeric_oz<2>, a.n_items, smem, tc_threads, a.ctas_per_sm);
-                k_numeric_oz<2><<<grid, tc_threads, smem, s>>>(a);
-            }
+        NumericArgs b = a;
+        b.group = a.item_groups ? 0 : -1;
+        e = wide ? launch_oz<3>(b, s, tc_threads, &grid) : launch_oz<2>(b, s, tc_threads, &grid);
+        if (e == cudaSuccess && a.item_groups) {
+            int g1 = 0;
+            b.group = 1;
+            e = launch_oz<1>(b, s, tc_threads, &g1);
+        }
+        if (e == cudaSuccess && a.n_lane_items) {
+            const int g = persistent_grid(k_numeric_oz_lane, a.n_items / 32 + 1, 0, kThreadsNum, a.ctas_per_sm);
+            k_numeric_oz_lane<<<g, kThreadsNum, 0, s>>>(a);
+            count_launch(1);
+            e = cudaGetLastError();
         }
         li = NumericLaunch{BSM_K_OZAKI_MMA, -1, tc_threads, grid, 1, wide ? 3 : (a.pass_nt == 1 ? 1 : 2)};
     } else if (a.prec == BSM_P_FP64_DMMA && a.dtype == BSM_FP64) {
@@ -1822,7 +1850,7 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     }
     if (e != cudaSuccess) return e;
     if (info) *info = li;
-    if (!tc) count_launch(1);  // the split paths count their launches themselves
+    if (!tc && a.prec != BSM_P_OZAKI) count_launch(1);  // the split and Ozaki paths count their own
     return cudaGetLastError();
 }
 
