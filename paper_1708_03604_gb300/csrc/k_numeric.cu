@@ -1566,19 +1566,53 @@ __global__ void k_split_plain(int64_t n, const T *data, float *out) {
 // Digits of x on its line's grid (see the Ozaki section above): slice p is
 // d_p * 2^(-9p) as BF16 bits, exact.  e = unbiased exponent of the line.
 __device__ __forceinline__ void oz_slices(double x, int e, uint32_t (&out)[kOzSlices]) {
-    if (x == 0.0) {  // padding and exact zeros: no FP64 work
+    // The recursion y_0 = x * 2^(7-e), d_p = rint(y_p), y_(p+1) = (y_p - d_p) * 512
+    // is exact in FP64 (y_p - d_p is exact, |y_p - d_p| <= 1/2), so it is run on
+    // the integers: r = |x| * 2^(62-e) truncated (below 2^63; `sticky` records
+    // whether anything was cut), digit p = r / 2^(55-9p) rounded half to even
+    // with the cut part counted, r minus the digit.  The same digits as the
+    // FP64 recursion -- signs of zero digits included -- without the FP64 pipe.
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    if (mag == 0) {  // padding and exact zeros
 #pragma unroll
         for (int p = 0; p < kOzSlices; ++p) out[p] = 0u;
         return;
     }
-    double y = ldexp(x, 7 - e);
-    double sc = 1.0;
+    const bool neg = (b >> 63) != 0;
+    int ex = (int)(mag >> 52);
+    unsigned long long m = mag & 0xfffffffffffffull;
+    if (ex) m |= 1ull << 52;
+    else ex = 1;
+    // |x| * 2^(62-e) = m * 2^(ex - 1013 - e), ex - 1013 - e <= 11 and m < 2^53 (2^52 for ex = 1)
+    const int sh = ex - 1013 - e;
+    long long r;
+    bool sticky;
+    if (sh >= 0) {
+        r = (long long)(m << sh);
+        sticky = false;
+    } else if (sh > -64) {
+        r = (long long)(m >> -sh);
+        sticky = (m & ((1ull << -sh) - 1ull)) != 0ull;
+    } else {
+        r = 0;
+        sticky = true;
+    }
 #pragma unroll
     for (int p = 0; p < kOzSlices; ++p) {
-        const double d = rint(y);
-        out[p] = __bfloat16_as_ushort(__double2bfloat16(d * sc));
-        y = (y - d) * 512.0;
-        sc *= 1.0 / 512.0;
+        const int k = 55 - 9 * p;
+        const long long rp = r;
+        long long q = r >> k;  // floor
+        const long long rem = r - (long long)((unsigned long long)q << k);
+        const long long half = 1ll << (k - 1);
+        if (rem > half || (rem == half && (sticky || (q & 1)))) ++q;
+        r = (long long)((unsigned long long)r - ((unsigned long long)q << k));
+        // d_p * 2^(-9p) with |d_p| <= 256: exact in FP32 and in BF16; a zero digit
+        // takes the sign of the remainder it rounded (rint keeps it)
+        float v = (float)q * __int_as_float((127 - 9 * p) << 23);
+        if (neg) v = -v;
+        if (q == 0) v = (neg ? (rp > 0 || (rp == 0 && sticky)) : (rp < 0)) ? -0.0f : 0.0f;
+        out[p] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
     }
 }
 
