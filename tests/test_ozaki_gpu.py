@@ -197,3 +197,58 @@ def test_ozaki_rejects_fp32(bsm):
     with pytest.raises(bsm.BsmError) as e:
         bsm.multiply(1.0, bsm.Matrix.from_host(w["A"]), bsm.Matrix.from_host(w["B"]), prec="ozaki")
     assert e.value.status == bsm.BSM_ERR_UNSUPPORTED
+
+
+def test_ozaki_integer_data_is_exact(bsm, oracle):
+    """Small integers: every slice product and level sum is exact and so is the
+    FP64 oracle's sum, so the two agree bit for bit (negative entries, exact
+    zeros and values that end a line's digits early included)."""
+    rng = np.random.default_rng(23)
+    bs = rng.integers(1, 41, size=30).astype(np.int32)
+    A, B = random_bcsr(bs, bs, 0.3, seed=131), random_bcsr(bs, bs, 0.3, seed=132)
+    A.data[:] = rng.integers(-100, 101, size=A.data.size)
+    B.data[:] = rng.integers(-100, 101, size=B.data.size) * 0.25
+    Cg = bsm.multiply(1.0, bsm.Matrix.from_host(A), bsm.Matrix.from_host(B), prec="ozaki")
+    ref = oracle.multiply(1.0, A, B)
+    _check_pattern(Cg, ref.C)
+    np.testing.assert_array_equal(Cg.data_host(), ref.C.data)
+
+
+def test_ozaki_subnormal_lines(bsm, oracle):
+    """Rows of A whose entries are all subnormal (the line exponent field is 0,
+    so the line is scaled as if its largest entry were 2^-1023) and rows
+    mixing subnormal and normal entries: every element within 2^-44 of
+    2^(ex + ey) per term of k, ex the line exponent the slicing uses."""
+    rng = np.random.default_rng(29)
+    bs = rng.integers(1, 24, size=20).astype(np.int32)
+    A, B = random_bcsr(bs, bs, 0.4, seed=141), random_bcsr(bs, bs, 0.4, seed=142)
+    ro = offsets(bs)
+    Ad = to_dense(A)
+    rows = np.arange(int(ro[-1]))
+    sub = rows % 3 == 0                  # all-subnormal rows
+    mix = rows % 3 == 1                  # subnormal and normal entries
+    for b in range(len(A.col_idx)):
+        i = int(np.searchsorted(np.asarray(A.row_ptr), b, side="right") - 1)
+        m, n = int(A.row_bs[i]), int(A.col_bs[A.col_idx[b]])
+        blk = A.data[A.blk_off[b]:A.blk_off[b] + m * n].reshape(m, n)
+        r = np.arange(ro[i], ro[i] + m)
+        tiny = rng.integers(-2**40, 2**40, size=(m, n)) * 2.0 ** -1074
+        blk[sub[r]] = tiny[sub[r]]
+        pick = rng.random((m, n)) < 0.5
+        blk[mix[r]] = np.where(pick[mix[r]], tiny[mix[r]], blk[mix[r]])
+    Cg = bsm.multiply(1.0, bsm.Matrix.from_host(A), bsm.Matrix.from_host(B), prec="ozaki")
+    ref = oracle.multiply(1.0, A, B)
+    _check_pattern(Cg, ref.C)
+    got = I.BCSR(ref.C.row_bs, ref.C.col_bs, ref.C.row_ptr, ref.C.col_idx, ref.C.blk_off, Cg.data_host())
+    Dg, Dr = to_dense(got), to_dense(ref.C)
+    Ad, Bd = to_dense(A), to_dense(B)
+    K = block_mask(A).astype(np.float64) @ block_mask(B).astype(np.float64)
+    rowmax = np.max(np.abs(Ad), axis=1)
+    colmax = np.max(np.abs(Bd), axis=0)
+    ex = np.maximum(np.floor(np.log2(np.where(rowmax > 0, rowmax, 1.0))), -1023)
+    ey = np.maximum(np.floor(np.log2(np.where(colmax > 0, colmax, 1.0))), -1023)
+    bound = K * np.ldexp(1.0, (ex[:, None] + ey[None, :] - 44).clip(-1074, 1023).astype(np.int64))
+    # the oracle's own rounding at the bottom of the FP64 range
+    bound = bound + K * 2.0 ** -1074
+    assert np.all(np.abs(Dg - Dr) <= bound)
+    assert np.any(Dg[sub] != 0.0)
