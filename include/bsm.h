@@ -267,11 +267,21 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  *                        with the compensated sum, flush_every <= 0), the
  *                        mma.sync kernel elsewhere -- for workloads where the
  *                        tuner measured the engine faster
+ *   BSM_TUNE_PANEL_STEPS the tcgen05 row-panel engine (BSM_P_TF32x3_PANEL, and
+ *                        BSM_P_TF32x3 with engine 1): k-steps (128 x 128 x 24
+ *                        products) summed in one FP32 accumulator buffer of
+ *                        tensor memory before the drain adds it into the
+ *                        compensated pair, 1..8 (default 3).  Fewer drains per
+ *                        k-step, at an error bound that grows with it: per
+ *                        element (3 * 2^-22 + 3 * T * s * 2^-23 + 2^-22 +
+ *                        steps * 2^-33) * sum_k |a_ik| |b_kj| for T k-steps per
+ *                        buffer and blocks of s rows
  * Values outside these ranges are BSM_ERR_ARG.
  */
 enum {
     BSM_TUNE_CTA_WARPS = 0, BSM_TUNE_CTAS_PER_SM = 1, BSM_TUNE_PASS_MT = 2, BSM_TUNE_PASS_NT = 3,
-    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_SCHED_TILE = 5, BSM_TUNE_ENGINE = 6, BSM_TUNE_COUNT = 7
+    BSM_TUNE_FP64_BUILD = 4, BSM_TUNE_SCHED_TILE = 5, BSM_TUNE_ENGINE = 6, BSM_TUNE_PANEL_STEPS = 7,
+    BSM_TUNE_COUNT = 8
 };
 bsm_status bsm_set_tuning(int32_t prec, int32_t param, int32_t value);
 bsm_status bsm_get_tuning(int32_t prec, int32_t param, int32_t *value);

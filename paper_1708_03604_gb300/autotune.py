@@ -21,7 +21,9 @@ recorded by the library around the launch) on the caller's operands:
   rows x ranked columns so that the blocks in flight share A's and B's
   blocks in L2;
 * for TF32x3, the engine: the per-C-block mma.sync kernel or the tcgen05
-  row-panel engine (where it applies);
+  row-panel engine (where it applies), and for the latter the k-steps summed
+  in one tensor-memory accumulator before each drain -- the fastest within
+  ``err_target`` of the FP64 path;
 * for the split paths, the interval F of the FP64 running sum (FP32
   accumulation over at most F block products), the fastest F whose result is
   within ``err_target`` (relative Frobenius) of the FP64 path on the same
@@ -58,6 +60,7 @@ for _p in SPLIT:
 # TF32x3 may also run on the tcgen05 row-panel engine where it applies
 SEARCH["tf32x3"] = SEARCH["tf32x3"] + [("engine", [0, 1])]
 FLUSH_CANDIDATES = [-1, 1, 2, 4, 8, 16]
+PANEL_STEPS = [3, 4, 6, 8]
 
 
 def _shapes(A: bsm.Matrix, B: bsm.Matrix):
@@ -79,6 +82,8 @@ def reset(prec: str, sizes=()):
     variants of these block sizes)."""
     for name, _ in SEARCH.get(prec, []):
         bsm.bsm_set_tuning(prec, name, -1)
+    if prec == "tf32x3":
+        bsm.bsm_set_tuning(prec, "panel_steps", -1)
     for m in sizes:
         for n in sizes:
             bsm.bsm_set_variant(prec, int(m), int(n), -1)
@@ -93,7 +98,7 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
     """Choose the variants and launch knobs of `prec` for A.B; returns the
     table (also left in effect in the library)."""
     if prec == "tf32x3_panel":
-        raise ValueError("the tf32x3_panel engine has no tuning knobs: tune 'tf32x3' for the kernel it falls back to")
+        raise ValueError("the tf32x3_panel engine is tuned through 'tf32x3' (its engine and panel_steps knobs)")
     fp64_like = prec in ("fp64", "fp64_dmma", "ozaki")  # lane variant = plain FP64 FMA
     shapes = [(m, n) for m, n in _shapes(A, B)
               if m * n <= 16 or (m, n) == (5, 5) or (fp64_like and (m, n) == (6, 6))]
@@ -155,6 +160,20 @@ def tune(A: bsm.Matrix, B: bsm.Matrix, eps: float = 0.0, prec: str = "tf32x3", r
             if panel_ran and t1 < t0 * (1.0 - gain):
                 params["engine"] = 1
                 flush = None       # the panel engine keeps its own compensated sum
+                # k-steps per accumulator buffer: the fastest within the error target
+                import torch
+                ref = bsm.multiply(1.0, A, B, 0.0, None, eps, build_stacks=False).data_tensor()
+                steps_best, steps_trials = (PANEL_STEPS[0], t1), {}
+                for v in PANEL_STEPS:
+                    bsm.bsm_set_tuning(prec, "panel_steps", v)
+                    t = _numeric_ms(A, B, eps, prec, reps, Cm, phase="total")
+                    err = _rel_err(torch, Cm.data_tensor_view(), ref)
+                    steps_trials[str(v)] = {"total_ms": t, "rel_fro_err_vs_fp64_path": err}
+                    if err <= err_target and t < steps_best[1] * (1.0 - gain):
+                        steps_best = (v, t)
+                bsm.bsm_set_tuning(prec, "panel_steps", steps_best[0])
+                params["panel_steps"] = steps_best[0]
+                engine_trials["panel_steps_trials"] = steps_trials
             else:
                 bsm.bsm_set_tuning(prec, "engine", 0)
                 params["engine"] = 0

@@ -313,7 +313,8 @@ def bsm_get_variant(prec, m: int, n: int) -> int:
     return v.value
 
 
-TUNE_PARAMS = {"cta_warps": 0, "ctas_per_sm": 1, "pass_mt": 2, "pass_nt": 3, "fp64_build": 4, "sched_tile": 5, "engine": 6}
+TUNE_PARAMS = {"cta_warps": 0, "ctas_per_sm": 1, "pass_mt": 2, "pass_nt": 3, "fp64_build": 4, "sched_tile": 5, "engine": 6,
+               "panel_steps": 7}
 KERNEL_NAMES = {-1: "none", 0: "fp64_cores", 1: "fp64_mma", 2: "split_mma", 3: "ozaki_mma", 4: "panel_tcgen05"}
 
 

@@ -107,6 +107,9 @@ void tune_range(int prec, int param, int *lo, int *hi) {
         case BSM_TUNE_ENGINE:
             if (prec == BSM_P_TF32x3) { *lo = 0; *hi = 1; }
             break;
+        case BSM_TUNE_PANEL_STEPS:
+            if (prec == BSM_P_TF32x3 || prec == BSM_P_TF32x3_PANEL) { *lo = 1; *hi = 8; }
+            break;
     }
 }
 // the tuning of `prec` into the numeric launch arguments
@@ -703,7 +706,7 @@ struct PanelOut {
     int32_t *status;
 };
 
-bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const PanelOut &o, Events &ev) {
+bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const PanelOut &o, Events &ev, int tune_prec) {
     bsm_status st;
     if ((st = panel_orders(A, B)) || (st = ensure_transpose(B))) return st;
     const int32_t nbr = A->nbr, nbc = B->nbc;
@@ -784,6 +787,7 @@ bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const Panel
     pa.status = o.status;
     pa.work_counter = counter;
     pa.wait_ns = panel_wait_ns();
+    pa.pair = tune_of(tune_prec)[BSM_TUNE_PANEL_STEPS] > 0 ? tune_of(tune_prec)[BSM_TUNE_PANEL_STEPS] : panel_pair();
     ev.mark(5);
     if ((st = cuda_check(launch_panel_numeric(pa, g_stream), "panel numeric"))) return st;
     ev.mark(6);
@@ -1606,7 +1610,7 @@ bsm_status bsm_multiply(double alpha, bsm_t A, bsm_t B, double beta, bsm_t C, do
     if (use_panel) {
         PanelOut po{nnzbC, crow_ptr, c_col, c_off, static_cast<double *>(c_data), old_off,
                     use_old ? C->data : nullptr, alpha, use_old ? beta : 0.0, C->status};
-        if ((st = run_panel(sc, A, B, panel_s, po, ev))) return st;
+        if ((st = run_panel(sc, A, B, panel_s, po, ev, opts.prec))) return st;
         int32_t hs = 0;
         e = cudaMemcpyAsync(&hs, C->status, sizeof(int32_t), cudaMemcpyDeviceToHost, g_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);

@@ -422,11 +422,13 @@ struct PanelArgs {
     unsigned long long *work_counter;     // zeroed by the caller
     unsigned long long wait_ns;           // limit of the main-loop waits (the drain of
                                           // work in flight always allows 2 s)
+    int32_t pair;                         // k-steps summed in one accumulator buffer (>= 1)
 };
 // limit of the panel kernel's main-loop waits (bsm_set_wait_limit)
 unsigned long long panel_wait_ns();
 int64_t panel_pack_bytes(int64_t nblk);
 int panel_slot();
+int panel_pair();   // default k-steps per accumulator buffer
 int panel_tile_rows();
 int panel_tile_cols();
 size_t panel_tile_smem(int32_t ngc);

@@ -75,7 +75,7 @@ constexpr int kStageBytes = 2 * kOperand;    // A, then B
 constexpr int kStages = 4;
 constexpr int kRing = 8;                  // tiles handed from the ticket warp to the copy warps
 constexpr int kPre = 4;                   // list entries the merge loads ahead
-constexpr int kPair = 3;                  // k-steps summed in one accumulator buffer before a drain
+constexpr int kPair = 3;                  // default k-steps summed in one accumulator buffer before a drain
 constexpr int kCopyWarps = 2, kMmaWarp = 3, kDrainWarps = 8;
 constexpr int kThreads = 32 * (2 + kCopyWarps + kDrainWarps);
 constexpr unsigned long long kWaitNs = 2000000000ull;  // a wait gives up after 2 s
@@ -664,8 +664,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
-        // kPair consecutive k-steps of a tile accumulate in one buffer before
-        // the drain adds it into the compensated pair
+        // a.pair (default kPair) consecutive k-steps of a tile accumulate in
+        // one buffer before the drain adds it into the compensated pair
         uint32_t st = 0, ph = 0, buf = 0, bph = 0;
         int in_group = 0, gflags = 0;
         if (lane == 0) {
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
                 }
                 mma_commit(saddr(&ctl.empty[st]));
                 gflags |= flags & kFirst;
-                if ((flags & kLast) || in_group + 1 == kPair) {
+                if ((flags & kLast) || in_group + 1 == a.pair) {
                     ctl.ameta_t[buf] = tile;
                     ctl.ameta_f[buf] = gflags | (flags & kLast);
                     mma_commit(saddr(&ctl.accf[buf]));
@@ -742,6 +742,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_panel_tf32x3(PanelArgs a) {
 
 int64_t panel_pack_bytes(int64_t nblk) { return nblk * kBlk; }
 int panel_slot() { return kSlot; }
+int panel_pair() { return kPair; }
 int panel_tile_rows() { return kRB; }
 int panel_tile_cols() { return kCB; }
 

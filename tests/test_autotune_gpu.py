@@ -133,6 +133,10 @@ def test_knob_ranges_are_checked(bsm):
         bsm.bsm_set_tuning("fp64", "sched_tile", 4)
     with pytest.raises(bsm.BsmError):
         bsm.bsm_set_tuning("bf16x6", "engine", 1)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("tf32x3_panel", "panel_steps", 9)
+    with pytest.raises(bsm.BsmError):
+        bsm.bsm_set_tuning("ozaki", "panel_steps", 3)
 
 
 def test_tuned_table_roundtrip(bsm, operands, tmp_path):
@@ -141,7 +145,10 @@ def test_tuned_table_roundtrip(bsm, operands, tmp_path):
     try:
         table = autotune.tune(A, B, 0.3, prec="tf32x3", reps=1)
         assert table["numeric_ms"]["tuned"] > 0
-        assert set(table["params"]) == {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm", "sched_tile", "engine"}
+        keys = {"cta_warps", "pass_mt", "pass_nt", "ctas_per_sm", "sched_tile", "engine"}
+        if table["params"]["engine"] == 1:
+            keys.add("panel_steps")
+        assert set(table["params"]) == keys
         # the flush interval the tuner chose keeps the error within its target
         if table["flush_every"] is not None:
             assert table["flush_trials"][str(table["flush_every"])]["rel_fro_err_vs_fp64_path"] <= 1e-6
