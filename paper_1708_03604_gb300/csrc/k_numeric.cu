@@ -1105,14 +1105,16 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc_lane(NumericArgs a) 
 // than kOzWindow terms of k they are converted to integers and added into a
 // 64-bit fixed-point sum with unit 2^-27 (exact; a window adds less than
 // 2^49.01 units, so 8192 windows fit, after which the sum is moved into the
-// output element).  Levels 4 and 5 (11 pairs, below 2^-33 of level 0) share
-// one rounded FP32 sum per window (the tensor core's FP32 additions round
-// toward zero, so it is restarted every window) whose window values add up in
-// an FP32 sum with round-to-nearest on the CUDA cores; levels >= 6 are
-// dropped (below 2^-50 of level 0).  Per term of k the error is below 2^-44
+// output element).  Levels 4 and 5 (11 pairs, below 2^-33 of level 0) have
+// a rounded FP32 sum each per window (the tensor core's FP32 additions round
+// toward zero, so they are restarted every window; two sums rather than one
+// keep every accumulator's chain of dependent MMAs at 6 per k-step or less),
+// whose window values add up in an FP32 sum with round-to-nearest on the
+// CUDA cores; levels >= 6 are dropped (below 2^-50 of level 0).  Per term of k the error is below 2^-44
 // of 2^(ex+ey): the rounded sums plus the cut digits and levels.
 constexpr int kOzSlices = 6;
-constexpr int kOzLevels = 5;    // FP32 sums: levels 0, 1, 2, 3 exact, 4..5 rounded
+constexpr int kOzLevels = 6;    // FP32 sums: levels 0, 1, 2, 3 exact, 4 and 5 rounded (one each,
+                                // so that no accumulator takes more than 6 of a k-step's 21 MMAs)
 constexpr int kOzWindow = 64;
 constexpr int kOzSpillWindows = 8192;
 constexpr int kOzStages = 3;
@@ -1180,7 +1182,7 @@ __device__ __forceinline__ void oz_pass(const NumericArgs &a, int64_t q, int lan
                 t += (long long)__float2int_rn(acc[2][j][v] * 262144.f) << 9;
                 t += (long long)__float2int_rn(acc[3][j][v] * 134217728.f);
                 fx[j][v] += t;
-                low[j][v] = __fadd_rn(low[j][v], acc[kOzLevels - 1][j][v]);
+                low[j][v] = __fadd_rn(low[j][v], __fadd_rn(acc[4][j][v], acc[5][j][v]));
 #pragma unroll
                 for (int l = 0; l < kOzLevels; ++l) acc[l][j][v] = 0.f;
             }
