@@ -245,9 +245,9 @@ bsm_status bsm_get_variant(int32_t prec, int32_t m, int32_t n, int32_t *variant)
  *                        in that one instance), FP64_DMMA 1..3 (default 3,
  *                        8-row tiles)
  *   BSM_TUNE_PASS_NT     along the columns: split paths 1..3 (default 3,
- *                        8-column tiles), OZAKI 1..3 (default 2; 3 runs a
- *                        kernel instance with a larger staging ring), FP64_DMMA
- *                        1..3 (default 3)
+ *                        8-column tiles), OZAKI 1..3 (default 3; 1 and 2 run
+ *                        a kernel instance with a smaller staging ring and
+ *                        fewer registers), FP64_DMMA 1..3 (default 3)
  *   BSM_TUNE_FP64_BUILD  BSM_P_FP64 only: FP64 FMA kernel build, 0 chosen by
  *                        the largest output block (default), 1 narrow (up to
  *                        9 elements per lane per pass), 2 wide (up to 24);

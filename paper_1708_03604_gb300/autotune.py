@@ -51,7 +51,7 @@ TILES = ("sched_tile", [0, 16, 32, 64, 128])
 SEARCH = {
     "fp64": [("fp64_build", [0, 1, 2]), ("ctas_per_sm", [0, 1, 2, 3, 4]), TILES],
     "fp64_dmma": [("pass_mt", [3, 2, 1]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 4]), TILES],
-    "ozaki": [("cta_warps", [4, 2]), ("pass_nt", [2, 1, 3]), ("ctas_per_sm", [0, 1, 2, 3]), TILES],
+    "ozaki": [("cta_warps", [4, 2]), ("pass_nt", [3, 2, 1]), ("ctas_per_sm", [0, 1, 2, 3]), TILES],
 }
 for _p in SPLIT:
     # pass_mt -1: blocks of one tile row in a 1-row kernel instance, the rest in a 2-row one

@@ -1834,9 +1834,10 @@ cudaError_t launch_numeric(const NumericArgs &a, cudaStream_t s, NumericLaunch *
     const int tc_threads = (a.cta_warps == 2 ? 2 : 4) * 32;
     int grid = 0;
     if (a.prec == BSM_P_OZAKI) {
-        // passes of up to 3 tiles take the instance with the wider ring; with
-        // item groups the blocks of one tile column run in the 1-tile instance
-        const bool wide = a.pass_nt == 3;
+        // passes of up to 3 tiles (the default) take the instance with the
+        // wider ring; with item groups the blocks of one tile column run in
+        // the 1-tile instance
+        const bool wide = a.pass_nt != 1 && a.pass_nt != 2;
         NumericArgs b = a;
         b.group = a.item_groups ? 0 : -1;
         e = wide ? launch_oz<3>(b, s, tc_threads, &grid) : launch_oz<2>(b, s, tc_threads, &grid);
