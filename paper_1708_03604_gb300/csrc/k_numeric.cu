@@ -632,7 +632,7 @@ __device__ __forceinline__ double pair_total(float hi, float lo, float b) {
 // starting at (mt0, nt0) of output block q: at most 32 x 24 output elements.
 // FF: cross-product sum as a compensated float pair (Kahan after every |F| block
 // products); otherwise an FP64 sum refreshed every F products.
-template <int PREC, int MTC, int NTC, bool FF, int PM, int PN>
+template <int PREC, int MTC, int NTC, bool FF, int PM, int PN, bool DUAL>
 __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lane, int mt0, int nt0,
                                         uint32_t *ring) {
     using PT = PrecTraits<PREC>;
@@ -651,7 +651,12 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
     const uint32_t ring_s = smem_addr(myring);
     constexpr int XC = PT::XW / 4, YC = PT::YW / 4;  // chunks per tile
 
-    float acc[MTC][NTC][4];
+    // DUAL (1-row instances summing more than one block product in the tensor
+    // core, F > 1): the piece products of a k-step alternate between two
+    // accumulators (term t into acc if t is even, acc2 if odd), so that the
+    // tensor core's chain of dependent MMAs on one tile is about half as long;
+    // the two are added (FP32, to nearest) where the single one was read
+    float acc[MTC][NTC][4], acc2[DUAL ? MTC : 1][DUAL ? NTC : 1][4];
     float shi[FF ? MTC : 1][FF ? NTC : 1][4], slo[FF ? MTC : 1][FF ? NTC : 1][4];
     double s64[FF ? 1 : MTC][FF ? 1 : NTC][4];
 #pragma unroll
@@ -661,6 +666,7 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 acc[i][j][v] = 0.f;
+                if constexpr (DUAL) acc2[i][j][v] = 0.f;
                 if constexpr (FF) {
                     shi[i][j][v] = 0.f;
                     slo[i][j][v] = 0.f;
@@ -760,7 +766,10 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                 for (int j = 0; j < NTC; ++j)
 #pragma unroll
                     for (int i = 0; i < MTC; ++i)
-                        if (mt0 + i < MT && nt0 + j < NT) mma_piece<PREC>(acc[i][j], fa[i][ia], fb[j][ib]);
+                        if (mt0 + i < MT && nt0 + j < NT) {
+                            if (DUAL && (t & 1)) mma_piece<PREC>(acc2[DUAL ? i : 0][DUAL ? j : 0], fa[i][ia], fb[j][ib]);
+                            else mma_piece<PREC>(acc[i][j], fa[i][ia], fb[j][ib]);
+                        }
             }
             if (++ck == ckt) {  // a block product is complete
                 ck = 0;
@@ -774,8 +783,13 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                         for (int j = 0; j < NTC; ++j)
 #pragma unroll
                             for (int v = 0; v < 4; ++v) {
-                                if constexpr (FF) kahan_acc(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
-                                else s64[i][j][v] += widen(acc[i][j][v]);
+                                float part = acc[i][j][v];
+                                if constexpr (DUAL) {
+                                    part = __fadd_rn(part, acc2[DUAL ? i : 0][DUAL ? j : 0][v]);
+                                    acc2[DUAL ? i : 0][DUAL ? j : 0][v] = 0.f;
+                                }
+                                if constexpr (FF) kahan_acc(shi[i][j][v], slo[i][j][v], part);
+                                else s64[i][j][v] += widen(part);
                                 acc[i][j][v] = 0.f;
                             }
                 }
@@ -798,8 +812,10 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
                 const int c = (nt0 + j) * 8 + 2 * t4 + (v & 1);
                 if (r < R && c < S) {
                     double sum;
-                    if constexpr (FF) sum = pair_total(shi[i][j][v], slo[i][j][v], acc[i][j][v]);
-                    else sum = s64[i][j][v] + widen(acc[i][j][v]);
+                    float part = acc[i][j][v];
+                    if constexpr (DUAL) part = __fadd_rn(part, acc2[DUAL ? i : 0][DUAL ? j : 0][v]);
+                    if constexpr (FF) sum = pair_total(shi[i][j][v], slo[i][j][v], part);
+                    else sum = s64[i][j][v] + widen(part);
                     double val = a.alpha == 1.0 ? sum : a.alpha * sum;
                     const int64_t e = (int64_t)r * S + c;
                     if (a.dtype == BSM_FP64) {
@@ -813,7 +829,7 @@ __device__ __forceinline__ void tc_pass(const NumericArgs &a, int64_t q, int lan
             }
 }
 
-template <int PREC, bool FF, int PM, int PN>
+template <int PREC, bool FF, int PM, int PN, bool DUAL>
 __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lane, uint32_t *ring) {
     const int32_t orc = a.out_blk_rc[q];
     const int MT = (rc_rows(orc) + 15) >> 4, NT = (rc_cols(orc) + 7) >> 3;
@@ -823,16 +839,16 @@ __device__ __forceinline__ void tc_item(const NumericArgs &a, int64_t q, int lan
         for (int nt0 = 0; nt0 < NT; nt0 += pn) {
             const int ntc = min(pn, NT - nt0);
             if (PM == 1 || mtc == 1) {
-                if (PN == 1 || ntc == 1) tc_pass<PREC, 1, 1, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                if (PN == 1 || ntc == 1) tc_pass<PREC, 1, 1, FF, PM, PN, DUAL>(a, q, lane, mt0, nt0, ring);
                 else if constexpr (PN >= 2) {
-                    if (PN == 2 || ntc == 2) tc_pass<PREC, 1, 2, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
-                    else if constexpr (PN >= 3) tc_pass<PREC, 1, 3, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                    if (PN == 2 || ntc == 2) tc_pass<PREC, 1, 2, FF, PM, PN, DUAL>(a, q, lane, mt0, nt0, ring);
+                    else if constexpr (PN >= 3) tc_pass<PREC, 1, 3, FF, PM, PN, DUAL>(a, q, lane, mt0, nt0, ring);
                 }
             } else if constexpr (PM >= 2) {
-                if (PN == 1 || ntc == 1) tc_pass<PREC, 2, 1, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                if (PN == 1 || ntc == 1) tc_pass<PREC, 2, 1, FF, PM, PN, DUAL>(a, q, lane, mt0, nt0, ring);
                 else if constexpr (PN >= 2) {
-                    if (PN == 2 || ntc == 2) tc_pass<PREC, 2, 2, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
-                    else if constexpr (PN >= 3) tc_pass<PREC, 2, 3, FF, PM, PN>(a, q, lane, mt0, nt0, ring);
+                    if (PN == 2 || ntc == 2) tc_pass<PREC, 2, 2, FF, PM, PN, DUAL>(a, q, lane, mt0, nt0, ring);
+                    else if constexpr (PN >= 3) tc_pass<PREC, 2, 3, FF, PM, PN, DUAL>(a, q, lane, mt0, nt0, ring);
                 }
             }
         }
@@ -1041,7 +1057,7 @@ __device__ __forceinline__ void cs_lane_dispatch(const NumericArgs &a, int64_t q
 // order, a warp each on the tensor cores: every item before the lane items
 // (a.group < 0), or one group of a multiply whose blocks of one tile row run
 // in a 1 x PN instance (group 1) and the rest in a 2 x PN instance (group 0).
-template <int PREC, bool FF, int PM, int PN>
+template <int PREC, bool FF, int PM, int PN, bool DUAL>
 __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
     extern __shared__ __align__(16) uint32_t tc_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1060,7 +1076,7 @@ __global__ void __launch_bounds__(kThreadsNum) k_numeric_tc(NumericArgs a) {
         int64_t q = t;
         if (a.item_order) q = (int64_t)((uint32_t)a.item_order[q] & 0x7fffffffu);
         BSM_DBG_WARP_SKIP(a, q, lane)
-        tc_item<PREC, FF, PM, PN>(a, q, lane, ring);
+        tc_item<PREC, FF, PM, PN, DUAL>(a, q, lane, ring);
     }
 }
 
@@ -1762,16 +1778,27 @@ cudaError_t launch_oz(const NumericArgs &a, cudaStream_t s, int threads, int *gr
     return cudaGetLastError();
 }
 
-template <int PREC, bool FF, int PM, int PN>
-cudaError_t launch_tc_pass(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
+template <int PREC, bool FF, int PM, int PN, bool DUAL>
+cudaError_t launch_tc_inst(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
     const size_t smem = sizeof(uint32_t) * (size_t)ring_words_per_warp<PREC, PM, PN>() * (threads / 32);
-    cudaError_t e = cudaFuncSetAttribute(k_numeric_tc<PREC, FF, PM, PN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_numeric_tc<PREC, FF, PM, PN, DUAL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    *grid = persistent_grid(k_numeric_tc<PREC, FF, PM, PN>, a.n_items, smem, threads, a.ctas_per_sm);
-    k_numeric_tc<PREC, FF, PM, PN><<<*grid, threads, smem, s>>>(a);
+    *grid = persistent_grid(k_numeric_tc<PREC, FF, PM, PN, DUAL>, a.n_items, smem, threads, a.ctas_per_sm);
+    k_numeric_tc<PREC, FF, PM, PN, DUAL><<<*grid, threads, smem, s>>>(a);
     count_launch(1);
     return cudaGetLastError();
+}
+
+// 1-row instances with two accumulators where F > 1 block products share the
+// tensor core's sum
+template <int PREC, bool FF, int PM, int PN>
+cudaError_t launch_tc_pass(const NumericArgs &a, cudaStream_t s, int threads, int *grid) {
+    const int F = a.flush_every > 0 ? a.flush_every : (a.flush_every < 0 ? -a.flush_every : 1);
+    if constexpr (PM == 1) {
+        if (F > 1) return launch_tc_inst<PREC, FF, PM, PN, true>(a, s, threads, grid);
+    }
+    return launch_tc_inst<PREC, FF, PM, PN, false>(a, s, threads, grid);
 }
 
 template <int PREC, bool FF, int PM>
