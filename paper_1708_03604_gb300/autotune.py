@@ -24,9 +24,10 @@ recorded by the library around the launch) on the caller's operands:
   row-panel engine (where it applies), and for the latter the k-steps summed
   in one tensor-memory accumulator before each drain -- the fastest within
   ``err_target`` of the FP64 path;
-* for the split paths, the interval F of the FP64 running sum (FP32
-  accumulation over at most F block products), the fastest F whose result is
-  within ``err_target`` (relative Frobenius) of the FP64 path on the same
+* for the split paths, the interval F of the cross-product sum (FP32
+  accumulation in the tensor core over at most F block products, then an FP64
+  running sum or a compensated FP32 pair), the fastest form and F whose result
+  is within ``err_target`` (relative Frobenius) of the FP64 path on the same
   operands.
 
 Each knob is searched in turn (coordinate descent from the library
@@ -59,7 +60,9 @@ for _p in SPLIT:
                   ("ctas_per_sm", [0, 1, 2, 3, 4]), TILES]
 # TF32x3 may also run on the tcgen05 row-panel engine where it applies
 SEARCH["tf32x3"] = SEARCH["tf32x3"] + [("engine", [0, 1])]
-FLUSH_CANDIDATES = [-1, 1, 2, 4, 8, 16]
+# flush_every: F > 0 an FP64 running sum every F block products, -F a
+# compensated FP32 pair refreshed every F products
+FLUSH_CANDIDATES = [-1, -2, -4, -8, 1, 2, 4, 8, 16]
 PANEL_STEPS = [3, 4, 6, 8]
 
 
