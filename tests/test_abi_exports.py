@@ -118,3 +118,31 @@ def test_product_limit_range():
     assert L.bsm_set_product_limit(2**31) == bsm.BSM_ERR_ARG
     assert L.bsm_set_product_limit(1000) == bsm.BSM_OK
     assert L.bsm_set_product_limit(2**31 - 1) == bsm.BSM_OK
+
+
+def test_tuning_knob_ranges_on_host():
+    """The tuning table is host state: every knob's range check runs without a
+    GPU, and a value set is read back (then the default restored)."""
+    from paper_1708_03604_gb300 import bsm
+    P, K = bsm.PREC, bsm.TUNE_PARAMS
+    L = bsm.lib()
+    ok, bad = bsm.BSM_OK, bsm.BSM_ERR_ARG
+    cases = [  # (prec, knob, value, expected status)
+        ("tf32x3", "panel_steps", 8, ok), ("tf32x3_panel", "panel_steps", 1, ok),
+        ("tf32x3_panel", "panel_steps", 9, bad), ("tf32x3", "panel_steps", 0, bad),
+        ("ozaki", "panel_steps", 3, bad), ("fp64", "panel_steps", 3, bad),
+        ("tf32x3", "pass_mt", 1, ok), ("bf16x6", "pass_mt", 3, bad), ("ozaki", "pass_mt", 1, bad),
+        ("ozaki", "pass_nt", 3, ok), ("ozaki", "pass_nt", 4, bad),
+        ("tf32x3", "engine", 1, ok), ("bf16x3", "engine", 1, bad),
+        ("fp64", "fp64_build", 2, ok), ("fp64", "fp64_build", 3, bad),
+        ("fp64", "sched_tile", 16, ok), ("fp64", "sched_tile", 7, bad),
+        ("tf32x3", "cta_warps", 3, bad), ("tf32x3", "ctas_per_sm", 17, bad),
+    ]
+    for prec, knob, value, want in cases:
+        got = L.bsm_set_tuning(P[prec], K[knob], value)
+        assert got == want, (prec, knob, value, got)
+        if got == ok:
+            assert bsm.bsm_get_tuning(prec, knob) == value
+            assert L.bsm_set_tuning(P[prec], K[knob], -1) == ok
+            assert bsm.bsm_get_tuning(prec, knob) == -1
+    assert L.bsm_set_tuning(P["tf32x3"], len(K), 1) == bad       # no such knob
