@@ -727,7 +727,7 @@ def run_headline(args, name, world, rank, local_rank):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "measured_unit_peaks_tflops": peaks, "tensor_peaks_tflops": tpk,
                 "split_precision": split,
-                "north_star_split": ({"leg": best[0], "speedup_vs_fp64": best[1]["speedup_vs_fp64"],
+                "split_fp64_sum_best": ({"leg": best[0], "speedup_vs_fp64": best[1]["speedup_vs_fp64"],
                                       "rel_fro_err_vs_oracle_rows": best[1].get("rel_fro_err_vs_oracle_rows"),
                                       "form": "split pieces on tensor cores, FP32 accumulation over at most "
                                               "F block products, FP64 running sum"} if best else None),
