@@ -747,7 +747,7 @@ bsm_status run_panel(Scratch &sc, bsm_mat *A, bsm_mat *B, int32_t s, const Panel
         e = launch_radix_sort_pairs(keys, iota, keys_alt, vals_alt, keys_sorted, order, ntiles, bits, rtmp, g_stream);
     if ((st = cuda_check(e, "panel tiles"))) return st;
     PanelArgs pa{};
-    pa.nbr = nbr; pa.nbc = nbc; pa.s = s;
+    pa.nbr = nbr; pa.nbc = nbc; pa.s = s; pa.nbk = A->nbc;
     pa.n_tiles = ntiles;
     pa.tile_order = order; pa.tile_g = tile_g; pa.tile_h = tile_h; pa.cblk = cblk;
     pa.ord_r = A->panel_ord_r; pa.ord_c = A->panel_ord_c;

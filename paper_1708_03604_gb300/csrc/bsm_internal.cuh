@@ -402,6 +402,7 @@ cudaError_t launch_add_backward(int64_t nnzb, const int64_t *z_blk_off, const in
 // column slot c) of tile t, or -1.
 struct PanelArgs {
     int32_t nbr, nbc, s;
+    int32_t nbk;                          // inner block dimension (A's block columns)
     int64_t n_tiles;
     const int32_t *tile_order;            // [n_tiles] processing order
     const int32_t *tile_g, *tile_h;       // [n_tiles]

@@ -427,6 +427,108 @@ __global__ void __launch_bounds__(256) k_panel_steps(PanelArgs a, int fill, int6
     if (!fill && lane == 0) step_cnt[t] = n;
 }
 
+// The same k-step records by bitmaps, one CTA of 128 threads per tile: each of
+// the 10 block-index lists (A's 5 rows, B's 5 columns) becomes a bitmap over k
+// in shared memory; the k-steps are the set bits of (OR of A's) AND (OR of
+// B's), in ascending k; the block of a list at k is its entry of rank
+// popcount(list bits below k) (A: the CSR position itself; B: b_t_blk of the
+// column-major position).  A block index always comes from a bit of its own
+// list, so it lies inside that list.  Used when the 22 bitmaps and prefix
+// arrays of nw = ceil(nbk / 32) words fit in shared memory.
+constexpr int kBmLists = kRB + kCB;
+__global__ void __launch_bounds__(128) k_panel_steps_bm(PanelArgs a, int fill, int64_t *step_cnt) {
+    extern __shared__ uint32_t bsm_[];
+    __shared__ int64_t lbeg[kBmLists], lend[kBmLists];
+    const int64_t t = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int nw = (a.nbk + 31) >> 5;
+    uint32_t *bm = bsm_;                                                  // [10][nw]
+    int32_t *pre = reinterpret_cast<int32_t *>(bsm_ + kBmLists * nw);     // [10][nw] exclusive
+    uint32_t *U = bsm_ + 2 * kBmLists * nw;                               // [nw]
+    int32_t *upre = reinterpret_cast<int32_t *>(bsm_ + (2 * kBmLists + 1) * nw);  // [nw] exclusive
+    if (tid < kBmLists) {
+        int64_t p = 0, pe = 0;
+        const int32_t g = a.tile_g[t], h = a.tile_h[t];
+        if (tid < kRB) {
+            const int pr = g * kRB + tid;
+            if (pr < a.nbr) {
+                const int i = a.ord_r[pr];
+                p = a.a_row_ptr[i];
+                pe = a.a_row_ptr[i + 1];
+            }
+        } else {
+            const int pc = h * kCB + tid - kRB;
+            if (pc < a.nbc) {
+                const int j = a.ord_c[pc];
+                p = a.b_t_ptr[j];
+                pe = a.b_t_ptr[j + 1];
+            }
+        }
+        lbeg[tid] = p;
+        lend[tid] = pe;
+    }
+    for (int w = tid; w < kBmLists * nw; w += blockDim.x) bm[w] = 0u;
+    __syncthreads();
+    for (int l = 0; l < kBmLists; ++l) {
+        const int32_t *list = l < kRB ? a.a_col_idx : a.b_t_row;
+        for (int64_t e = lbeg[l] + tid; e < lend[l]; e += blockDim.x) {
+            const uint32_t k = (uint32_t)list[e];
+            atomicOr(&bm[l * nw + (k >> 5)], 1u << (k & 31));
+        }
+    }
+    __syncthreads();
+    for (int w = tid; w < nw; w += blockDim.x) {
+        uint32_t ao = 0u, bo = 0u;
+#pragma unroll
+        for (int l = 0; l < kRB; ++l) ao |= bm[l * nw + w];
+#pragma unroll
+        for (int l = kRB; l < kBmLists; ++l) bo |= bm[l * nw + w];
+        U[w] = ao & bo;
+    }
+    __syncthreads();
+    // exclusive word prefixes of the popcounts: one thread per array
+    if (tid <= kBmLists) {
+        const uint32_t *src = tid < kBmLists ? bm + tid * nw : U;
+        int32_t *dst = tid < kBmLists ? pre + tid * nw : upre;
+        int32_t run = 0;
+        for (int w = 0; w < nw; ++w) {
+            dst[w] = run;
+            run += __popc(src[w]);
+        }
+    }
+    __syncthreads();
+    const int32_t total = upre[nw - 1] + __popc(U[nw - 1]);
+    if (!fill) {
+        if (tid == 0) step_cnt[t] = total > 0 ? total : 1;  // a tile with only old blocks: one empty step
+        return;
+    }
+    int32_t *rec = a.steps + a.step_ptr[t] * kBmLists;
+    if (total == 0) {
+        if (tid < kBmLists) rec[tid] = -1;
+        return;
+    }
+    for (int w = tid; w < nw; w += blockDim.x) {
+        uint32_t u = U[w];
+        int32_t sidx = upre[w];
+        while (u) {
+            const int bit = __ffs(u) - 1;
+            u &= u - 1u;
+            const uint32_t below = (1u << bit) - 1u;
+#pragma unroll
+            for (int l = 0; l < kBmLists; ++l) {
+                const uint32_t bits = bm[l * nw + w];
+                int32_t blk = -1;
+                if ((bits >> bit) & 1u) {
+                    const int64_t pos = lbeg[l] + pre[l * nw + w] + __popc(bits & below);
+                    blk = l < kRB ? (int32_t)pos : a.b_t_blk[pos];
+                }
+                rec[(int64_t)sidx * kBmLists + l] = blk;
+            }
+            ++sidx;
+        }
+    }
+}
+
 // Drain warp of tensor-memory lanes 32 quarter .. +31 (tile rows) and columns
 // 64 HALF .. +63 of both accumulator buffers: its threads keep the compensated
 // pair of their 64 elements in registers (sum FP32, compensation BF16), add
@@ -802,7 +904,13 @@ cudaError_t launch_panel_tile_keys(int64_t ntiles, const int32_t *tile_g, const 
 
 cudaError_t launch_panel_steps(const PanelArgs &a, int fill, int64_t *step_cnt, cudaStream_t s) {
     if (a.n_tiles == 0) return cudaSuccess;
-    k_panel_steps<<<(unsigned)((a.n_tiles * 32 + 255) / 256), 256, 0, s>>>(a, fill, step_cnt);
+    const int nw = (a.nbk + 31) >> 5;
+    const size_t smem = (size_t)(2 * kBmLists + 2) * nw * sizeof(uint32_t);
+    if (nw > 0 && smem <= 48 * 1024 && a.n_tiles < (int64_t(1) << 31)) {
+        k_panel_steps_bm<<<(unsigned)a.n_tiles, 128, smem, s>>>(a, fill, step_cnt);
+    } else {  // the bitmaps do not fit: the warp-per-tile merge
+        k_panel_steps<<<(unsigned)((a.n_tiles * 32 + 255) / 256), 256, 0, s>>>(a, fill, step_cnt);
+    }
     count_launch(1);
     return cudaGetLastError();
 }
